@@ -1,0 +1,338 @@
+"""Benchmark of the TT finite-volume shallow-water stage on GB300.
+
+One step = one full SSP-RK3 step (three stages: WENO5 reconstruction by
+cross, Taylor reciprocal, LLF fluxes from Hadamard products, rounding) of the
+nonlinear 256 x 256 workload (3 seeded Gaussian bumps, rank cap 32, tol
+1e-8), through the C ABI of libttfv.so.  Metric: equivalent cell updates per
+second, N^2 x steps / s (summed over ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (Oracle B, the TT algorithm in
+numpy) on this machine's host cores on the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "equiv. cell-updates/s per RK step at fixed L2 err vs FP64 oracle; % roofline"
+UNIT = "cell-updates/s"
+WORKLOAD = "nonlinear256_weno5"
+# GB300 FP64: 2 FMA / clk / SM (4 flop), 152 SMs, 2070 MHz maximum SM clock
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def make_state(w, cap):
+    from synth import initial_tt
+    Q, p = initial_tt(w)
+    return Q, p
+
+
+def traffic_for(kernel_class):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, if it was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = tab.get(kernel_class)
+    if not ent:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, ent["source"])
+    try:
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+def cpu_baseline(w, p, Q, nsteps):
+    """Oracle B (numpy TT algorithm) timed on the host cores from the initial
+    state for `nsteps` RK steps; returns (result dict, oracle state)."""
+    from oracle import tt_fv as TB
+    t0 = time.perf_counter()
+    Qo = Q
+    for _ in range(nsteps):
+        Qo = TB.step(Qo, w, p, seed=0)
+    dt = time.perf_counter() - t0
+    n = w["n"]
+    cores = os.cpu_count()
+    return {"value": n * n * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {nsteps} SSP-RK3 step(s) of the {w['n']}x{w['n']} WENO5 workload from its initial "
+                      f"state (ranks small, cheaper than later steps); numpy/OpenBLAS float64 on {cores} threads",
+            "seconds": dt}, Qo
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from synth import workload
+    from oracle import tt_fv as TB
+    w = workload(args.workload)
+    Q, p = make_state(w, w["cap"])
+    n = w["n"]
+    for _ in range(args.warmup):
+        Q = TB.step(Q, w, p, seed=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Q = TB.step(Q, w, p, seed=0)
+    dt = time.perf_counter() - t0
+    value = n * n * args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "scheme": w["scheme"], "eqn": w["eqn"],
+                       "rank_cap": w["cap"], "tol": w["tol"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"SSP-RK3 steps {args.warmup + 1}..{args.warmup + args.steps} from the "
+                                       f"initial state, numpy/OpenBLAS float64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    from synth import workload
+    from paper_2408_03483_gb300 import api, capi
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    capi.load()
+    w = workload(args.workload)
+    n, cap = w["n"], w["cap"]
+    Q, p = make_state(w, cap)
+    stream = torch.cuda.current_stream()
+
+    def new_solver(state):
+        q0 = [api.DevTT.from_cores(A, B, cap=cap) for A, B in state]
+        return api.Solver(q0, w["eqn"], w["scheme"], n, p["dt"], w["tol"], cap, g=p["g"], H=p["H"], f=p["f"],
+                          kick=4, max_sweeps=10, max_iter=50, seed=0)
+
+    # ---- parity sample: first step from the initial state vs the oracle
+    s0 = new_solver(Q)
+    s0.step(1)
+    first = s0.get()
+    s0.close()
+
+    # ---- device-timed region
+    s = new_solver(Q)
+    for _ in range(args.warmup):
+        s.step(1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    s.profile(True)
+    s.kernel_profile(reset=True)
+    launches0 = api.launch_count()
+    step_ms = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = api.launch_count() - launches0
+    prof = s.kernel_profile(reset=True)
+    s.profile(False)
+    clk = clocks.stop()
+    ranks_after = s.stats()["rank"]
+    dev_status = s.stats()["device_status"]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # ---- end-to-end through the public API from pinned host buffers
+    st = s.get()
+    host = [(torch.empty((cap, n), dtype=torch.float64).pin_memory(),
+             torch.empty((cap, n), dtype=torch.float64).pin_memory()) for _ in range(3)]
+    for (ha, hb), q in zip(host, st):
+        ha.copy_(q.a.cpu())
+        hb.copy_(q.b.cpu())
+    ranks_host = [q.rank for q in st]
+    dev_in = [api.DevTT(n, n, cap) for _ in range(3)]
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    e2e0 = time.perf_counter()
+    for _ in range(args.steps):
+        for (ha, hb), d, r in zip(host, dev_in, ranks_host):
+            d.a[:r].copy_(ha[:r], non_blocking=True)
+            d.b[:r].copy_(hb[:r], non_blocking=True)
+            d.rank = r
+            h2d += 8 * 2 * n * r
+        s.set(dev_in)
+        s.step(1)
+        out = s.get()
+        for (ha, hb), q in zip(host, out):
+            ha[:q.rank].copy_(q.a[:q.rank], non_blocking=True)
+            hb[:q.rank].copy_(q.b[:q.rank], non_blocking=True)
+            d2h += 8 * 2 * n * q.rank
+        torch.cuda.synchronize()
+        ranks_host = [q.rank for q in out]
+    e2e_s = time.perf_counter() - e2e0
+    s.close()
+
+    if rank != 0:
+        return
+    value = n * n * args.steps * world / (total_ms / 1e3)
+    # ---- roofline of the dominant kernel class (FP64 ALU bound)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
+    hbm_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        pass
+    tr = traffic_for(dom)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": tr,
+                "peak_source": "derived FP64: 152 SM x 2 FMA/clk x 2 flop x 2.070 GHz (no FP64 entry in "
+                               "MEASURED_PEAKS.json)",
+                "launches": d["launches"], "share": d["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)}
+    classes = {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                   "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else 0.0),
+                   "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else 0.0)}
+               for k, v in prof.items() if v["launches"]}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "scheme": w["scheme"], "eqn": w["eqn"],
+                       "rank_cap": cap, "tol": w["tol"], "steps_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
+                       "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
+            "clocks": clk, "gpu_launches": launches, "roofline": roofline, "kernel_classes": classes,
+            "ranks_after": ranks_after, "device_status": dev_status, "wall_s_timed": wall,
+            "e2e": {"value": n * n * args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                    "d2h_bytes_per_step": d2h // args.steps}}
+    # ---- CPU oracle baseline and the parity of the first step
+    if not args.no_cpu_baseline and world == 1:
+        from oracle import tt as T
+        cb, Qo = cpu_baseline(w, p, Q, args.cpu_sample_steps)
+        line["cpu_baseline"] = cb
+        if args.cpu_sample_steps == 1:
+            scale = np.linalg.norm(T.full(Qo[0]))
+            line["l2_err_vs_oracle"] = {
+                "fields": [float(np.linalg.norm(first[c].full().numpy() - T.full(Qo[c])) / scale)
+                           for c in range(3)],
+                "note": "first step from the initial state, relative to ||h||; bar 10 x tol"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

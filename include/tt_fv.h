@@ -1,0 +1,221 @@
+/*
+ * tt_fv.h -- C ABI of the GB300 tensor-train finite-volume shallow-water stage.
+ *
+ * Method: Danis, Truong, DeSantis, Petersen, Rasmussen, Alexandrov,
+ * "High-order Tensor-Train Finite Volume Method for Shallow Water Equations",
+ * arXiv 2408.03483.  Section / equation / algorithm numbers below refer to it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A 2-D TT ("matrix TT", Sec. 3.1, Eq. TT_def_2D) is a pair of cores:
+ *       X[i, j] = sum_{k < rank} a[k * n1 + i] * b[k * n2 + j],
+ *   i.e. a = G1 (n1 x rank, column-major, i fastest) and b = G2^T
+ *   (n2 x rank, column-major).  The first index is x, the second y.
+ * - Every pointer in a tt2 is DEVICE memory owned by the caller, sized for
+ *   `cap` columns (a: n1 * cap doubles, b: n2 * cap doubles).  The library
+ *   never allocates, frees or keeps caller memory beyond a call, except the
+ *   workspace handed to tt_fv_init, which the context uses until destroy.
+ * - `ws` / `ws_bytes`: caller-provided device workspace (>= the size the
+ *   matching *_workspace_size function returns; 256-byte aligned).
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *   stream-ordered; a call returns after its last launch and may read a few
+ *   integers back from the device (ranks, iteration counts) on that stream.
+ * - Errors are return codes only; nothing aborts or traps.  TT_ERR_ARG: bad
+ *   argument (no work done); TT_ERR_OOM: workspace too small; TT_ERR_CUDA: a
+ *   CUDA call failed; TT_ERR_NOCONV: an iteration hit its cap (Taylor
+ *   reciprocal, Jacobi SVD); the output is then the last iterate.
+ *   Reaching a rank cap truncates to the cap and is counted, not an error.
+ * - All arithmetic is IEEE FP64.
+ */
+#ifndef TT_FV_H
+#define TT_FV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_ARG = 1,
+  TT_ERR_OOM = 2,
+  TT_ERR_CUDA = 3,
+  TT_ERR_NOCONV = 4,
+  TT_ERR_TIMEOUT = 5,
+  TT_ERR_RANKCAP = 6
+} tt_status;
+
+typedef struct {
+  int32_t n1, n2;   /* mode sizes */
+  int32_t rank;     /* current rank (columns in use) */
+  int32_t cap;      /* allocated columns */
+  double* a;        /* n1 x cap, device */
+  double* b;        /* n2 x cap, device */
+} tt2;
+
+enum { TT_LINEAR = 0, TT_NONLINEAR = 1 };          /* Eq. linear-SWE / nonlinear-SWE */
+enum { TT_UP3 = 0, TT_UP5 = 1, TT_WENO5 = 2 };      /* Sec. 2.3 reconstructions */
+enum { TT_FP64 = 0, TT_TF32 = 1, TT_BF16 = 2 };     /* contraction precision */
+enum { TT_PIVOT_MAXVOL = 0, TT_PIVOT_LEARNED = 1 };
+
+/* Cross-interpolated functions (tt_cross `fn`). */
+enum {
+  TT_FN_ENTRY = 0,       /* F = inputs[0] itself (exact-recovery test)              */
+  TT_FN_WENO_S1 = 1,     /* WENO5 Step 1 (Sec. 2.3.1, Algorithm 2) of inputs[0]     */
+  TT_FN_WENO_S2 = 2,     /* WENO5 Step 2 at all Gauss points (Algorithm 3)          */
+  TT_FN_LLF_LAMBDA = 3   /* max(|hu-/h-| + sqrt(g h-), |hu+/h+| + sqrt(g h+)) (Sec. 4.2) */
+};
+
+typedef struct {
+  int32_t eqn;        /* TT_LINEAR | TT_NONLINEAR */
+  int32_t recon;      /* TT_UP3 | TT_UP5 | TT_WENO5 */
+  int32_t nx, ny;     /* cells; domain [0,lx] x [0,ly], doubly periodic */
+  double lx, ly;
+  double g, H, f;     /* gravity, mean depth (linear SWE), Coriolis parameter */
+  double dt;          /* time step */
+  double tol;         /* relative Frobenius truncation tolerance of every round */
+  int32_t rank_cap;   /* rank cap of every round */
+  int32_t precision;  /* TT_FP64 (only value accepted by this build) */
+  int32_t pivots;     /* TT_PIVOT_MAXVOL (only value accepted by this build) */
+  int32_t kick;       /* cross kick fibres per sweep (default 4 if <= 0) */
+  int32_t max_sweeps; /* cross sweep cap (default 10 if <= 0) */
+  int32_t max_iter;   /* Taylor reciprocal iteration cap (default 50 if <= 0) */
+  uint32_t seed;      /* seed of the cross kick indices */
+} tt_fv_params;
+
+typedef struct {
+  int32_t rank[3];            /* current ranks of the three fields */
+  int64_t rounds;             /* TT roundings performed */
+  int64_t syncs;              /* device->host reads of ranks / counters */
+  int64_t jacobi_sweeps;      /* sweeps of the small SVDs */
+  int64_t cross_calls, cross_sweeps;
+  int64_t taylor_iters;       /* Algorithm 1 loop iterations */
+  int64_t cap_hits;           /* rounds truncated by the rank cap */
+  int64_t qb_attempts, qb_uncertified;  /* range-finder attempts / residual above target */
+  double flops;               /* algorithmic FP64 flops issued */
+  double bytes;               /* algorithmic bytes moved by the core kernels */
+  uint32_t device_status;     /* latched device error bits (0 = none) */
+} tt_fv_stats;
+
+typedef struct tt_fv_ctx tt_fv_ctx;
+
+/* Kernel classes of the per-launch profile (tt_fv_kernel_profile). */
+enum {
+  TT_K_GEMM = 0,      /* FP64 split-K GEMM (range finder, factor products)     */
+  TT_K_FORM = 1,      /* full Hadamard face tensor formation                   */
+  TT_K_QR = 2,        /* Householder TSQR row blocks                           */
+  TT_K_QR_APPLY = 3,  /* application of the TSQR orthogonal factors            */
+  TT_K_JACOBI = 4,    /* one-sided Jacobi SVD of the small core                */
+  TT_K_MAXVOL = 5,    /* maximum-volume row selection                          */
+  TT_K_EVAL = 6,      /* cross fibre evaluation (WENO5, LLF speed)             */
+  TT_K_STENCIL = 7,   /* core stencils: reconstruction, quadrature, (T-1)/dx   */
+  TT_K_OTHER = 8,     /* copies, transposes, norms, small solves               */
+  TT_K_NCLASS = 9
+};
+
+typedef struct {
+  double ms;          /* summed device time of the launches (CUDA events)      */
+  double flops;       /* algorithmic FP64 flops of those launches              */
+  double bytes;       /* algorithmic DRAM bytes of those launches              */
+  int64_t launches;
+} tt_kernel_prof;
+
+/* ---------------------------------------------------------------- solver */
+
+/* Device workspace needed by tt_fv_init for these parameters (bytes). */
+size_t tt_fv_workspace_size(const tt_fv_params* p);
+
+/* Create a solver context: copies the initial fields q0 (h, hu, hv for the
+ * nonlinear SWE; eta, u, v for the linear SWE; cell averages in TT format,
+ * ranks <= rank_cap, n1 = nx, n2 = ny) into state held in `ws`.  The context
+ * keeps using `ws` (caller-owned) until tt_fv_destroy. */
+tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws_bytes,
+                     void* stream, tt_fv_ctx** out);
+
+/* nsteps full SSP-RK3 steps (Eq. tt-ssprk3 with Eq. tt-forward-euler). */
+tt_status tt_fv_step(tt_fv_ctx* ctx, int32_t nsteps);
+
+/* One SSP-RK3 stage: stage 0 sets u1 = F(u^n); stage 1 sets
+ * u2 = round(3/4 u^n + 1/4 F(u1)); stage 2 sets u^{n+1} = round(1/3 u^n + 2/3 F(u2))
+ * and makes it the new u^n.  Stages must be called in order 0, 1, 2. */
+tt_status tt_fv_stage(tt_fv_ctx* ctx, int32_t stage);
+
+/* Copy the current state (u^n after a full step, or the latest stage value)
+ * into caller cores (cap >= rank, n1/n2 matching); sets q_out[c].rank. */
+tt_status tt_fv_get(tt_fv_ctx* ctx, tt2 q_out[3]);
+
+/* Replace u^n by caller cores (checkpoint resume). */
+tt_status tt_fv_set(tt_fv_ctx* ctx, const tt2 q[3]);
+
+tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* out);
+void tt_fv_destroy(tt_fv_ctx* ctx);
+
+/* Enable (1) or disable (0) CUDA-event timing of every kernel launch of the
+ * context, accumulated per kernel class; costs two event records per launch. */
+tt_status tt_fv_profile(tt_fv_ctx* ctx, int32_t enable);
+/* Copy the accumulated per-class profile (TT_K_NCLASS entries) and, if
+ * reset != 0, clear it. */
+tt_status tt_fv_kernel_profile(tt_fv_ctx* ctx, tt_kernel_prof out[TT_K_NCLASS], int32_t reset);
+/* Kernels launched by this library in this process so far. */
+uint64_t tt_launch_count(void);
+
+/* ---------------------------------------------------------------- primitives */
+
+/* TT rounding (Sec. 3.2): y = round(x, tol) with rank <= rank_cap, the
+ * truncated SVD of X at relative Frobenius tolerance tol (keep the smallest k
+ * with sqrt(sum_{i>k} s_i^2) <= tol ||X||_F, then min(k, rank_cap), k >= 1).
+ * y->a / y->b must not alias x; y->cap >= rank_cap.  err_out (host, may be
+ * NULL) receives the discarded Frobenius norm. */
+size_t tt_round_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap);
+tt_status tt_round(const tt2* x, double tol, int32_t rank_cap, tt2* y, double* err_out,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* y = round(x o z, tol): the TT Hadamard product (Sec. 4.2, cores are
+ * row-wise Kronecker products of rank x.rank * z.rank) followed by rounding. */
+size_t tt_round_hadamard_workspace_size(int32_t n1, int32_t n2, int32_t rank_x, int32_t rank_z,
+                                        int32_t rank_cap);
+tt_status tt_round_hadamard(const tt2* x, const tt2* z, double tol, int32_t rank_cap, tt2* y,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* TT cross interpolation (Sec. 3.3): y ~ F where F is the entrywise function
+ * `fn` of the input TTs, by alternating maximum-volume sweeps seeded by the
+ * guess x0, kick fibres per sweep drawn from SplitMix64(seed), and a final
+ * round at (tol, rank_cap).  fparams (host):
+ *   TT_FN_ENTRY      : unused;
+ *   TT_FN_WENO_S1    : {eps, side (-1: right-face value, +1: left-face value),
+ *                       mode (0: stencil along the first index, 1: second)};
+ *   TT_FN_WENO_S2    : {eps, mode (1: output n1 x 3*n2, columns m*n2+j;
+ *                       0: output 3*n1 x n2, rows m*n1+i), nq (= 3)};
+ *   TT_FN_LLF_LAMBDA : {g}; inputs = {h-, hu-, h+, hu+} (hu = hv for y faces).
+ * The output shape is (y->n1, y->n2). */
+size_t tt_cross_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap,
+                               int32_t kick);
+tt_status tt_cross(int32_t fn, const tt2* inputs, int32_t ninputs, const tt2* x0,
+                   const double* fparams, double tol, int32_t rank_cap, int32_t kick,
+                   int32_t max_sweeps, uint32_t seed, tt2* y, int32_t* sweeps_out, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/* Taylor-series TT reciprocal, Algorithm 1: y ~ 1/x with x_avg = sum(x)/N,
+ * x~ = round(1 - x/x_avg), dy <- round(dy o x~), y <- round(y + dy) until
+ * ||dy||_F / sqrt(N) <= tol.  TT_ERR_NOCONV after max_iter iterations. */
+size_t tt_reciprocal_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap);
+tt_status tt_reciprocal(const tt2* x, double tol, int32_t rank_cap, int32_t max_iter, tt2* y,
+                        int32_t* iters_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Linear reconstruction on cores (Sec. 4.3.1) of one field for the faces
+ * normal to `direction` (0: x faces, 1: y faces), scheme TT_UP3 | TT_UP5.
+ * Outputs qm (state left of face: cell i-1's right-face value) and qp (cell
+ * i's left-face value), rank = x.rank, stacked over the Gauss points:
+ * x faces n1 x (nq n2), y faces (nq n1) x n2, quadrature index outermost. */
+tt_status tt_recon_linear(const tt2* x, int32_t direction, int32_t scheme, tt2* qm, tt2* qp,
+                          void* stream);
+
+/* Library version string. */
+const char* tt_fv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TT_FV_H */

@@ -14,8 +14,8 @@ et al.) with rank adaptation by "kick" fibres, written from that principle:
      by maxvol; evaluate the row fibres F(I u kick, :), take their leading
      right singular vectors, choose new columns J by maxvol;
   3. stop when the current skeleton predicts the next sweep's column fibres to
-     relative Frobenius error <= tol, when the column pivots are stationary
-     (the rank cap binds), or after max_sweeps sweeps;
+     relative Frobenius error <= tol, when the rank cap is reached with
+     stationary column pivots, or after max_sweeps sweeps;
   4. return the skeleton X = U_c U_c[I]^{-1} F(I, :), then TT-round it.
 
 Kick indices come from SplitMix64 (Steele, Lea & Flood, 2014) driven by a
@@ -55,23 +55,22 @@ def kick_indices(n, count, seed, sweep, exclude):
 
 
 def lu_pivot_rows(U):
-    """Row pivots of Gaussian elimination with partial pivoting on U (n x r):
-    at step k the row of largest |entry| in column k among the remaining rows
-    (ties: the smallest row index)."""
+    """Row pivots of Gaussian elimination with partial pivoting on U (n x r),
+    rows left in place: at step k the not-yet-chosen row with the largest
+    |W[i, k]| (ties: the smallest row index) becomes pivot k, and every other
+    unchosen row is eliminated against it."""
     W = np.array(U, dtype=float, copy=True)
     n, r = W.shape
-    perm = list(range(n))
+    free = np.ones(n, dtype=bool)
     piv = []
     for k in range(r):
-        col = np.abs(W[k:, k])
-        p = k + int(np.argmax(col))
-        if p != k:
-            W[[k, p], :] = W[[p, k], :]
-            perm[k], perm[p] = perm[p], perm[k]
-        piv.append(perm[k])
-        if W[k, k] != 0.0:
-            f = W[k + 1:, k] / W[k, k]
-            W[k + 1:, k:] -= np.outer(f, W[k, k:])
+        col = np.where(free, np.abs(W[:, k]), -1.0)
+        p = int(np.argmax(col))
+        piv.append(p)
+        free[p] = False
+        if W[p, k] != 0.0:
+            f = np.where(free, W[:, k] / W[p, k], 0.0)
+            W[:, k:] -= np.outer(f, W[p, k:])
     return piv
 
 
@@ -133,8 +132,8 @@ def cross2d(evalF, n1, n2, x0, tol, cap, kick=4, max_sweeps=10, seed=0,
         prev = (Uc, I, R[:len(I), :])
         Vr = _orth_left(R.T, tol, cap)
         Jn = maxvol(Vr)
-        if set(Jn) == set(J):
-            break  # stationary pivots: a further sweep reproduces this skeleton
+        if len(Jn) >= cap and set(Jn) == set(J):
+            break  # rank cap reached with stationary pivots: no further gain
         J = Jn
     Uc, I, RI = prev
     A = np.linalg.solve(Uc[I, :].T, Uc.T).T

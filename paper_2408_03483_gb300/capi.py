@@ -1,0 +1,124 @@
+"""ctypes binding of the C ABI declared in include/tt_fv.h.
+
+Argument marshalling only: every step of the TT finite-volume stage runs in
+libttfv.so.  PyTorch supplies device memory (cores, workspaces) and streams.
+There is no CPU fallback: importing this module without the built library, or
+calling it without a CUDA device, raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+TT_OK, TT_ERR_ARG, TT_ERR_OOM, TT_ERR_CUDA, TT_ERR_NOCONV, TT_ERR_TIMEOUT, TT_ERR_RANKCAP = range(7)
+TT_LINEAR, TT_NONLINEAR = 0, 1
+TT_UP3, TT_UP5, TT_WENO5 = 0, 1, 2
+TT_FP64, TT_TF32, TT_BF16 = 0, 1, 2
+TT_PIVOT_MAXVOL, TT_PIVOT_LEARNED = 0, 1
+TT_FN_ENTRY, TT_FN_WENO_S1, TT_FN_WENO_S2, TT_FN_LLF_LAMBDA = 0, 1, 2, 3
+
+STATUS_NAMES = {0: "TT_OK", 1: "TT_ERR_ARG", 2: "TT_ERR_OOM", 3: "TT_ERR_CUDA", 4: "TT_ERR_NOCONV",
+                5: "TT_ERR_TIMEOUT", 6: "TT_ERR_RANKCAP"}
+
+SCHEMES = {"up3": TT_UP3, "up5": TT_UP5, "weno5": TT_WENO5}
+EQNS = {"linear": TT_LINEAR, "nonlinear": TT_NONLINEAR}
+
+
+class TTError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} returned {STATUS_NAMES.get(code, code)}")
+        self.code = code
+
+
+class tt2(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int32), ("n2", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("cap", ctypes.c_int32), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p)]
+
+
+class tt_fv_params(ctypes.Structure):
+    _fields_ = [("eqn", ctypes.c_int32), ("recon", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("g", ctypes.c_double), ("H", ctypes.c_double), ("f", ctypes.c_double),
+                ("dt", ctypes.c_double), ("tol", ctypes.c_double), ("rank_cap", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("pivots", ctypes.c_int32), ("kick", ctypes.c_int32),
+                ("max_sweeps", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("seed", ctypes.c_uint32)]
+
+
+class tt_fv_stats(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32 * 3), ("rounds", ctypes.c_int64), ("syncs", ctypes.c_int64),
+                ("jacobi_sweeps", ctypes.c_int64), ("cross_calls", ctypes.c_int64),
+                ("cross_sweeps", ctypes.c_int64), ("taylor_iters", ctypes.c_int64),
+                ("cap_hits", ctypes.c_int64), ("qb_attempts", ctypes.c_int64),
+                ("qb_uncertified", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("device_status", ctypes.c_uint32)]
+
+
+TT_K_NAMES = ["gemm", "form_hadamard", "qr", "qr_apply", "jacobi_svd", "maxvol", "cross_eval", "stencil",
+              "other"]
+
+
+class tt_kernel_prof(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
+
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_i32 = ctypes.c_int32
+_d = ctypes.c_double
+
+# name -> (restype, argtypes); the list mirrors include/tt_fv.h
+SIGNATURES = {
+    "tt_fv_version": (ctypes.c_char_p, []),
+    "tt_fv_workspace_size": (_sz, [_P(tt_fv_params)]),
+    "tt_fv_init": (ctypes.c_int, [_P(tt_fv_params), _P(tt2), _vp, _sz, _vp, _P(_vp)]),
+    "tt_fv_step": (ctypes.c_int, [_vp, _i32]),
+    "tt_fv_stage": (ctypes.c_int, [_vp, _i32]),
+    "tt_fv_get": (ctypes.c_int, [_vp, _P(tt2)]),
+    "tt_fv_set": (ctypes.c_int, [_vp, _P(tt2)]),
+    "tt_fv_stats_get": (ctypes.c_int, [_vp, _P(tt_fv_stats)]),
+    "tt_fv_destroy": (None, [_vp]),
+    "tt_fv_profile": (ctypes.c_int, [_vp, _i32]),
+    "tt_fv_kernel_profile": (ctypes.c_int, [_vp, _P(tt_kernel_prof), _i32]),
+    "tt_launch_count": (ctypes.c_uint64, []),
+    "tt_round_workspace_size": (_sz, [_i32, _i32, _i32, _i32]),
+    "tt_round": (ctypes.c_int, [_P(tt2), _d, _i32, _P(tt2), _P(_d), _vp, _sz, _vp]),
+    "tt_round_hadamard_workspace_size": (_sz, [_i32, _i32, _i32, _i32, _i32]),
+    "tt_round_hadamard": (ctypes.c_int, [_P(tt2), _P(tt2), _d, _i32, _P(tt2), _vp, _sz, _vp]),
+    "tt_cross_workspace_size": (_sz, [_i32, _i32, _i32, _i32, _i32]),
+    "tt_cross": (ctypes.c_int, [_i32, _P(tt2), _i32, _P(tt2), _P(_d), _d, _i32, _i32, _i32, ctypes.c_uint32,
+                                _P(tt2), _P(_i32), _vp, _sz, _vp]),
+    "tt_reciprocal_workspace_size": (_sz, [_i32, _i32, _i32, _i32]),
+    "tt_reciprocal": (ctypes.c_int, [_P(tt2), _d, _i32, _i32, _P(tt2), _P(_i32), _vp, _sz, _vp]),
+    "tt_recon_linear": (ctypes.c_int, [_P(tt2), _i32, _i32, _P(tt2), _P(tt2), _vp]),
+}
+
+_lib = None
+
+
+def lib_path():
+    return _build.lib_path()
+
+
+def load(path=None):
+    """Load libttfv.so (built by paper_2408_03483_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    import torch  # noqa: F401  (loads the CUDA runtime the library shares)
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(name, code):
+    if code != TT_OK:
+        raise TTError(name, code)

@@ -1,0 +1,458 @@
+// TT cross interpolation of a 2-D tensor given entrywise (Sec. 3.3):
+// alternating maximum-volume sweeps on column and row fibres with kick
+// fibres for rank growth, the skeleton U_c U_c[I]^{-1} F(I, :), then a round.
+// The evaluated functions are the WENO5 Step-1 and Step-2 reconstructions
+// (Algorithms 2-3, Sec. 2.3) and the LLF wave speed (Sec. 4.2).
+#include <cmath>
+#include <set>
+#include <algorithm>
+
+#include "coeffs.cuh"
+#include "tt_ops.cuh"
+
+namespace ttfv {
+
+// ============================================================== evaluators
+struct DevTT {
+  const double* a;
+  const double* b;
+  int n1, n2, r;
+};
+struct EvalArgs {
+  int fn;
+  DevTT in[4];
+  double prm[4];
+  WenoConst wc;
+};
+
+__device__ __forceinline__ double entry(const DevTT& x, int i, int j) {
+  double s = 0.0;
+  for (int k = 0; k < x.r; ++k) s = fma(x.a[i + (size_t)k * x.n1], x.b[j + (size_t)k * x.n2], s);
+  return s;
+}
+
+// WENO5 value at the right face of the centre cell from v_{-2..2} (Sec. 2.3.1)
+__device__ double weno5_face(double vm2, double vm1, double v0, double vp1, double vp2, double eps) {
+  const double q0 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
+  const double q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
+  const double q2 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
+  const double e0 = v0 - 2.0 * vp1 + vp2, f0 = 3.0 * v0 - 4.0 * vp1 + vp2;
+  const double e1 = vm1 - 2.0 * v0 + vp1, f1 = vm1 - vp1;
+  const double e2 = vm2 - 2.0 * vm1 + v0, f2 = vm2 - 4.0 * vm1 + 3.0 * v0;
+  const double b0 = 13.0 / 12.0 * e0 * e0 + 0.25 * f0 * f0;
+  const double b1 = 13.0 / 12.0 * e1 * e1 + 0.25 * f1 * f1;
+  const double b2 = 13.0 / 12.0 * e2 * e2 + 0.25 * f2 * f2;
+  const double a0 = 0.3 / ((b0 + eps) * (b0 + eps));
+  const double a1 = 0.6 / ((b1 + eps) * (b1 + eps));
+  const double a2 = 0.1 / ((b2 + eps) * (b2 + eps));
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// WENO5 Step-2 point value at Gauss point m (0-based) from v_{-2..2}
+// (Sec. 2.3.2: nonlinear gamma weights; sigma split at the centre point).
+__device__ double weno5_quad(const double* v, int m, double eps, const WenoConst& w) {
+  double cand[3];
+  for (int r = 0; r < 3; ++r) {
+    double s = 0.0;
+    for (int l = 0; l < 3; ++l) s = fma(w.C3[m][r][l], v[2 - r + l], s);
+    cand[r] = s;
+  }
+  const double e0 = v[2] - 2.0 * v[3] + v[4], f0 = 3.0 * v[2] - 4.0 * v[3] + v[4];
+  const double e1 = v[1] - 2.0 * v[2] + v[3], f1 = v[1] - v[3];
+  const double e2 = v[0] - 2.0 * v[1] + v[2], f2 = v[0] - 4.0 * v[1] + 3.0 * v[2];
+  double beta[3];
+  beta[0] = 13.0 / 12.0 * e0 * e0 + 0.25 * f0 * f0;
+  beta[1] = 13.0 / 12.0 * e1 * e1 + 0.25 * f1 * f1;
+  beta[2] = 13.0 / 12.0 * e2 * e2 + 0.25 * f2 * f2;
+  if (m != 1) {
+    double num = 0.0, den = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      const double a = w.gam3[m][r] / ((beta[r] + eps) * (beta[r] + eps));
+      num = fma(a, cand[r], num);
+      den += a;
+    }
+    return num / den;
+  }
+  double np = 0.0, dp = 0.0, nm = 0.0, dm = 0.0;
+  for (int r = 0; r < 3; ++r) {
+    const double bb = (beta[r] + eps) * (beta[r] + eps);
+    const double ap = w.gp[r] / bb, am = w.gm[r] / bb;
+    np = fma(ap, cand[r], np);
+    dp += ap;
+    nm = fma(am, cand[r], nm);
+    dm += am;
+  }
+  return w.sp * (np / dp) - w.sm * (nm / dm);
+}
+
+__device__ double eval_fn(const EvalArgs& e, int i, int j) {
+  switch (e.fn) {
+    case TT_FN_ENTRY:
+      return entry(e.in[0], i, j);
+    case TT_FN_WENO_S1: {
+      const DevTT& x = e.in[0];
+      const int mode = (int)e.prm[2];
+      double v[5];
+      for (int s = -2; s <= 2; ++s) {
+        if (mode == 0) {
+          int ii = (i + s) % x.n1;
+          if (ii < 0) ii += x.n1;
+          v[s + 2] = entry(x, ii, j);
+        } else {
+          int jj = (j + s) % x.n2;
+          if (jj < 0) jj += x.n2;
+          v[s + 2] = entry(x, i, jj);
+        }
+      }
+      if (e.prm[1] < 0.0) return weno5_face(v[0], v[1], v[2], v[3], v[4], e.prm[0]);
+      return weno5_face(v[4], v[3], v[2], v[1], v[0], e.prm[0]);
+    }
+    case TT_FN_WENO_S2: {
+      const DevTT& x = e.in[0];
+      const int mode = (int)e.prm[1];
+      double v[5];
+      int m;
+      if (mode == 1) {  // columns (m, j)
+        m = j / x.n2;
+        const int jj0 = j % x.n2;
+        for (int s = -2; s <= 2; ++s) {
+          int jj = (jj0 + s) % x.n2;
+          if (jj < 0) jj += x.n2;
+          v[s + 2] = entry(x, i, jj);
+        }
+      } else {  // rows (m, i)
+        m = i / x.n1;
+        const int ii0 = i % x.n1;
+        for (int s = -2; s <= 2; ++s) {
+          int ii = (ii0 + s) % x.n1;
+          if (ii < 0) ii += x.n1;
+          v[s + 2] = entry(x, ii, j);
+        }
+      }
+      return weno5_quad(v, m, e.prm[0], e.wc);
+    }
+    case TT_FN_LLF_LAMBDA: {
+      const double g = e.prm[0];
+      const double hm = entry(e.in[0], i, j), qm = entry(e.in[1], i, j);
+      const double hp = entry(e.in[2], i, j), qp = entry(e.in[3], i, j);
+      const double lm = fabs(qm / hm) + sqrt(g * hm);
+      const double lp = fabs(qp / hp) + sqrt(g * hp);
+      return fmax(lm, lp);
+    }
+  }
+  return 0.0;
+}
+
+// C[i + b*n1] = F(i, J[b]) for all rows i
+__global__ void k_eval_cols(EvalArgs e, int n1, const int* __restrict__ J, int nj, double* __restrict__ C) {
+  const long total = (long)n1 * nj;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int i = int(t % n1), b = int(t / n1);
+    C[t] = eval_fn(e, i, J[b]);
+  }
+}
+// RT[j + a*n2] = F(I[a], j) for all columns j
+__global__ void k_eval_rows(EvalArgs e, int n2, const int* __restrict__ I, int ni, double* __restrict__ RT) {
+  const long total = (long)n2 * ni;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int j = int(t % n2), a = int(t / n2);
+    RT[t] = eval_fn(e, I[a], j);
+  }
+}
+
+// ============================================================== small kernels
+// Wk = US[:, :k] with column j divided by sig[j] (e_j where sig[j] == 0)
+__global__ void k_unscale(const double* US, const double* sig, int p, int k, double* W) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p * k; t += gridDim.x * blockDim.x) {
+    const int i = t % p, j = t / p;
+    W[t] = sig[j] > 0.0 ? US[t] / sig[j] : (i == j ? 1.0 : 0.0);
+  }
+}
+// G[a + b*k] = U[I[a] + b*n] (rows I of U, k x c)
+__global__ void k_gather_rows(const double* U, long ldu, const int* I, int k, int c, double* G) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k * c; t += gridDim.x * blockDim.x) {
+    const int a = t % k, b = t / k;
+    G[t] = U[I[a] + (size_t)b * ldu];
+  }
+}
+// X = P^{-1} G: Gaussian elimination with partial pivoting on [P | G] in
+// shared memory (k <= 112, c <= 120), one CTA.
+__global__ void __launch_bounds__(1024) k_small_solve(const double* P, int k, const double* G, int c, double* X) {
+  extern __shared__ double sm[];
+  double* A = sm;  // k x (k + c), column-major with ld k
+  const int w = k + c;
+  __shared__ int piv;
+  for (int t = threadIdx.x; t < k * w; t += blockDim.x) {
+    const int i = t % k, j = t / k;
+    A[t] = j < k ? P[i + (size_t)j * k] : G[i + (size_t)(j - k) * k];
+  }
+  __syncthreads();
+  for (int col = 0; col < k; ++col) {
+    if (threadIdx.x == 0) {
+      int best = col;
+      double bv = fabs(A[col + (size_t)col * k]);
+      for (int i = col + 1; i < k; ++i) {
+        const double v = fabs(A[i + (size_t)col * k]);
+        if (v > bv) {
+          bv = v;
+          best = i;
+        }
+      }
+      piv = best;
+    }
+    __syncthreads();
+    const int pr = piv;
+    if (pr != col)
+      for (int j = threadIdx.x; j < w; j += blockDim.x) {
+        const double x = A[col + (size_t)j * k];
+        A[col + (size_t)j * k] = A[pr + (size_t)j * k];
+        A[pr + (size_t)j * k] = x;
+      }
+    __syncthreads();
+    const double d = A[col + (size_t)col * k];
+    for (long t = threadIdx.x; t < (long)(k - col - 1) * (w - col - 1); t += blockDim.x) {
+      const int i = col + 1 + int(t % (k - col - 1)), j = col + 1 + int(t / (k - col - 1));
+      const double f = d != 0.0 ? A[i + (size_t)col * k] / d : 0.0;
+      A[i + (size_t)j * k] = fma(-f, A[col + (size_t)j * k], A[i + (size_t)j * k]);
+    }
+    __syncthreads();
+  }
+  // back substitution, one thread per right-hand side column
+  for (int j = threadIdx.x; j < c; j += blockDim.x) {
+    double* x = A + (size_t)(k + j) * k;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = x[i];
+      for (int l = i + 1; l < k; ++l) s = fma(-A[i + (size_t)l * k], x[l], s);
+      const double d = A[i + (size_t)i * k];
+      x[i] = d != 0.0 ? s / d : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * c; t += blockDim.x) X[t] = A[(size_t)k * k + t];
+}
+
+static void small_solve(Exec& ex, const double* P, int k, const double* G, int c, double* X) {
+  if (ex.dry) return;
+  const size_t smem = (size_t)k * (k + c) * 8;
+  TT_REQUIRE(smem <= 220 * 1024, TT_ERR_ARG);
+  TT_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TT_KERNEL(ex, K_OTHER, 2.0 / 3.0 * k * (double)k * k + 2.0 * k * (double)k * c, 8.0 * k * (double)(k + 2 * c),
+            k_small_solve<<<1, 1024, smem, ex.s>>>(P, k, G, c, X));
+}
+
+// ============================================================== host helpers
+static unsigned long long splitmix64_h(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// `count` distinct indices in [0, n) outside `exclude`, drawn in order from
+// splitmix64(seed * 2^32 + sweep * 2^16 + t), t = 0, 1, ...
+static std::vector<int> kick_indices(int n, int count, unsigned seed, int sweep, const std::vector<int>& exclude) {
+  std::vector<int> out;
+  std::set<int> ex(exclude.begin(), exclude.end());
+  long long t = 0;
+  const long long limit = 64LL * (count + 1) + n;
+  while ((int)out.size() < count && t < limit) {
+    const unsigned long long x = ((unsigned long long)seed << 32) + ((unsigned long long)(sweep & 0xFFFF) << 16) +
+                                 (unsigned long long)t;
+    const int v = int(splitmix64_h(x) % (unsigned long long)n);
+    ++t;
+    if (ex.count(v)) continue;
+    ex.insert(v);
+    out.push_back(v);
+  }
+  return out;
+}
+
+static EvalArgs make_args(const CrossFn& f) {
+  EvalArgs e{};
+  e.fn = f.fn;
+  for (int q = 0; q < f.nin && q < 4; ++q) e.in[q] = DevTT{f.in[q].a, f.in[q].b, f.in[q].n1, f.in[q].n2, f.in[q].r};
+  for (int q = 0; q < 4; ++q) e.prm[q] = f.prm[q];
+  e.wc = weno_const();
+  return e;
+}
+
+static int eval_cost(const CrossFn& f) {
+  int r = 0;
+  for (int q = 0; q < f.nin; ++q) r += f.in[q].r;
+  return (f.fn == TT_FN_WENO_S1 || f.fn == TT_FN_WENO_S2) ? 5 * r : r;
+}
+
+// Leading left singular vectors of C (m x c) truncated at (tol, cap) into U
+// (m x k, ld m); returns k.
+static int orth_left(Exec& ex, const double* C, int m, int c, double tol, int cap, double* U) {
+  Scope sc(*ex.ar);
+  QRTree t;
+  tsqr(ex, C, m, c, m, t);
+  double* US = ex.ar->get<double>((size_t)c * c);
+  double* V = ex.ar->get<double>((size_t)c * c);
+  double* sig = ex.ar->get<double>(c);
+  int* kd = ex.ar->get<int>(4);
+  double* tail = ex.ar->get<double>(2);
+  jacobi_svd(ex, t.R, c, tol, cap, US, V, sig, kd, tail);
+  int k = fetch_int(ex, kd);
+  if (ex.dry) k = std::min(cap, c);
+  k = std::min(k, m);
+  double* W = ex.ar->get<double>((size_t)c * k);
+  if (!ex.dry)
+    TT_KERNEL(ex, K_OTHER, (double)c * k, 16.0 * c * k, k_unscale<<<ceil_div((long)c * k, 256), 256, 0, ex.s>>>(US, sig, c, k, W));
+  tsqr_apply(ex, t, W, k, c, U, m);
+  return k;
+}
+
+static std::vector<int> fetch_idx(Exec& ex, const int* d, int n) {
+  std::vector<int> out(n);
+  if (ex.dry) {
+    for (int i = 0; i < n; ++i) out[i] = i;
+    return out;
+  }
+  TT_CUDA(cudaMemcpyAsync(out.data(), d, sizeof(int) * n, cudaMemcpyDeviceToHost, ex.s));
+  TT_CUDA(cudaStreamSynchronize(ex.s));
+  ex.syncs++;
+  return out;
+}
+
+static void upload_idx(Exec& ex, int* d, const std::vector<int>& h) {
+  if (ex.dry || h.empty()) return;
+  // pageable source: the copy is staged before the call returns
+  TT_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, ex.s));
+  TT_CUDA(cudaStreamSynchronize(ex.s));
+}
+
+// ============================================================== cross
+int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, int cap, int kick, int max_sweeps,
+          unsigned seed, TT& y) {
+  TT_REQUIRE(cap >= 1 && cap + kick <= 112 && x0.r >= 1 && x0.r <= 112, TT_ERR_ARG);
+  TT_REQUIRE(x0.n2 == n2, TT_ERR_ARG);
+  ex.cross_calls++;
+  Scope sc(*ex.ar);
+  const EvalArgs ea = make_args(f);
+  const int cost = eval_cost(f);
+  const int cmax = cap + kick;
+  double* C = ex.ar->get<double>((size_t)n1 * cmax);
+  double* RT = ex.ar->get<double>((size_t)n2 * cmax);
+  double* Uc = ex.ar->get<double>((size_t)n1 * cmax);
+  double* Uc_prev = ex.ar->get<double>((size_t)n1 * cmax);
+  double* RT_prev = ex.ar->get<double>((size_t)n2 * cmax);
+  double* Vr = ex.ar->get<double>((size_t)n2 * cmax);
+  double* G = ex.ar->get<double>((size_t)cmax * cmax);
+  double* P = ex.ar->get<double>((size_t)cmax * cmax);
+  double* X = ex.ar->get<double>((size_t)cmax * cmax);
+  double* D = ex.ar->get<double>((size_t)n1 * cmax);
+  double* nrm = ex.ar->get<double>(4);
+  int* dJ = ex.ar->get<int>(cmax);
+  int* dI = ex.ar->get<int>(cmax);
+  int* dIprev = ex.ar->get<int>(cmax);
+
+  // 1. column pivots from the maxvol rows of an orthonormal basis of x0's second core
+  std::vector<int> J;
+  const int r0 = std::max(1, std::min({x0.r, cap, n1, n2}));
+  {
+    Scope s2(*ex.ar);
+    QRTree tb;
+    tsqr(ex, x0.b, n2, x0.r, n2, tb);
+    double* Iden = ex.ar->get<double>((size_t)x0.r * x0.r);
+    double* Qb = ex.ar->get<double>((size_t)n2 * x0.r);
+    set_identity(ex, Iden, x0.r);
+    tsqr_apply(ex, tb, Iden, x0.r, x0.r, Qb, n2);
+    if (n2 > r0) {
+      maxvol(ex, Qb, n2, r0, 1e-2, 200, dJ);
+      J = fetch_idx(ex, dJ, r0);
+    } else {
+      for (int j = 0; j < n2; ++j) J.push_back(j);
+    }
+  }
+  std::vector<int> I, Iprev;
+  int kprev = 0;
+  bool have_prev = false;
+  int sweeps = 0;
+  for (int s = 0; s < max_sweeps; ++s) {
+    sweeps = s + 1;
+    ex.cross_sweeps++;
+    std::vector<int> Jx = J;
+    {
+      std::vector<int> kk = kick_indices(n2, std::min(kick, n2 - (int)J.size()), seed, 2 * s, J);
+      Jx.insert(Jx.end(), kk.begin(), kk.end());
+    }
+    const int cj = (int)Jx.size();
+    upload_idx(ex, dJ, Jx);
+    if (!ex.dry)
+      TT_KERNEL(ex, K_EVAL, 2.0 * n1 * (double)cj * cost, 8.0 * n1 * (double)cj,
+                k_eval_cols<<<std::max(1, std::min(ceil_div((long)n1 * cj, 256), 2368)), 256, 0, ex.s>>>(ea, n1, dJ,
+                                                                                                      cj, C));
+    if (have_prev) {
+      // prediction of the previous skeleton on the new column fibres:
+      // Uc_prev (Uc_prev[I])^{-1} F(I, Jx), with F(I, Jx) from the stored rows
+      Scope s3(*ex.ar);
+      double* Gp = ex.ar->get<double>((size_t)kprev * cj);
+      // F(I, Jx)[a, b] = RT_prev[Jx[b] + a n2]  -> gather rows Jx of RT_prev (cj x kprev), then transpose
+      double* Gt = ex.ar->get<double>((size_t)cj * kprev);
+      if (!ex.dry)
+        TT_KERNEL(ex, K_OTHER, 0, 16.0 * cj * kprev,
+                  k_gather_rows<<<ceil_div((long)cj * kprev, 256), 256, 0, ex.s>>>(RT_prev, n2, dJ, cj, kprev, Gt));
+      transpose(ex, Gt, cj, kprev, cj, Gp, kprev);
+      if (!ex.dry)
+        TT_KERNEL(ex, K_OTHER, 0, 16.0 * kprev * kprev,
+                  k_gather_rows<<<ceil_div((long)kprev * kprev, 256), 256, 0, ex.s>>>(Uc_prev, n1, dIprev, kprev,
+                                                                                        kprev, P));
+      small_solve(ex, P, kprev, Gp, cj, X);
+      scaled_copy(ex, D, C, (long)n1 * cj, 1.0);
+      gemm(ex, n1, cj, kprev, -1.0, Uc_prev, 1, n1, X, 1, kprev, 1.0, D, n1);
+      sumsq(ex, D, n1, cj, n1, nrm);
+      sumsq(ex, C, n1, cj, n1, nrm + 1);
+      double v[2];
+      fetch_doubles(ex, nrm, 2, v);
+      const double err = v[1] > 0.0 ? std::sqrt(v[0] / v[1]) : 0.0;
+      if (err <= tol) break;
+    }
+    const int kc = orth_left(ex, C, n1, cj, tol, cap, Uc);
+    maxvol(ex, Uc, n1, kc, 1e-2, 200, dI);
+    I = fetch_idx(ex, dI, kc);
+    std::vector<int> Ix = I;
+    {
+      std::vector<int> kk = kick_indices(n1, std::min(kick, n1 - (int)I.size()), seed, 2 * s + 1, I);
+      Ix.insert(Ix.end(), kk.begin(), kk.end());
+    }
+    const int ri = (int)Ix.size();
+    upload_idx(ex, dI, Ix);
+    if (!ex.dry)
+      TT_KERNEL(ex, K_EVAL, 2.0 * n2 * (double)ri * cost, 8.0 * n2 * (double)ri,
+                k_eval_rows<<<std::max(1, std::min(ceil_div((long)n2 * ri, 256), 2368)), 256, 0, ex.s>>>(ea, n2, dI,
+                                                                                                      ri, RT));
+    // prev = (Uc, I, R[:|I|, :])
+    scaled_copy(ex, Uc_prev, Uc, (long)n1 * kc, 1.0);
+    scaled_copy(ex, RT_prev, RT, (long)n2 * kc, 1.0);
+    upload_idx(ex, dIprev, I);
+    kprev = kc;
+    Iprev = I;
+    have_prev = true;
+    const int kr = orth_left(ex, RT, n2, ri, tol, cap, Vr);
+    maxvol(ex, Vr, n2, kr, 1e-2, 200, dJ);
+    std::vector<int> Jn = fetch_idx(ex, dJ, kr);
+    // rank cap reached with stationary pivots: a further sweep gains nothing
+    if (kr >= cap && std::set<int>(Jn.begin(), Jn.end()) == std::set<int>(J.begin(), J.end())) break;
+    J = Jn;
+  }
+  // skeleton: A = Uc_prev (Uc_prev[I])^{-1}, B = F(I, :)^T = RT_prev[:, :k]
+  {
+    Scope s4(*ex.ar);
+    const int k = kprev;
+    double* Pinv = ex.ar->get<double>((size_t)k * k);
+    double* Iden = ex.ar->get<double>((size_t)k * k);
+    double* A = ex.ar->get<double>((size_t)n1 * k);
+    if (!ex.dry)
+      TT_KERNEL(ex, K_OTHER, 0, 16.0 * k * k,
+                k_gather_rows<<<ceil_div((long)k * k, 256), 256, 0, ex.s>>>(Uc_prev, n1, dIprev, k, k, P));
+    set_identity(ex, Iden, k);
+    small_solve(ex, P, k, Iden, k, Pinv);
+    gemm(ex, n1, k, k, 1.0, Uc_prev, 1, n1, Pinv, 1, k, 0.0, A, n1);
+    round_cores(ex, A, RT_prev, n1, n2, k, tol, cap, y);
+  }
+  return sweeps;
+}
+
+}  // namespace ttfv

@@ -1,0 +1,868 @@
+// The TT finite-volume SSP-RK3 stage (Sec. 4) and the C ABI (include/tt_fv.h).
+//
+// Stage composition (Sec. 4.1-4.4):
+//  * reconstruction: Upwind3/Upwind5 by stencils on one core at a time
+//    (Sec. 4.3.1); WENO5 by two crosses per side (Algorithms 2 and 3), Step-2
+//    results stored N x (Nq N) for x faces and (Nq N) x N for y faces with the
+//    quadrature index outermost;
+//  * LLF flux in TT (Eq. LLF-TT): linear SWE by TT sums with lambda =
+//    sqrt(gH), no rounding; nonlinear SWE with 1/h by Algorithm 1, every
+//    Hadamard product and sum rounded, lambda by cross;
+//  * face quadrature, (T - 1)/dx on the core normal to the face, source term;
+//  * F(u) = round(u + dt L(u)) and the SSP-RK3 combinations of Eq. tt-ssprk3.
+// Face convention: face row i of an x-face TT is the face x_{i-1/2}; Qm holds
+// cell i-1's right-face value, Qp cell i's left-face value.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <algorithm>
+
+#include "coeffs.cuh"
+#include "tt_ops.cuh"
+
+namespace ttfv {
+
+// ============================================================== helpers
+static TT alloc_tt(Arena& ar, int n1, int n2, int cap) {
+  TT t;
+  t.n1 = n1;
+  t.n2 = n2;
+  t.cap = cap;
+  t.r = 0;
+  t.a = ar.get<double>((size_t)n1 * cap);
+  t.b = ar.get<double>((size_t)n2 * cap);
+  return t;
+}
+
+static void copy_tt(Exec& ex, const TT& src, TT& dst) {
+  TT_REQUIRE(src.n1 == dst.n1 && src.n2 == dst.n2 && src.r <= dst.cap, TT_ERR_ARG);
+  scaled_copy(ex, dst.a, src.a, (long)src.n1 * src.r, 1.0);
+  scaled_copy(ex, dst.b, src.b, (long)src.n2 * src.r, 1.0);
+  dst.r = src.r;
+}
+
+static TT const_tt(Exec& ex, int n1, int n2, double c) {
+  TT t = alloc_tt(*ex.ar, n1, n2, 1);
+  fill(ex, t.a, n1, c);
+  fill(ex, t.b, n2, 1.0);
+  t.r = 1;
+  return t;
+}
+
+// ============================================================== Algorithm 1
+int reciprocal(Exec& ex, const TT& x, double tol, int cap, int max_iter, TT& y, bool* noconv) {
+  Scope sc(*ex.ar);
+  const int n1 = x.n1, n2 = x.n2;
+  const double N = (double)n1 * n2;
+  double* sn = ex.ar->get<double>(2);
+  tt_sum_norm(ex, x, sn);
+  double v[2];
+  fetch_doubles(ex, sn, 2, v);
+  const double x_avg = ex.dry ? 1.0 : v[0] / N;
+  TT one = const_tt(ex, n1, n2, 1.0);
+  TT xt = alloc_tt(*ex.ar, n1, n2, cap);
+  round_sum(ex, {Term{1.0, one}, Term{-1.0 / x_avg, x}}, tol, cap, xt);
+  TT dy = alloc_tt(*ex.ar, n1, n2, cap);
+  copy_tt(ex, one, dy);
+  TT_REQUIRE(y.cap >= cap && y.n1 == n1 && y.n2 == n2, TT_ERR_ARG);
+  copy_tt(ex, one, y);
+  double err = 1.0;
+  int it = 0;
+  while (err > tol && it < max_iter) {
+    round_hadamard(ex, dy, xt, tol, cap, dy);
+    round_sum(ex, {Term{1.0, y}, Term{1.0, dy}}, tol, cap, y);
+    tt_sum_norm(ex, dy, sn);
+    fetch_doubles(ex, sn, 2, v);
+    err = ex.dry ? 0.0 : v[1] / std::sqrt(N);
+    ++it;
+  }
+  ex.taylor_iters += it;
+  scaled_copy(ex, y.a, y.a, (long)n1 * y.r, 1.0 / x_avg);
+  if (noconv) *noconv = (err > tol);
+  return it;
+}
+
+// ============================================================== linear recon
+static void add_taps(StencilOut& o, const double* coef, int ntap, int shift0, int base) {
+  for (int t = 0; t < ntap; ++t) {
+    if (coef[t] == 0.0) continue;
+    TT_REQUIRE(o.ntaps < kMaxTaps, TT_ERR_ARG);
+    o.shift[o.ntaps] = shift0 + t;
+    o.base[o.ntaps] = base;
+    o.coef[o.ntaps] = coef[t];
+    o.ntaps++;
+  }
+}
+
+// Step 1 on the core normal to the faces (right-face stencil shifted by one
+// cell for Qm, left-face stencil for Qp), Step 2 on the other core stacked
+// over the Gauss points (Sec. 4.3.1).
+void recon_linear(Exec& ex, const TT& x, int direction, int scheme, TT& qm, TT& qp) {
+  const ReconCoeffs& R = recon_coeffs();
+  const int nq = scheme == TT_UP3 ? 2 : 3;
+  const double* right = scheme == TT_UP3 ? R.up3_minus : R.up5_minus;
+  const double* left = scheme == TT_UP3 ? R.up3_plus : R.up5_plus;
+  const double* nrm_core = direction == 0 ? x.a : x.b;
+  const double* tan_core = direction == 0 ? x.b : x.a;
+  const int nn = direction == 0 ? x.n1 : x.n2;  // normal mode size
+  const int nt = direction == 0 ? x.n2 : x.n1;  // tangential mode size
+  double* m_nrm = direction == 0 ? qm.a : qm.b;
+  double* p_nrm = direction == 0 ? qp.a : qp.b;
+  double* stack = direction == 0 ? qm.b : qm.a;
+  StencilSet s1;
+  s1.nout = 2;
+  s1.out[0].dst = m_nrm;
+  s1.out[0].ld = nn;
+  add_taps(s1.out[0], right, 5, -2 - 1, 0);  // Qm[i] = right-face value of cell i-1
+  s1.out[1].dst = p_nrm;
+  s1.out[1].ld = nn;
+  add_taps(s1.out[1], left, 5, -2, 0);
+  stencil(ex, s1, nrm_core, nn, nn, x.r);
+  StencilSet s2;
+  s2.nout = nq;
+  for (int m = 0; m < nq; ++m) {
+    s2.out[m].dst = stack;
+    s2.out[m].ld = (long)nq * nt;
+    s2.out[m].row0 = m * nt;
+    if (nq == 2)
+      add_taps(s2.out[m], R.lin2[m], 3, -1, 0);
+    else
+      add_taps(s2.out[m], R.lin3[m], 5, -2, 0);
+  }
+  stencil(ex, s2, tan_core, nt, nt, x.r);
+  // Qp shares the stacked core of Qm
+  if (direction == 0)
+    qp.b = qm.b;
+  else
+    qp.a = qm.a;
+  qm.r = qp.r = x.r;
+}
+
+// ============================================================== solver context
+struct Solver {
+  tt_fv_params p{};
+  cudaStream_t s = nullptr;
+  Arena ar;
+  Exec ex;
+  TT Qn[3], Qs[3];
+  int step_count = 0;
+  int next_stage = 0;
+  int nq = 2;
+  int h_int[16];
+  double h_dbl[16];
+  Prof prof;
+  ~Solver() {
+    for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
+    for (const Prof::Rec& r : prof.pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+};
+
+static int nq_of(int recon) { return recon == TT_UP3 ? 2 : 3; }
+
+// faces of one field for direction d (0: x, 1: y)
+static void face_tts(Solver& S, Exec& ex, const TT& q, int d, int fieldc, unsigned seed, TT& qm, TT& qp) {
+  const tt_fv_params& p = S.p;
+  const int n1 = q.n1, n2 = q.n2, nq = S.nq, cap = p.rank_cap;
+  const int f1 = d == 0 ? n1 : nq * n1, f2 = d == 0 ? nq * n2 : n2;
+  const double dx = p.lx / p.nx, dy = p.ly / p.ny;
+  if (p.recon != TT_WENO5) {
+    qm.n1 = qp.n1 = f1;
+    qm.n2 = qp.n2 = f2;
+    qm.cap = qp.cap = q.r;
+    if (d == 0) {
+      qm.a = ex.ar->get<double>((size_t)n1 * q.r);
+      qp.a = ex.ar->get<double>((size_t)n1 * q.r);
+      qm.b = ex.ar->get<double>((size_t)f2 * q.r);
+    } else {
+      qm.b = ex.ar->get<double>((size_t)n2 * q.r);
+      qp.b = ex.ar->get<double>((size_t)n2 * q.r);
+      qm.a = ex.ar->get<double>((size_t)f1 * q.r);
+    }
+    recon_linear(ex, q, d, p.recon, qm, qp);
+    return;
+  }
+  const double e1 = d == 0 ? dx * dx : dy * dy, e2 = d == 0 ? dy * dy : dx * dx;
+  const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
+  const unsigned seed_base = seed + 64u * d + 8u * fieldc;
+  for (int k = 0; k < 2; ++k) {
+    Scope sc(*ex.ar);
+    CrossFn f1n;
+    f1n.fn = TT_FN_WENO_S1;
+    f1n.in = &q;
+    f1n.nin = 1;
+    f1n.prm[0] = e1;
+    f1n.prm[1] = k == 0 ? -1.0 : 1.0;
+    f1n.prm[2] = d;
+    TT vt = alloc_tt(*ex.ar, n1, n2, cap);
+    cross(ex, f1n, n1, n2, q, p.tol, cap, kick, sweeps, seed_base + 4u * k, vt);
+    // initial guess of Step 2: the Step-1 result repeated over the Gauss points
+    TT x0 = d == 0 ? alloc_tt(*ex.ar, n1, 3 * n2, vt.r) : alloc_tt(*ex.ar, 3 * n1, n2, vt.r);
+    x0.r = vt.r;
+    for (int c = 0; c < vt.r; ++c) {
+      if (d == 0) {
+        scaled_copy(ex, x0.a + (size_t)c * n1, vt.a + (size_t)c * n1, n1, 1.0);
+        for (int m = 0; m < 3; ++m)
+          scaled_copy(ex, x0.b + (size_t)c * 3 * n2 + m * n2, vt.b + (size_t)c * n2, n2, 1.0);
+      } else {
+        scaled_copy(ex, x0.b + (size_t)c * n2, vt.b + (size_t)c * n2, n2, 1.0);
+        for (int m = 0; m < 3; ++m)
+          scaled_copy(ex, x0.a + (size_t)c * 3 * n1 + m * n1, vt.a + (size_t)c * n1, n1, 1.0);
+      }
+    }
+    CrossFn f2n;
+    f2n.fn = TT_FN_WENO_S2;
+    f2n.in = &vt;
+    f2n.nin = 1;
+    f2n.prm[0] = e2;
+    f2n.prm[1] = d == 0 ? 1.0 : 0.0;
+    f2n.prm[2] = 3;
+    TT tmp = alloc_tt(*ex.ar, f1, f2, cap);
+    cross(ex, f2n, f1, f2, x0, p.tol, cap, kick, sweeps, seed_base + 4u * k + 1u, tmp);
+    // qm / qp storage is allocated by the caller, outside this scope
+    TT& dst = k == 0 ? qm : qp;
+    if (k == 0) {
+      // Qm: cell i-1's right-face value -> shift the normal core by one
+      StencilSet st;
+      st.nout = 1;
+      double one = 1.0;
+      if (d == 0) {
+        st.out[0].dst = dst.a;
+        st.out[0].ld = f1;
+        add_taps(st.out[0], &one, 1, -1, 0);
+        stencil(ex, st, tmp.a, f1, f1, tmp.r);
+        scaled_copy(ex, dst.b, tmp.b, (long)f2 * tmp.r, 1.0);
+      } else {
+        st.out[0].dst = dst.b;
+        st.out[0].ld = f2;
+        add_taps(st.out[0], &one, 1, -1, 0);
+        stencil(ex, st, tmp.b, f2, f2, tmp.r);
+        scaled_copy(ex, dst.a, tmp.a, (long)f1 * tmp.r, 1.0);
+      }
+      dst.r = tmp.r;
+    } else {
+      copy_tt(ex, tmp, dst);
+    }
+  }
+}
+
+// LLF flux of the linear SWE (TT sums only)
+static void flux_linear(Solver& S, const TT qm[3], const TT qp[3], int d, std::vector<Term> out[3]) {
+  const double g = S.p.g, H = S.p.H, lam = std::sqrt(g * H);
+  const int k = d == 0 ? 1 : 2;
+  for (int c = 0; c < 3; ++c) {
+    out[c].clear();
+    if (c == 0) {
+      out[c].push_back(Term{0.5 * H, qm[k]});
+      out[c].push_back(Term{0.5 * H, qp[k]});
+    } else if (c == k) {
+      out[c].push_back(Term{0.5 * g, qm[0]});
+      out[c].push_back(Term{0.5 * g, qp[0]});
+    }
+    out[c].push_back(Term{-0.5 * lam, qp[c]});
+    out[c].push_back(Term{0.5 * lam, qm[c]});
+  }
+}
+
+// LLF flux of the nonlinear SWE with the Taylor reciprocal; results rounded
+static void flux_nonlinear(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int d, unsigned seed, TT Fh[3]) {
+  const tt_fv_params& p = S.p;
+  const double tol = p.tol, g = p.g;
+  const int cap = p.rank_cap, mi = p.max_iter > 0 ? p.max_iter : 50;
+  const int n1 = qm[0].n1, n2 = qm[0].n2;
+  const int k = d == 0 ? 1 : 2;
+  TT F[2][3];
+  for (int side = 0; side < 2; ++side) {
+    const TT* Q = side == 0 ? qm : qp;
+    for (int c = 1; c < 3; ++c) F[side][c] = alloc_tt(*ex.ar, n1, n2, cap);
+    Scope sc(*ex.ar);
+    TT rh = alloc_tt(*ex.ar, n1, n2, cap);
+    bool nc = false;
+    reciprocal(ex, Q[0], tol, cap, mi, rh, &nc);
+    TT_REQUIRE(!nc, TT_ERR_NOCONV);
+    TT u = alloc_tt(*ex.ar, n1, n2, cap), v = alloc_tt(*ex.ar, n1, n2, cap), hh = alloc_tt(*ex.ar, n1, n2, cap);
+    TT t1 = alloc_tt(*ex.ar, n1, n2, cap);
+    round_hadamard(ex, Q[1], rh, tol, cap, u);
+    round_hadamard(ex, Q[2], rh, tol, cap, v);
+    round_hadamard(ex, Q[0], Q[0], tol, cap, hh);
+    if (d == 0) {
+      round_hadamard(ex, Q[1], u, tol, cap, t1);
+      round_sum(ex, {Term{1.0, t1}, Term{0.5 * g, hh}}, tol, cap, F[side][1]);
+      round_hadamard(ex, Q[1], v, tol, cap, F[side][2]);
+    } else {
+      round_hadamard(ex, Q[2], u, tol, cap, F[side][1]);
+      round_hadamard(ex, Q[2], v, tol, cap, t1);
+      round_sum(ex, {Term{1.0, t1}, Term{0.5 * g, hh}}, tol, cap, F[side][2]);
+    }
+    F[side][0] = Q[k];
+  }
+  TT lam = alloc_tt(*ex.ar, n1, n2, cap);
+  {
+    TT ins[4] = {qm[0], qm[k], qp[0], qp[k]};
+    CrossFn fl;
+    fl.fn = TT_FN_LLF_LAMBDA;
+    fl.in = ins;
+    fl.nin = 4;
+    fl.prm[0] = g;
+    const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
+    cross(ex, fl, n1, n2, qp[0], tol, cap, kick, sweeps, seed, lam);
+  }
+  for (int c = 0; c < 3; ++c) {
+    Scope sc(*ex.ar);
+    TT dd = alloc_tt(*ex.ar, n1, n2, cap), ld = alloc_tt(*ex.ar, n1, n2, cap);
+    round_sum(ex, {Term{1.0, qp[c]}, Term{-1.0, qm[c]}}, tol, cap, dd);
+    round_hadamard(ex, lam, dd, tol, cap, ld);
+    round_sum(ex, {Term{0.5, F[0][c]}, Term{0.5, F[1][c]}, Term{-0.5, ld}}, tol, cap, Fh[c]);
+  }
+}
+
+// sum_m w_m over the stacked index, then (T - 1)/h on the normal core:
+// returns the TT of (F_{i+1/2} - F_{i-1/2}) / h (Eq. SWE-system-TT).
+static TT quad_and_difference(Solver& S, Exec& ex, const TT& Fh, int d) {
+  const ReconCoeffs& R = recon_coeffs();
+  const int nq = S.nq;
+  const double* w = nq == 2 ? R.w2 : R.w3;
+  const int n = d == 0 ? S.p.ny : S.p.nx;  // tangential size
+  const int nn = d == 0 ? S.p.nx : S.p.ny;
+  const double h = d == 0 ? S.p.lx / S.p.nx : S.p.ly / S.p.ny;
+  TT out = alloc_tt(*ex.ar, S.p.nx, S.p.ny, Fh.r);
+  out.r = Fh.r;
+  StencilSet sq;
+  sq.nout = 1;
+  sq.out[0].dst = d == 0 ? out.b : out.a;
+  sq.out[0].ld = n;
+  for (int m = 0; m < nq; ++m) {
+    double c = w[m];
+    add_taps(sq.out[0], &c, 1, 0, m * n);
+  }
+  stencil(ex, sq, d == 0 ? Fh.b : Fh.a, (long)nq * n, n, Fh.r);
+  StencilSet sd;
+  sd.nout = 1;
+  sd.out[0].dst = d == 0 ? out.a : out.b;
+  sd.out[0].ld = nn;
+  const double cd[2] = {-1.0 / h, 1.0 / h};
+  add_taps(sd.out[0], cd, 2, 0, 0);
+  stencil(ex, sd, d == 0 ? Fh.a : Fh.b, nn, nn, Fh.r);
+  return out;
+}
+
+// F(u) = round(u + dt L(u)) for the three fields (Eq. tt-forward-euler)
+static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT out[3]) {
+  Scope sc(*ex.ar);
+  const tt_fv_params& p = S.p;
+  std::vector<Term> terms[3];
+  for (int c = 0; c < 3; ++c) terms[c].push_back(Term{1.0, Q[c]});
+  for (int d = 0; d < 2; ++d) {
+    TT qm[3], qp[3];
+    const int f1 = d == 0 ? p.nx : S.nq * p.nx, f2 = d == 0 ? S.nq * p.ny : p.ny;
+    for (int c = 0; c < 3; ++c) {
+      if (p.recon == TT_WENO5) {
+        qm[c] = alloc_tt(*ex.ar, f1, f2, p.rank_cap);
+        qp[c] = alloc_tt(*ex.ar, f1, f2, p.rank_cap);
+      }
+      face_tts(S, ex, Q[c], d, c, seed, qm[c], qp[c]);
+    }
+    if (p.eqn == TT_LINEAR) {
+      std::vector<Term> fl[3];
+      flux_linear(S, qm, qp, d, fl);
+      for (int c = 0; c < 3; ++c) {
+        const int R = total_rank(fl[c]);
+        TT cat = alloc_tt(*ex.ar, f1, f2, R);
+        tt_concat(ex, fl[c], cat);
+        TT D = quad_and_difference(S, ex, cat, d);
+        terms[c].push_back(Term{-p.dt, D});
+      }
+    } else {
+      TT Fh[3];
+      for (int c = 0; c < 3; ++c) Fh[c] = alloc_tt(*ex.ar, f1, f2, p.rank_cap);
+      flux_nonlinear(S, ex, qm, qp, d, seed + 64u * d + 40u, Fh);
+      for (int c = 0; c < 3; ++c) {
+        TT D = quad_and_difference(S, ex, Fh[c], d);
+        terms[c].push_back(Term{-p.dt, D});
+      }
+    }
+  }
+  if (p.f != 0.0) {
+    terms[1].push_back(Term{p.dt * p.f, Q[2]});
+    terms[2].push_back(Term{-p.dt * p.f, Q[1]});
+  }
+  for (int c = 0; c < 3; ++c) round_sum(ex, terms[c], p.tol, p.rank_cap, out[c]);
+}
+
+// kick-index seed of a stage: depends on the stage and call site only, so a
+// solver restarted from a checkpoint draws the same kicks
+static unsigned stage_seed(const Solver& S, int stage) { return S.p.seed + 1000u * (unsigned)stage; }
+
+static void run_stage(Solver& S, Exec& ex, int stage) {
+  TT_REQUIRE(stage == S.next_stage, TT_ERR_ARG);
+  Scope sc(*ex.ar);
+  const tt_fv_params& p = S.p;
+  TT f[3];
+  for (int c = 0; c < 3; ++c) f[c] = alloc_tt(*ex.ar, p.nx, p.ny, p.rank_cap);
+  forward_euler(S, ex, S.Qs, stage_seed(S, stage), f);
+  if (stage == 0) {
+    for (int c = 0; c < 3; ++c) copy_tt(ex, f[c], S.Qs[c]);
+  } else if (stage == 1) {
+    for (int c = 0; c < 3; ++c)
+      round_sum(ex, {Term{0.75, S.Qn[c]}, Term{0.25, f[c]}}, p.tol, p.rank_cap, S.Qs[c]);
+  } else {
+    for (int c = 0; c < 3; ++c) {
+      round_sum(ex, {Term{1.0 / 3.0, S.Qn[c]}, Term{2.0 / 3.0, f[c]}}, p.tol, p.rank_cap, S.Qn[c]);
+      copy_tt(ex, S.Qn[c], S.Qs[c]);
+    }
+    S.step_count++;
+  }
+  S.next_stage = (stage + 1) % 3;
+}
+
+// ---------------------------------------------------------------- C ABI glue
+static tt_status guard_status(Exec& ex) {
+  if (ex.dry || ex.dev_status == nullptr) return TT_OK;
+  unsigned st = 0;
+  TT_CUDA(cudaMemcpyAsync(&st, ex.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, ex.s));
+  TT_CUDA(cudaStreamSynchronize(ex.s));
+  prof_flush(ex);
+  if (st & DEV_JACOBI_NOCONV) return TT_ERR_NOCONV;
+  return TT_OK;
+}
+
+static bool valid_params(const tt_fv_params* p) {
+  if (!p) return false;
+  if (p->eqn != TT_LINEAR && p->eqn != TT_NONLINEAR) return false;
+  if (p->recon < TT_UP3 || p->recon > TT_WENO5) return false;
+  if (p->nx < 8 || p->ny < 8 || p->rank_cap < 1 || p->rank_cap > 100) return false;
+  if (!(p->tol >= 0.0) || !(p->dt > 0.0) || !(p->lx > 0.0) || !(p->ly > 0.0) || !(p->g > 0.0)) return false;
+  if (p->precision != TT_FP64 || p->pivots != TT_PIVOT_MAXVOL) return false;
+  if (p->eqn == TT_LINEAR && !(p->H > 0.0)) return false;
+  return true;
+}
+
+static bool valid_tt(const tt2* x) {
+  return x && x->n1 >= 1 && x->n2 >= 1 && x->rank >= 1 && x->cap >= x->rank && x->a && x->b;
+}
+
+static TT to_tt(const tt2& x) {
+  TT t;
+  t.n1 = x.n1;
+  t.n2 = x.n2;
+  t.r = x.rank;
+  t.cap = x.cap;
+  t.a = x.a;
+  t.b = x.b;
+  return t;
+}
+
+// Sets up an Exec over caller workspace: first 256 bytes = device status.
+static void setup_exec(Exec& ex, Arena& ar, void* ws, size_t ws_bytes, cudaStream_t s, int* hi, double* hd,
+                       bool dry) {
+  ar.base = static_cast<char*>(ws);
+  ar.cap = ws_bytes;
+  ar.off = 0;
+  ar.dry = dry;
+  ex.ar = &ar;
+  ex.s = s;
+  ex.dry = dry;
+  ex.h_pinned = hi;
+  ex.h_pinned_d = hd;
+  ex.dev_status = ar.get<unsigned>(64);
+  if (!dry) TT_CUDA(cudaMemsetAsync(ex.dev_status, 0, sizeof(unsigned), s));
+}
+
+// ---------------------------------------------------------------- call wrappers
+template <typename F>
+static size_t dry_bytes(F&& body) {
+  Arena ar;
+  Exec ex;
+  int hi[16];
+  double hd[16];
+  setup_exec(ex, ar, nullptr, 0, nullptr, hi, hd, true);
+  try {
+    body(ex);
+  } catch (const Error&) {
+    return 0;
+  }
+  return ar.peak + ar.peak / 4 + (4u << 20);
+}
+
+template <typename F>
+static tt_status run_call(void* ws, size_t ws_bytes, void* stream, F&& body) {
+  if (!ws) return TT_ERR_ARG;
+  Arena ar;
+  Exec ex;
+  int hi[16];
+  double hd[16];
+  try {
+    setup_exec(ex, ar, ws, ws_bytes, static_cast<cudaStream_t>(stream), hi, hd, false);
+    tt_status r = body(ex);
+    if (r != TT_OK) return r;
+    return guard_status(ex);
+  } catch (const Error& e) {
+    return e.code;
+  }
+}
+
+}  // namespace ttfv
+
+using namespace ttfv;
+
+struct tt_fv_ctx {
+  Solver S;
+};
+
+extern "C" {
+
+const char* tt_fv_version(void) { return "tt_fv 0.1 (sm_103a, FP64)"; }
+
+static size_t solver_bytes(const tt_fv_params* p, bool with_state) {
+  // dry run of one stage at the rank cap
+  Solver S;
+  S.p = *p;
+  S.nq = nq_of(p->recon);
+  Exec ex;
+  int hi[16];
+  double hd[16];
+  setup_exec(ex, S.ar, nullptr, 0, nullptr, hi, hd, true);
+  try {
+    for (int c = 0; c < 3; ++c) {
+      S.Qn[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
+      S.Qs[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
+      S.Qn[c].r = S.Qs[c].r = p->rank_cap;
+    }
+    (void)with_state;
+    for (int st = 0; st < 3; ++st) run_stage(S, ex, st);
+  } catch (const Error&) {
+    return 0;
+  }
+  const size_t peak = S.ar.peak;
+  return peak + peak / 2 + (64u << 20);
+}
+
+size_t tt_fv_workspace_size(const tt_fv_params* p) {
+  if (!valid_params(p)) return 0;
+  return solver_bytes(p, true);
+}
+
+tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws_bytes, void* stream,
+                     tt_fv_ctx** out) {
+  if (!out || !valid_params(p) || !q0 || !ws) return TT_ERR_ARG;
+  for (int c = 0; c < 3; ++c)
+    if (!valid_tt(&q0[c]) || q0[c].n1 != p->nx || q0[c].n2 != p->ny || q0[c].rank > p->rank_cap)
+      return TT_ERR_ARG;
+  tt_fv_ctx* ctx = new (std::nothrow) tt_fv_ctx();
+  if (!ctx) return TT_ERR_OOM;
+  Solver& S = ctx->S;
+  S.p = *p;
+  S.s = static_cast<cudaStream_t>(stream);
+  S.nq = nq_of(p->recon);
+  try {
+    setup_exec(S.ex, S.ar, ws, ws_bytes, S.s, S.h_int, S.h_dbl, false);
+    S.ex.prof = &S.prof;
+    for (int c = 0; c < 3; ++c) {
+      S.Qn[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
+      S.Qs[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
+      copy_tt(S.ex, to_tt(q0[c]), S.Qn[c]);
+      copy_tt(S.ex, to_tt(q0[c]), S.Qs[c]);
+    }
+    S.ar.peak = S.ar.off;
+  } catch (const Error& e) {
+    delete ctx;
+    return e.code;
+  }
+  *out = ctx;
+  return TT_OK;
+}
+
+tt_status tt_fv_stage(tt_fv_ctx* ctx, int32_t stage) {
+  if (!ctx || stage < 0 || stage > 2) return TT_ERR_ARG;
+  try {
+    run_stage(ctx->S, ctx->S.ex, stage);
+    return guard_status(ctx->S.ex);
+  } catch (const Error& e) {
+    return e.code;
+  }
+}
+
+tt_status tt_fv_step(tt_fv_ctx* ctx, int32_t nsteps) {
+  if (!ctx || nsteps < 0 || ctx->S.next_stage != 0) return TT_ERR_ARG;
+  for (int n = 0; n < nsteps; ++n)
+    for (int st = 0; st < 3; ++st) {
+      tt_status r = tt_fv_stage(ctx, st);
+      if (r != TT_OK) return r;
+    }
+  return TT_OK;
+}
+
+tt_status tt_fv_get(tt_fv_ctx* ctx, tt2 q_out[3]) {
+  if (!ctx || !q_out) return TT_ERR_ARG;
+  Solver& S = ctx->S;
+  try {
+    for (int c = 0; c < 3; ++c) {
+      const TT& src = S.Qs[c];
+      if (!q_out[c].a || !q_out[c].b || q_out[c].n1 != src.n1 || q_out[c].n2 != src.n2 || q_out[c].cap < src.r)
+        return TT_ERR_ARG;
+      TT dst = to_tt(q_out[c]);
+      dst.r = 0;
+      copy_tt(S.ex, src, dst);
+      q_out[c].rank = src.r;
+    }
+    TT_CUDA(cudaStreamSynchronize(S.s));
+  } catch (const Error& e) {
+    return e.code;
+  }
+  return TT_OK;
+}
+
+tt_status tt_fv_set(tt_fv_ctx* ctx, const tt2 q[3]) {
+  if (!ctx || !q) return TT_ERR_ARG;
+  Solver& S = ctx->S;
+  for (int c = 0; c < 3; ++c)
+    if (!valid_tt(&q[c]) || q[c].n1 != S.p.nx || q[c].n2 != S.p.ny || q[c].rank > S.p.rank_cap) return TT_ERR_ARG;
+  try {
+    for (int c = 0; c < 3; ++c) {
+      copy_tt(S.ex, to_tt(q[c]), S.Qn[c]);
+      copy_tt(S.ex, to_tt(q[c]), S.Qs[c]);
+    }
+    S.next_stage = 0;
+  } catch (const Error& e) {
+    return e.code;
+  }
+  return TT_OK;
+}
+
+tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* o) {
+  if (!ctx || !o) return TT_ERR_ARG;
+  Solver& S = ctx->S;
+  Exec& ex = S.ex;
+  std::memset(o, 0, sizeof(*o));
+  for (int c = 0; c < 3; ++c) o->rank[c] = S.Qs[c].r;
+  o->rounds = ex.rounds;
+  o->syncs = ex.syncs;
+  o->jacobi_sweeps = ex.jacobi_sweeps;
+  o->cross_calls = ex.cross_calls;
+  o->cross_sweeps = ex.cross_sweeps;
+  o->taylor_iters = ex.taylor_iters;
+  o->cap_hits = ex.cap_hits;
+  o->qb_attempts = ex.qb_attempts;
+  o->qb_uncertified = ex.qb_uncertified;
+  o->flops = ex.flops;
+  o->bytes = ex.bytes;
+  unsigned st = 0;
+  if (cudaMemcpyAsync(&st, ex.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, S.s) != cudaSuccess ||
+      cudaStreamSynchronize(S.s) != cudaSuccess)
+    return TT_ERR_CUDA;
+  o->device_status = st;
+  return TT_OK;
+}
+
+void tt_fv_destroy(tt_fv_ctx* ctx) { delete ctx; }
+
+tt_status tt_fv_profile(tt_fv_ctx* ctx, int32_t enable) {
+  if (!ctx) return TT_ERR_ARG;
+  try {
+    TT_CUDA(cudaStreamSynchronize(ctx->S.s));
+    prof_flush(ctx->S.ex);
+  } catch (const Error& e) {
+    return e.code;
+  }
+  ctx->S.prof.on = enable != 0;
+  return TT_OK;
+}
+
+tt_status tt_fv_kernel_profile(tt_fv_ctx* ctx, tt_kernel_prof out[TT_K_NCLASS], int32_t reset) {
+  if (!ctx || !out) return TT_ERR_ARG;
+  Prof& pf = ctx->S.prof;
+  try {
+    TT_CUDA(cudaStreamSynchronize(ctx->S.s));
+    prof_flush(ctx->S.ex);
+  } catch (const Error& e) {
+    return e.code;
+  }
+  for (int c = 0; c < TT_K_NCLASS; ++c) {
+    out[c].ms = pf.ms[c];
+    out[c].flops = pf.flops[c];
+    out[c].bytes = pf.bytes[c];
+    out[c].launches = pf.n[c];
+    if (reset) {
+      pf.ms[c] = pf.flops[c] = pf.bytes[c] = 0.0;
+      pf.n[c] = 0;
+    }
+  }
+  return TT_OK;
+}
+
+uint64_t tt_launch_count(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------- primitives
+static TT fake_tt(Arena& ar, int n1, int n2, int r) {
+  TT t = alloc_tt(ar, n1, n2, r);
+  t.r = r;
+  return t;
+}
+
+size_t tt_round_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap) {
+  if (n1 < 1 || n2 < 1 || rank_in < 1 || rank_cap < 1) return 0;
+  return dry_bytes([&](Exec& ex) {
+    TT x = fake_tt(*ex.ar, n1, n2, rank_in);
+    TT y = fake_tt(*ex.ar, n1, n2, rank_cap);
+    round_tt(ex, x, 0.0, rank_cap, y);
+  });
+}
+
+tt_status tt_round(const tt2* x, double tol, int32_t rank_cap, tt2* y, double* err_out, void* ws, size_t ws_bytes,
+                   void* stream) {
+  if (!valid_tt(x) || !y || !y->a || !y->b || y->n1 != x->n1 || y->n2 != x->n2 || rank_cap < 1 ||
+      y->cap < std::min(rank_cap, std::min(x->n1, x->n2)) || !(tol >= 0.0))
+    return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    TT X = to_tt(*x), Y = to_tt(*y);
+    RoundInfo ri = round_tt(ex, X, tol, rank_cap, Y);
+    y->rank = Y.r;
+    if (err_out) *err_out = ri.err;
+    return TT_OK;
+  });
+}
+
+size_t tt_round_hadamard_workspace_size(int32_t n1, int32_t n2, int32_t rank_x, int32_t rank_z, int32_t rank_cap) {
+  if (n1 < 1 || n2 < 1 || rank_x < 1 || rank_z < 1 || rank_cap < 1) return 0;
+  return dry_bytes([&](Exec& ex) {
+    TT x = fake_tt(*ex.ar, n1, n2, rank_x), z = fake_tt(*ex.ar, n1, n2, rank_z);
+    TT y = fake_tt(*ex.ar, n1, n2, rank_cap);
+    round_hadamard(ex, x, z, 0.0, rank_cap, y);
+  });
+}
+
+tt_status tt_round_hadamard(const tt2* x, const tt2* z, double tol, int32_t rank_cap, tt2* y, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (!valid_tt(x) || !valid_tt(z) || !y || !y->a || !y->b || x->n1 != z->n1 || x->n2 != z->n2 ||
+      y->n1 != x->n1 || y->n2 != x->n2 || rank_cap < 1 || y->cap < std::min(rank_cap, std::min(x->n1, x->n2)) ||
+      !(tol >= 0.0))
+    return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    TT X = to_tt(*x), Z = to_tt(*z), Y = to_tt(*y);
+    round_hadamard(ex, X, Z, tol, rank_cap, Y);
+    y->rank = Y.r;
+    return TT_OK;
+  });
+}
+
+size_t tt_cross_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap, int32_t kick) {
+  if (n1 < 1 || n2 < 1 || rank_in < 1 || rank_cap < 1 || kick < 0) return 0;
+  return dry_bytes([&](Exec& ex) {
+    TT x0 = fake_tt(*ex.ar, n1, n2, rank_in);
+    TT y = fake_tt(*ex.ar, n1, n2, rank_cap);
+    CrossFn f;
+    f.fn = TT_FN_ENTRY;
+    f.in = &x0;
+    f.nin = 1;
+    cross(ex, f, n1, n2, x0, 0.0, rank_cap, kick, 2, 0, y);
+  });
+}
+
+tt_status tt_cross(int32_t fn, const tt2* inputs, int32_t ninputs, const tt2* x0, const double* fparams, double tol,
+                   int32_t rank_cap, int32_t kick, int32_t max_sweeps, uint32_t seed, tt2* y, int32_t* sweeps_out,
+                   void* ws, size_t ws_bytes, void* stream) {
+  if (fn < TT_FN_ENTRY || fn > TT_FN_LLF_LAMBDA || !inputs || ninputs < 1 || ninputs > 4 || !valid_tt(x0) || !y ||
+      !y->a || !y->b || rank_cap < 1 || kick < 0 || max_sweeps < 1 || x0->n2 != y->n2 || !(tol >= 0.0) ||
+      y->cap < rank_cap)
+    return TT_ERR_ARG;
+  const int need = fn == TT_FN_LLF_LAMBDA ? 4 : 1;
+  if (ninputs != need) return TT_ERR_ARG;
+  for (int q = 0; q < ninputs; ++q) {
+    if (!valid_tt(&inputs[q])) return TT_ERR_ARG;
+    // every evaluated entry must index inside the inputs
+    int e1 = y->n1, e2 = y->n2;
+    if (fn == TT_FN_WENO_S2) {
+      if (!fparams || fparams[2] != 3.0) return TT_ERR_ARG;
+      if (fparams[1] == 1.0)
+        e2 = 3 * inputs[q].n2;
+      else if (fparams[1] == 0.0)
+        e1 = 3 * inputs[q].n1;
+      else
+        return TT_ERR_ARG;
+      if (y->n1 != e1 || y->n2 != e2) return TT_ERR_ARG;
+    } else if (inputs[q].n1 != e1 || inputs[q].n2 != e2) {
+      return TT_ERR_ARG;
+    }
+  }
+  if (fn == TT_FN_WENO_S1 && (fparams[2] != 0.0 && fparams[2] != 1.0)) return TT_ERR_ARG;
+  if ((fn == TT_FN_WENO_S1 || fn == TT_FN_WENO_S2 || fn == TT_FN_ENTRY) && !fparams && fn != TT_FN_ENTRY)
+    return TT_ERR_ARG;
+  if (fn == TT_FN_LLF_LAMBDA && !fparams) return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    TT ins[4];
+    for (int q = 0; q < ninputs; ++q) ins[q] = to_tt(inputs[q]);
+    CrossFn f;
+    f.fn = fn;
+    f.in = ins;
+    f.nin = ninputs;
+    if (fparams)
+      for (int q = 0; q < 3; ++q) f.prm[q] = fparams[q];
+    if (fn == TT_FN_LLF_LAMBDA) f.prm[0] = fparams[0];
+    TT X0 = to_tt(*x0), Y = to_tt(*y);
+    const int sw = cross(ex, f, y->n1, y->n2, X0, tol, rank_cap, kick, max_sweeps, seed, Y);
+    y->rank = Y.r;
+    if (sweeps_out) *sweeps_out = sw;
+    return TT_OK;
+  });
+}
+
+size_t tt_reciprocal_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap) {
+  if (n1 < 1 || n2 < 1 || rank_in < 1 || rank_cap < 1) return 0;
+  return dry_bytes([&](Exec& ex) {
+    TT x = fake_tt(*ex.ar, n1, n2, rank_in);
+    TT y = fake_tt(*ex.ar, n1, n2, rank_cap);
+    reciprocal(ex, x, 1.0, rank_cap, 2, y, nullptr);
+  });
+}
+
+tt_status tt_reciprocal(const tt2* x, double tol, int32_t rank_cap, int32_t max_iter, tt2* y, int32_t* iters_out,
+                        void* ws, size_t ws_bytes, void* stream) {
+  if (!valid_tt(x) || !y || !y->a || !y->b || y->n1 != x->n1 || y->n2 != x->n2 || rank_cap < 1 ||
+      y->cap < rank_cap || max_iter < 1 || !(tol > 0.0))
+    return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    TT X = to_tt(*x), Y = to_tt(*y);
+    bool nc = false;
+    const int it = reciprocal(ex, X, tol, rank_cap, max_iter, Y, &nc);
+    y->rank = Y.r;
+    if (iters_out) *iters_out = it;
+    return nc ? TT_ERR_NOCONV : TT_OK;
+  });
+}
+
+tt_status tt_recon_linear(const tt2* x, int32_t direction, int32_t scheme, tt2* qm, tt2* qp, void* stream) {
+  if (!valid_tt(x) || !qm || !qp || (direction != 0 && direction != 1) || (scheme != TT_UP3 && scheme != TT_UP5))
+    return TT_ERR_ARG;
+  const int nq = nq_of(scheme);
+  const int f1 = direction == 0 ? x->n1 : nq * x->n1, f2 = direction == 0 ? nq * x->n2 : x->n2;
+  for (tt2* q : {qm, qp})
+    if (!q->a || !q->b || q->n1 != f1 || q->n2 != f2 || q->cap < x->rank) return TT_ERR_ARG;
+  Arena ar;
+  Exec ex;
+  int hi[16];
+  double hd[16];
+  try {
+    ar.dry = false;
+    ex.ar = &ar;
+    ex.s = static_cast<cudaStream_t>(stream);
+    ex.h_pinned = hi;
+    ex.h_pinned_d = hd;
+    TT X = to_tt(*x), M = to_tt(*qm), P = to_tt(*qp);
+    double* shared_keep = direction == 0 ? P.b : P.a;
+    recon_linear(ex, X, direction, scheme, M, P);
+    // the library shares the stacked core between qm and qp; the C ABI hands
+    // the caller two independent copies
+    if (direction == 0)
+      scaled_copy(ex, shared_keep, M.b, (long)f2 * x->rank, 1.0);
+    else
+      scaled_copy(ex, shared_keep, M.a, (long)f1 * x->rank, 1.0);
+    qm->rank = qp->rank = x->rank;
+  } catch (const Error& e) {
+    return e.code;
+  }
+  return TT_OK;
+}
+
+}  // extern "C"

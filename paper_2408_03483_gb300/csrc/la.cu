@@ -1,0 +1,716 @@
+// Dense FP64 building blocks of TT rounding and cross (Sec. 3.2-3.3):
+// split-K GEMM, full Hadamard-product formation, sums of squares, Householder
+// TSQR with implicit Q, one-sided Jacobi SVD, maximum-volume row selection.
+//
+// GB300 has 2 FP64 FMA/clk/SM (about 8 GFLOP/s per SM), so every kernel with
+// real FP64 work spreads it over at least ~2 CTAs per SM (split-K, row
+// blocks); the small dense factorisations (p <= 112) run one per CTA with the
+// matrix resident in shared memory.
+#include <cfloat>
+#include <cmath>
+#include <algorithm>
+
+#include "tt_common.cuh"
+
+namespace ttfv {
+
+static int g_sm_count = 0;
+static int sm_count() {
+  if (g_sm_count == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sm_count <= 0) g_sm_count = 152;
+  }
+  return g_sm_count;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (all threads get the result).  `red` holds >= 33 doubles.
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// ============================================================== GEMM
+// C = alpha * A B + beta * C with generic strides; tile 32x32, BK 16,
+// 256 threads x 4 outputs; deterministic split-K through a partial buffer.
+constexpr int GB = 32, GK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_partial(int M, int N, int K, int kchunk,
+                                                      const double* __restrict__ A, long ars, long acs,
+                                                      const double* __restrict__ B, long brs, long bcs,
+                                                      double* __restrict__ P) {
+  __shared__ double As[GK][GB + 1];
+  __shared__ double Bs[GK][GB + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.x * GB, j0 = blockIdx.y * GB;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k0 = kb; k0 < ke; k0 += GK) {
+    for (int t = threadIdx.x; t < GB * GK; t += 256) {
+      int ii, kk;
+      if (ars == 1) { ii = t % GB; kk = t / GB; } else { kk = t % GK; ii = t / GK; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      As[kk][ii] = (gi < M && gk < ke) ? A[gi * ars + gk * acs] : 0.0;
+    }
+    for (int t = threadIdx.x; t < GB * GK; t += 256) {
+      int jj, kk;
+      if (brs == 1) { kk = t % GK; jj = t / GK; } else { jj = t % GB; kk = t / GB; }
+      const int gj = j0 + jj, gk = k0 + kk;
+      Bs[kk][jj] = (gj < N && gk < ke) ? B[gk * brs + gj * bcs] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      const double a0 = As[kk][tx], a1 = As[kk][tx + 16];
+      const double b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  double* Pz = P + (size_t)blockIdx.z * M * N;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int i = i0 + tx + 16 * u, j = j0 + ty + 16 * v;
+      if (i < M && j < N) Pz[i + (size_t)j * M] = acc[u][v];
+    }
+}
+
+__global__ void k_gemm_reduce(int M, int N, int nsplit, const double* __restrict__ P, double alpha,
+                              double beta, double* __restrict__ C, long ldc) {
+  const long total = (long)M * N;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nsplit; ++z) s += P[t + (size_t)z * total];
+    const int i = int(t % M), j = int(t / M);
+    double* c = C + i + (size_t)j * ldc;
+    *c = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *c);
+  }
+}
+
+void gemm(Exec& ex, int M, int N, int K, double alpha, const double* A, long ars, long acs,
+          const double* B, long brs, long bcs, double beta, double* C, long ldc) {
+  if (M <= 0 || N <= 0) return;
+  const int tiles = ceil_div(M, GB) * ceil_div(N, GB);
+  int nsplit = std::max(1, std::min(ceil_div(2 * sm_count(), tiles), ceil_div(std::max(K, 1), 64)));
+  int kchunk = ceil_div(ceil_div(std::max(K, 1), nsplit), GK) * GK;
+  nsplit = ceil_div(std::max(K, 1), kchunk);
+  Scope sc(*ex.ar);
+  double* P = ex.ar->get<double>((size_t)nsplit * M * N);
+  if (ex.dry) return;
+  dim3 grid(ceil_div(M, GB), ceil_div(N, GB), nsplit);
+  const double mnk = 2.0 * M * N * (double)K;
+  TT_KERNEL(ex, K_GEMM, mnk, 8.0 * ((double)M * K + (double)K * N + (double)nsplit * M * N),
+            k_gemm_partial<<<grid, 256, 0, ex.s>>>(M, N, K, kchunk, A, ars, acs, B, brs, bcs, P));
+  const long total = (long)M * N;
+  const int blocks = std::max(1, std::min(ceil_div(total, 256), 4 * sm_count()));
+  TT_KERNEL(ex, K_GEMM, (double)nsplit * total, 8.0 * total * (nsplit + (beta == 0.0 ? 1 : 2)),
+            k_gemm_reduce<<<blocks, 256, 0, ex.s>>>(M, N, nsplit, P, alpha, beta, C, ldc));
+}
+
+// ============================================================== Hadamard slab
+// Y[i,j] = (A1 B1^T)[i,j] * (A2 B2^T)[i,j]: the full face tensor of a TT
+// Hadamard product, formed without the r1*r2-column Khatri-Rao cores.
+constexpr int HB = 32, HK = 16;
+__global__ void __launch_bounds__(256) k_form_hadamard(int n1, int n2, const double* __restrict__ A1, int r1,
+                                                       const double* __restrict__ B1,
+                                                       const double* __restrict__ A2, int r2,
+                                                       const double* __restrict__ B2,
+                                                       double* __restrict__ Y, long ldy) {
+  __shared__ double As[HK][HB + 1];
+  __shared__ double Bs[HK][HB + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.x * HB, j0 = blockIdx.y * HB;
+  double acc[2][2][2] = {};
+  for (int f = 0; f < 2; ++f) {
+    const double* A = f ? A2 : A1;
+    const double* B = f ? B2 : B1;
+    const int r = f ? r2 : r1;
+    for (int k0 = 0; k0 < r; k0 += HK) {
+      for (int t = threadIdx.x; t < HB * HK; t += 256) {
+        const int ii = t % HB, kk = t / HB;
+        const int gi = i0 + ii, gj = j0 + ii, gk = k0 + kk;
+        As[kk][ii] = (gi < n1 && gk < r) ? A[gi + (size_t)gk * n1] : 0.0;
+        Bs[kk][ii] = (gj < n2 && gk < r) ? B[gj + (size_t)gk * n2] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < HK; ++kk) {
+        const double a0 = As[kk][tx], a1 = As[kk][tx + 16];
+        const double b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+        acc[f][0][0] = fma(a0, b0, acc[f][0][0]);
+        acc[f][0][1] = fma(a0, b1, acc[f][0][1]);
+        acc[f][1][0] = fma(a1, b0, acc[f][1][0]);
+        acc[f][1][1] = fma(a1, b1, acc[f][1][1]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int i = i0 + tx + 16 * u, j = j0 + ty + 16 * v;
+      if (i < n1 && j < n2) Y[i + (size_t)j * ldy] = acc[0][u][v] * acc[1][u][v];
+    }
+}
+
+void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, const double* B1,
+                        const double* A2, int r2, const double* B2, double* Y, long ldy) {
+  if (ex.dry) return;
+  dim3 grid(ceil_div(n1, HB), ceil_div(n2, HB));
+  TT_KERNEL(ex, K_FORM, 2.0 * n1 * (double)n2 * (r1 + r2) + (double)n1 * n2,
+            8.0 * ((double)(n1 + n2) * (r1 + r2) + (double)n1 * n2),
+            k_form_hadamard<<<grid, 256, 0, ex.s>>>(n1, n2, A1, r1, B1, A2, r2, B2, Y, ldy));
+}
+
+// ============================================================== sum of squares
+__global__ void k_sumsq_partial(const double* __restrict__ X, int m, int n, long ld, double* part) {
+  __shared__ double red[33];
+  double s = 0.0;
+  const long total = (long)m * n;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const double x = X[(t % m) + (t / m) * ld];
+    s = fma(x, x, s);
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void k_sum_fixed(const double* part, int n, double* out) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) s += part[t];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+void sumsq(Exec& ex, const double* X, int m, int n, long ld, double* out) {
+  Scope sc(*ex.ar);
+  const int blocks = std::max(1, std::min(ceil_div((long)m * n, 256), 2 * sm_count()));
+  double* part = ex.ar->get<double>(blocks);
+  if (ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, 2.0 * m * (double)n, 8.0 * m * (double)n,
+            k_sumsq_partial<<<blocks, 256, 0, ex.s>>>(X, m, n, ld, part));
+  TT_KERNEL(ex, K_OTHER, blocks, 8.0 * blocks, k_sum_fixed<<<1, 256, 0, ex.s>>>(part, blocks, out));
+}
+
+// ============================================================== TSQR
+// Householder QR of row blocks held in shared memory (LAPACK sign convention:
+// beta = -sign(alpha) ||x||, v(0) = 1, tau = (beta - alpha) / beta).
+constexpr int QR_THREADS = 512;
+constexpr size_t QR_SMEM_MAX = 200 * 1024;
+
+__device__ void cta_householder_qr(double* A, int mb, int p, double* tau_out, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double s_tau;
+  for (int j = 0; j < p; ++j) {
+    double* col = A + (size_t)j * mb;
+    double s = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < mb; i += blockDim.x) s = fma(col[i], col[i], s);
+    const double sigma = block_sum(s, red);
+    const double alpha = col[j];
+    double tau = 0.0, scale = 0.0, beta = alpha;
+    if (sigma > 0.0) {
+      const double nrm = sqrt(fma(alpha, alpha, sigma));
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    __syncthreads();
+    if (sigma > 0.0)
+      for (int i = j + 1 + threadIdx.x; i < mb; i += blockDim.x) col[i] *= scale;
+    if (threadIdx.x == 0) {
+      col[j] = beta;
+      s_tau = tau;
+      tau_out[j] = tau;
+    }
+    __syncthreads();
+    tau = s_tau;
+    if (tau != 0.0) {
+      for (int c = j + 1 + w; c < p; c += nw) {
+        double* cc = A + (size_t)c * mb;
+        double d = 0.0;
+        for (int i = j + 1 + lane; i < mb; i += 32) d = fma(col[i], cc[i], d);
+        d = warp_sum(d) + cc[j];
+        const double f = tau * d;
+        if (lane == 0) cc[j] -= f;
+        for (int i = j + 1 + lane; i < mb; i += 32) cc[i] = fma(-f, col[i], cc[i]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const double* __restrict__ X, int m, int p, long ldx,
+                                                          int mb, double* V, double* tau, double* Rst, long ldr) {
+  extern __shared__ double sm[];
+  __shared__ double red[33];
+  const int b = blockIdx.x, r0 = b * mb;
+  double* A = sm;
+  for (int t = threadIdx.x; t < mb * p; t += blockDim.x) {
+    const int i = t % mb, j = t / mb;
+    A[t] = (r0 + i < m) ? X[(r0 + i) + (size_t)j * ldx] : 0.0;
+  }
+  __syncthreads();
+  cta_householder_qr(A, mb, p, tau + (size_t)b * p, red);
+  double* Vb = V + (size_t)b * mb * p;
+  for (int t = threadIdx.x; t < mb * p; t += blockDim.x) Vb[t] = A[t];
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int i = t % p, j = t / p;
+    Rst[(size_t)(b * p + i) + (size_t)j * ldr] = (i <= j) ? A[i + (size_t)j * mb] : 0.0;
+  }
+}
+
+static int qr_block_rows(int p, int level) {
+  const int lim = int(QR_SMEM_MAX / (8 * (size_t)p));
+  int mb = level == 0 ? std::max(2 * p, 128) : std::max(2 * p, std::min(4 * p, 256));
+  mb = std::min(mb, lim);
+  return std::max(mb, p);
+}
+
+void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t) {
+  TT_REQUIRE(p >= 1 && p <= 112 && m >= 1, TT_ERR_ARG);
+  t = QRTree{};
+  t.m = m;
+  t.p = p;
+  const double* in = X;
+  long ldin = ldx;
+  int rows = m;
+  for (int level = 0;; ++level) {
+    TT_REQUIRE(level < 32, TT_ERR_ARG);
+    const int mb = std::max(qr_block_rows(p, level), p);
+    const int nb = ceil_div(rows, mb);
+    double* V = ex.ar->get<double>((size_t)nb * mb * p);
+    double* tau = ex.ar->get<double>((size_t)nb * p);
+    double* Rst = ex.ar->get<double>((size_t)nb * p * p);
+    t.mrows.push_back(rows);
+    t.mb.push_back(mb);
+    t.nb.push_back(nb);
+    t.V.push_back(V);
+    t.tau.push_back(tau);
+    if (!ex.dry) {
+      const size_t smem = (size_t)mb * p * 8;
+      TT_CUDA(cudaFuncSetAttribute(k_qr_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      // algorithmic work: Householder QR of the valid rows of each block
+      const double fl = 2.0 * rows * (double)p * p - nb * (2.0 / 3.0) * p * (double)p * p;
+      TT_KERNEL(ex, K_QR, std::max(fl, 0.0), 8.0 * ((double)rows * p * 2 + (double)nb * p * p),
+                k_qr_blocks<<<nb, QR_THREADS, smem, ex.s>>>(in, rows, p, ldin, mb, V, tau, Rst, (long)nb * p));
+    }
+    if (nb == 1) {
+      t.R = Rst;  // p x p with ld = p
+      t.levels = level + 1;
+      return;
+    }
+    in = Rst;
+    ldin = (long)nb * p;
+    rows = nb * p;
+  }
+}
+
+// Apply the reflectors of each block (in reverse order) to [Zin_block; 0].
+__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const double* __restrict__ V,
+                                                                const double* __restrict__ tau, int mb, int p,
+                                                                int rows, int k, const double* __restrict__ Zin,
+                                                                long ldzi, int zin_rows_per_block,
+                                                                double* __restrict__ Zout, long ldzo) {
+  extern __shared__ double sm[];
+  const int b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* Z = sm;  // mb x k
+  for (int t = threadIdx.x; t < mb * k; t += blockDim.x) {
+    const int i = t % mb, j = t / mb;
+    Z[t] = (i < zin_rows_per_block) ? Zin[(size_t)(b * zin_rows_per_block + i) + (size_t)j * ldzi] : 0.0;
+  }
+  __syncthreads();
+  const double* Vb = V + (size_t)b * mb * p;
+  const double* tb = tau + (size_t)b * p;
+  for (int jr = p - 1; jr >= 0; --jr) {
+    const double tj = tb[jr];
+    if (tj != 0.0) {
+      const double* v = Vb + (size_t)jr * mb;
+      for (int c = w; c < k; c += nw) {
+        double* zc = Z + (size_t)c * mb;
+        double d = 0.0;
+        for (int i = jr + 1 + lane; i < mb; i += 32) d = fma(v[i], zc[i], d);
+        d = warp_sum(d) + zc[jr];
+        const double f = tj * d;
+        if (lane == 0) zc[jr] -= f;
+        for (int i = jr + 1 + lane; i < mb; i += 32) zc[i] = fma(-f, v[i], zc[i]);
+      }
+    }
+    __syncthreads();
+  }
+  const int r0 = b * mb;
+  for (int t = threadIdx.x; t < mb * k; t += blockDim.x) {
+    const int i = t % mb, j = t / mb;
+    if (r0 + i < rows) Zout[(size_t)(r0 + i) + (size_t)j * ldzo] = Z[t];
+  }
+}
+
+void tsqr_apply(Exec& ex, const QRTree& t, const double* C, int k, long ldc, double* Out, long ldo) {
+  TT_REQUIRE(k >= 1, TT_ERR_ARG);
+  Scope sc(*ex.ar);
+  const int p = t.p;
+  // top-down: the last level's single block takes [C; 0]
+  const double* zin = C;
+  long ldzi = ldc;
+  for (int l = t.levels - 1; l >= 0; --l) {
+    const int rows = t.mrows[l], mb = t.mb[l], nb = t.nb[l];
+    double* zout;
+    long ldzo;
+    if (l == 0) {
+      zout = Out;
+      ldzo = ldo;
+    } else {
+      zout = ex.ar->get<double>((size_t)rows * k);
+      ldzo = rows;
+    }
+    if (!ex.dry) {
+      const size_t smem = (size_t)mb * k * 8;
+      TT_REQUIRE(smem <= QR_SMEM_MAX + 16 * 1024, TT_ERR_ARG);
+      TT_CUDA(cudaFuncSetAttribute(k_qr_apply_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      TT_KERNEL(ex, K_QR_APPLY, 4.0 * rows * (double)p * k, 8.0 * ((double)rows * (p + k) + (double)nb * p * k),
+                k_qr_apply_blocks<<<nb, QR_THREADS, smem, ex.s>>>(t.V[l], t.tau[l], mb, p, rows, k, zin, ldzi, p,
+                                                                   zout, ldzo));
+    }
+    zin = zout;
+    ldzi = ldzo;
+  }
+}
+
+// ============================================================== Jacobi SVD
+// One-sided (Hestenes) Jacobi on the columns of M, parallel round-robin
+// ordering, one warp per column pair, everything in shared memory.
+constexpr int JAC_THREADS = 1024;
+constexpr int JAC_MAX_SWEEPS = 40;
+
+__global__ void __launch_bounds__(JAC_THREADS) k_jacobi_svd(const double* __restrict__ Min, int p, double tol,
+                                                           int cap, double* US, double* Vout, double* sig,
+                                                           int* k_out, double* tail_out, unsigned* status,
+                                                           int* sweeps_out) {
+  extern __shared__ double sm[];
+  double* M = sm;                      // p x p
+  double* V = sm + (size_t)p * p;      // p x p
+  __shared__ double norms[128];
+  __shared__ int order[128];
+  __shared__ int s_rot;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    M[t] = Min[t];
+    V[t] = ((t % p) == (t / p)) ? 1.0 : 0.0;
+  }
+  const int q = p + (p & 1);  // even number of players; index p is a dummy
+  const double eps = DBL_EPSILON * p;
+  int sweep = 0;
+  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int step = 0; step < q - 1; ++step) {
+      for (int pr = w; pr < q / 2; pr += nw) {
+        const int a = pr, bpos = q - 1 - pr;
+        const int i = (a == 0) ? 0 : 1 + ((a - 1 + step) % (q - 1));
+        const int j = 1 + ((bpos - 1 + step) % (q - 1));
+        if (i >= p || j >= p) continue;
+        double* ci = M + (size_t)i * p;
+        double* cj = M + (size_t)j * p;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = lane; r < p; r += 32) {
+          const double x = ci[r], y = cj[r];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (al == 0.0 || be == 0.0 || fabs(ga) <= eps * sqrt(al) * sqrt(be)) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = c * t;
+        for (int r = lane; r < p; r += 32) {
+          const double x = ci[r], y = cj[r];
+          ci[r] = c * x - s * y;
+          cj[r] = s * x + c * y;
+        }
+        double* vi = V + (size_t)i * p;
+        double* vj = V + (size_t)j * p;
+        for (int r = lane; r < p; r += 32) {
+          const double x = vi[r], y = vj[r];
+          vi[r] = c * x - s * y;
+          vj[r] = s * x + c * y;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  // column norms -> singular values; sort descending (ties by index)
+  for (int j = w; j < p; j += nw) {
+    double s = 0.0;
+    for (int r = lane; r < p; r += 32) s = fma(M[r + (size_t)j * p], M[r + (size_t)j * p], s);
+    s = warp_sum(s);
+    if (lane == 0) norms[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    int rk = 0;
+    for (int l = 0; l < p; ++l) rk += (norms[l] > norms[j]) || (norms[l] == norms[j] && l < j);
+    order[rk] = j;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int r = t % p, c = t / p, src = order[c];
+    US[t] = M[r + (size_t)src * p];
+    Vout[t] = V[r + (size_t)src * p];
+  }
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int c = 0; c < p; ++c) {
+      const double s = norms[order[c]];
+      sig[c] = s;
+      tot = fma(s, s, tot);
+    }
+    // smallest k with tail(k) <= tol ||M||_F, at least 1, at most cap
+    int k = p;
+    double tail = 0.0;
+    const double bound = tol * tol * tot;
+    for (int c = p - 1; c >= 0; --c) {
+      const double s = norms[order[c]];
+      const double nt = fma(s, s, tail);
+      if (nt <= bound) {
+        tail = nt;
+        k = c;
+      } else {
+        break;
+      }
+    }
+    if (tot == 0.0) k = 1;
+    if (k < 1) k = 1;
+    if (k > cap) k = cap;
+    double dis = 0.0;
+    for (int c = p - 1; c >= k; --c) {
+      const double s = norms[order[c]];
+      dis = fma(s, s, dis);
+    }
+    *k_out = k;
+    tail_out[0] = sqrt(dis);
+    tail_out[1] = sqrt(tot);
+    if (sweep >= JAC_MAX_SWEEPS) atomicOr(status, DEV_JACOBI_NOCONV);
+    if (sweeps_out) *sweeps_out = sweep + 1;
+  }
+}
+
+void jacobi_svd(Exec& ex, const double* M, int p, double tol, int cap, double* US, double* V, double* sig,
+                int* k_out, double* tail_out) {
+  TT_REQUIRE(p >= 1 && p <= 112, TT_ERR_ARG);
+  if (ex.dry) return;
+  const size_t smem = 2 * (size_t)p * p * 8;
+  TT_CUDA(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // algorithmic work: a nominal 6 sweeps of p(p-1)/2 pair rotations, each
+  // three length-p dot products and four length-p column updates
+  TT_KERNEL(ex, K_JACOBI, 6.0 * (p * (p - 1) / 2.0) * 18.0 * p, 8.0 * 4.0 * p * (double)p,
+            k_jacobi_svd<<<1, JAC_THREADS, smem, ex.s>>>(M, p, tol, cap, US, V, sig, k_out, tail_out,
+                                                         ex.dev_status, nullptr));
+}
+
+// ============================================================== maxvol
+constexpr int MV_THREADS = 1024;
+
+struct ArgMax {
+  double v;
+  long idx;
+};
+__device__ __forceinline__ ArgMax amax_better(ArgMax a, ArgMax b) {
+  // larger value wins; ties go to the smaller index
+  if (b.v > a.v || (b.v == a.v && b.idx < a.idx)) return b;
+  return a;
+}
+__device__ ArgMax block_argmax(ArgMax x, double* rv, long* ri) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMax y{__shfl_xor_sync(0xffffffffu, x.v, o), __shfl_xor_sync(0xffffffffu, x.idx, o)};
+    x = amax_better(x, y);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    rv[w] = x.v;
+    ri[w] = x.idx;
+  }
+  __syncthreads();
+  if (w == 0) {
+    ArgMax y{lane < nw ? rv[lane] : -1.0, lane < nw ? ri[lane] : 0x7fffffffffffffffL};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ArgMax z{__shfl_xor_sync(0xffffffffu, y.v, o), __shfl_xor_sync(0xffffffffu, y.idx, o)};
+      y = amax_better(y, z);
+    }
+    if (lane == 0) {
+      rv[32] = y.v;
+      ri[32] = y.idx;
+    }
+  }
+  __syncthreads();
+  return ArgMax{rv[32], ri[32]};
+}
+
+// W: n x r scratch (copy of U), B: n x r scratch, P: r x r scratch.
+__global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict__ U, int n, int r, double delta,
+                                                      int max_iter, double* W, double* B, double* P, int* I,
+                                                      unsigned* status) {
+  __shared__ double rv[33];
+  __shared__ long ri[33];
+  __shared__ int piv[128];
+  extern __shared__ unsigned char freeflag[];  // n bytes
+  for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) W[t] = U[t];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) freeflag[i] = 1;
+  __syncthreads();
+  // 1. partial-pivoting row choice, rows left in place
+  for (int k = 0; k < r; ++k) {
+    ArgMax best{-1.0, 0x7fffffffffffffffL};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (freeflag[i]) best = amax_better(best, ArgMax{fabs(W[i + (size_t)k * n]), (long)i});
+    best = block_argmax(best, rv, ri);
+    const int pr = (int)best.idx;
+    if (threadIdx.x == 0) {
+      piv[k] = pr;
+      freeflag[pr] = 0;
+    }
+    __syncthreads();
+    const double pv = W[pr + (size_t)k * n];
+    if (pv != 0.0 && k + 1 < r) {
+      // column k is read only (it is not used again), columns k+1.. updated
+      for (long t = threadIdx.x; t < (long)n * (r - k - 1); t += blockDim.x) {
+        const int i = int(t % n), c = k + 1 + int(t / n);
+        if (freeflag[i]) {
+          const double f = W[i + (size_t)k * n] / pv;
+          W[i + (size_t)c * n] = fma(-f, W[pr + (size_t)c * n], W[i + (size_t)c * n]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // 2. B = U P^{-1} with P = U[piv, :]: Gauss-Jordan on [P | I] in P (r x 2r)
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int i = t % r, j = t / r;
+    P[i + (size_t)j * r] = U[piv[i] + (size_t)j * n];
+    P[i + (size_t)(j + r) * r] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // Solve X P = U for X = B: equivalently P^T X^T = U^T.  Invert P by
+  // Gauss-Jordan with partial pivoting (row swaps recorded in the matrix).
+  __shared__ int gpiv;
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) {
+      int best = k;
+      double bv = fabs(P[k + (size_t)k * r]);
+      for (int i = k + 1; i < r; ++i) {
+        const double v = fabs(P[i + (size_t)k * r]);
+        if (v > bv) {
+          bv = v;
+          best = i;
+        }
+      }
+      gpiv = best;
+    }
+    __syncthreads();
+    const int pr = gpiv;
+    if (pr != k)
+      for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) {
+        const double a = P[k + (size_t)c * r];
+        P[k + (size_t)c * r] = P[pr + (size_t)c * r];
+        P[pr + (size_t)c * r] = a;
+      }
+    __syncthreads();
+    const double d = P[k + (size_t)k * r];
+    __syncthreads();
+    if (d != 0.0) {
+      for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) P[k + (size_t)c * r] /= d;
+    }
+    __syncthreads();
+    for (long t = threadIdx.x; t < (long)r * 2 * r; t += blockDim.x) {
+      const int i = int(t % r), c = int(t / r);
+      if (i != k) {
+        const double f = P[i + (size_t)k * r];
+        if (c != k) P[i + (size_t)c * r] = fma(-f, P[k + (size_t)c * r], P[i + (size_t)c * r]);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x)
+      if (i != k) P[i + (size_t)k * r] = 0.0;
+    __syncthreads();
+  }
+  // Pinv = P[:, r:2r];  B = U Pinv (n x r)
+  for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) {
+    const int i = int(t % n), j = int(t / n);
+    double s = 0.0;
+    for (int l = 0; l < r; ++l) s = fma(U[i + (size_t)l * n], P[l + (size_t)(j + r) * r], s);
+    B[t] = s;
+  }
+  for (int k = threadIdx.x; k < r; k += blockDim.x) I[k] = piv[k];
+  __syncthreads();
+  // 3. swap rows while some |B_ij| > 1 + delta (ties: smallest i*r + j)
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    ArgMax best{-1.0, 0x7fffffffffffffffL};
+    for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) {
+      const int i = int(t % n), j = int(t / n);
+      best = amax_better(best, ArgMax{fabs(B[t]), (long)i * r + j});
+    }
+    best = block_argmax(best, rv, ri);
+    if (best.v <= 1.0 + delta) break;
+    const int bi = int(best.idx / r), bj = int(best.idx % r);
+    const double pivv = B[bi + (size_t)bj * n];
+    // B -= B[:, j] (B[i, :] - e_j)^T / pivot ; use W as scratch for the column and row
+    for (int i = threadIdx.x; i < n; i += blockDim.x) W[i] = B[i + (size_t)bj * n];
+    for (int j = threadIdx.x; j < r; j += blockDim.x) W[n + j] = B[bi + (size_t)j * n] - (j == bj ? 1.0 : 0.0);
+    __syncthreads();
+    for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) {
+      const int i = int(t % n), j = int(t / n);
+      B[t] = fma(-W[i] / pivv, W[n + j], B[t]);
+    }
+    if (threadIdx.x == 0) I[bj] = bi;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && it >= max_iter) atomicOr(status, DEV_MAXVOL_NOCONV);
+}
+
+void maxvol(Exec& ex, const double* U, int n, int r, double delta, int max_iter, int* I) {
+  TT_REQUIRE(r >= 1 && r <= 128 && n >= r, TT_ERR_ARG);
+  Scope sc(*ex.ar);
+  double* W = ex.ar->get<double>((size_t)n * r + n + r);
+  double* B = ex.ar->get<double>((size_t)n * r);
+  double* P = ex.ar->get<double>((size_t)2 * r * r);
+  if (ex.dry) return;
+  const size_t smem = (size_t)n;
+  TT_REQUIRE(smem <= 200 * 1024, TT_ERR_ARG);
+  if (smem > 48 * 1024)
+    TT_CUDA(cudaFuncSetAttribute(k_maxvol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // algorithmic work: LU pivoting n r^2 plus B = U P^{-1} 2 n r^2
+  TT_KERNEL(ex, K_MAXVOL, 3.0 * n * (double)r * r, 8.0 * 3.0 * n * (double)r,
+            k_maxvol<<<1, MV_THREADS, smem, ex.s>>>(U, n, r, delta, max_iter, W, B, P, I, ex.dev_status));
+}
+
+}  // namespace ttfv

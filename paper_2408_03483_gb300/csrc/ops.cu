@@ -1,0 +1,486 @@
+// TT operations on device cores: periodic core stencils (Sec. 4.3.1 and the
+// (T - 1)/dx flux difference of Eq. SWE-system-TT), Gauss-point block sums,
+// TT sums by core concatenation, Khatri-Rao Hadamard cores, and TT rounding
+// (Sec. 3.2) by three exact routes chosen from the shape.
+#include <cmath>
+#include <algorithm>
+
+#include "tt_ops.cuh"
+
+namespace ttfv {
+
+// ============================================================== elementwise
+__global__ void k_scaled_copy(double* __restrict__ dst, const double* __restrict__ src, long n, double a) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    dst[t] = a * src[t];
+}
+__global__ void k_fill(double* __restrict__ dst, long n, double v) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) dst[t] = v;
+}
+
+static int grid_for(long n) { return std::max(1, std::min(ceil_div(n, 256), 1184)); }
+
+void scaled_copy(Exec& ex, double* dst, const double* src, long n, double alpha) {
+  if (n <= 0 || ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, n, 16.0 * n, k_scaled_copy<<<grid_for(n), 256, 0, ex.s>>>(dst, src, n, alpha));
+}
+void fill(Exec& ex, double* dst, long n, double v) {
+  if (n <= 0 || ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, 0, 8.0 * n, k_fill<<<grid_for(n), 256, 0, ex.s>>>(dst, n, v));
+}
+
+// ============================================================== launch accounting
+std::atomic<unsigned long long> g_launches{0};
+
+cudaEvent_t prof_begin(Exec& ex) {
+  if (!ex.prof || !ex.prof->on) return nullptr;
+  Prof& pf = *ex.prof;
+  cudaEvent_t a;
+  if (!pf.pool.empty()) {
+    a = pf.pool.back();
+    pf.pool.pop_back();
+  } else {
+    TT_CUDA(cudaEventCreate(&a));
+  }
+  TT_CUDA(cudaEventRecord(a, ex.s));
+  return a;
+}
+
+void prof_end(Exec& ex, cudaEvent_t a, int cls, double flops, double bytes) {
+  TT_CUDA(cudaGetLastError());
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ex.flops += flops;
+  ex.bytes += bytes;
+  if (!a) return;
+  Prof& pf = *ex.prof;
+  cudaEvent_t b;
+  if (!pf.pool.empty()) {
+    b = pf.pool.back();
+    pf.pool.pop_back();
+  } else {
+    TT_CUDA(cudaEventCreate(&b));
+  }
+  TT_CUDA(cudaEventRecord(b, ex.s));
+  pf.pending.push_back(Prof::Rec{cls, a, b, flops, bytes});
+}
+
+void prof_flush(Exec& ex) {
+  if (!ex.prof || ex.prof->pending.empty()) return;
+  Prof& pf = *ex.prof;
+  for (const Prof::Rec& r : pf.pending) {
+    float ms = 0.0f;
+    TT_CUDA(cudaEventSynchronize(r.b));
+    TT_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    pf.ms[r.cls] += ms;
+    pf.flops[r.cls] += r.flops;
+    pf.bytes[r.cls] += r.bytes;
+    pf.n[r.cls] += 1;
+    pf.pool.push_back(r.a);
+    pf.pool.push_back(r.b);
+  }
+  pf.pending.clear();
+}
+
+// ============================================================== core stencils
+// out_o[i, k] = sum_t c_{o,t} * in[base_{o,t} + (i + s_{o,t}) mod n, k]
+// for the n rows of output o; one launch produces every output.
+__global__ void k_stencil(StencilSet st, const double* __restrict__ in, long ldin, int n, int r) {
+  const int o = blockIdx.z;
+  const StencilOut& so = st.out[o];
+  for (int k = blockIdx.y; k < r; k += gridDim.y) {
+    const double* col = in + (size_t)k * ldin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      double acc = 0.0;
+      for (int t = 0; t < so.ntaps; ++t) {
+        int ii = i + so.shift[t];
+        ii %= n;
+        if (ii < 0) ii += n;
+        acc = fma(so.coef[t], col[so.base[t] + ii], acc);
+      }
+      so.dst[(size_t)so.row0 + i + (size_t)k * so.ld] = acc;
+    }
+  }
+}
+
+void stencil(Exec& ex, const StencilSet& st, const double* in, long ldin, int n, int r) {
+  if (r <= 0 || n <= 0) return;
+  int taps = 0;
+  for (int o = 0; o < st.nout; ++o) taps += st.out[o].ntaps;
+  if (ex.dry) return;
+  TT_REQUIRE(st.nout >= 1 && st.nout <= kMaxStencilOut, TT_ERR_ARG);
+  dim3 grid(ceil_div(n, 256), std::min(r, 1024), st.nout);
+  // algorithmic bytes: each input column read once, each output written once
+  // (a stacked input of several blocks is read block by block)
+  int maxbase = 0;
+  for (int o = 0; o < st.nout; ++o)
+    for (int t = 0; t < st.out[o].ntaps; ++t) maxbase = std::max(maxbase, st.out[o].base[t]);
+  const double in_rows = (double)n * (1 + maxbase / std::max(n, 1));
+  TT_KERNEL(ex, K_STENCIL, 2.0 * n * (double)r * taps, 8.0 * r * (in_rows + (double)n * st.nout),
+            k_stencil<<<grid, 256, 0, ex.s>>>(st, in, ldin, n, r));
+}
+
+// ============================================================== Khatri-Rao cores
+// Z[i, a*r2 + b] = X[i, a] * Y[i, b] (row-wise Kronecker; the TT Hadamard cores)
+__global__ void k_khatri_rao(const double* __restrict__ X, int r1, const double* __restrict__ Y, int r2, int n,
+                             double* __restrict__ Z) {
+  const long total = (long)n * r1 * r2;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int i = int(t % n);
+    const long c = t / n;
+    const int a = int(c / r2), b = int(c % r2);
+    Z[t] = X[i + (size_t)a * n] * Y[i + (size_t)b * n];
+  }
+}
+
+void khatri_rao(Exec& ex, const double* X, int r1, const double* Y, int r2, int n, double* Z) {
+  if (ex.dry) return;
+  const long total = (long)n * r1 * r2;
+  TT_KERNEL(ex, K_OTHER, (double)total, 8.0 * ((double)n * (r1 + r2) + (double)total),
+            k_khatri_rao<<<grid_for(total), 256, 0, ex.s>>>(X, r1, Y, r2, n, Z));
+}
+
+// ============================================================== sketch matrix
+// Rademacher entries from SplitMix64 of (seed, index): a fixed deterministic
+// test matrix for the randomized range finder.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void k_rademacher(double* __restrict__ O, long n, unsigned long long seed) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    O[t] = (splitmix64(seed * 0x100000000ull + (unsigned long long)t) >> 63) ? 1.0 : -1.0;
+}
+
+// ============================================================== transposes
+__global__ void k_transpose(const double* __restrict__ X, int m, int n, long ldx, double* __restrict__ Y, long ldy) {
+  __shared__ double tile[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int i = i0 + threadIdx.x, j = j0 + dy;
+    tile[dy][threadIdx.x] = (i < m && j < n) ? X[i + (size_t)j * ldx] : 0.0;
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int j = j0 + threadIdx.x, i = i0 + dy;
+    if (i < m && j < n) Y[j + (size_t)i * ldy] = tile[threadIdx.x][dy];
+  }
+}
+// Y (n x m) = X^T for X (m x n)
+void transpose(Exec& ex, const double* X, int m, int n, long ldx, double* Y, long ldy) {
+  if (ex.dry) return;
+  dim3 grid(ceil_div(m, 32), ceil_div(n, 32));
+  TT_KERNEL(ex, K_OTHER, 0, 16.0 * m * (double)n, k_transpose<<<grid, dim3(32, 8), 0, ex.s>>>(X, m, n, ldx, Y, ldy));
+}
+
+// ============================================================== sync helpers
+int fetch_int(Exec& ex, const int* d) {
+  if (ex.dry) return -1;
+  TT_CUDA(cudaMemcpyAsync(ex.h_pinned, d, sizeof(int), cudaMemcpyDeviceToHost, ex.s));
+  TT_CUDA(cudaStreamSynchronize(ex.s));
+  ex.syncs++;
+  prof_flush(ex);
+  return ex.h_pinned[0];
+}
+void fetch_doubles(Exec& ex, const double* d, int n, double* out) {
+  if (ex.dry) {
+    for (int i = 0; i < n; ++i) out[i] = 0.0;
+    return;
+  }
+  TT_REQUIRE(n <= 16, TT_ERR_ARG);
+  TT_CUDA(cudaMemcpyAsync(ex.h_pinned_d, d, sizeof(double) * n, cudaMemcpyDeviceToHost, ex.s));
+  TT_CUDA(cudaStreamSynchronize(ex.s));
+  ex.syncs++;
+  prof_flush(ex);
+  for (int i = 0; i < n; ++i) out[i] = ex.h_pinned_d[i];
+}
+
+// ============================================================== TT sums
+void tt_concat(Exec& ex, const std::vector<Term>& terms, TT& out) {
+  int off = 0;
+  for (const Term& t : terms) {
+    TT_REQUIRE(t.x.n1 == out.n1 && t.x.n2 == out.n2, TT_ERR_ARG);
+    TT_REQUIRE(off + t.x.r <= out.cap, TT_ERR_ARG);
+    scaled_copy(ex, out.a + (size_t)off * out.n1, t.x.a, (long)out.n1 * t.x.r, t.c);
+    scaled_copy(ex, out.b + (size_t)off * out.n2, t.x.b, (long)out.n2 * t.x.r, 1.0);
+    off += t.x.r;
+  }
+  out.r = off;
+}
+
+int total_rank(const std::vector<Term>& terms) {
+  int r = 0;
+  for (const Term& t : terms) r += t.x.r;
+  return r;
+}
+
+// ============================================================== rounding
+// residual target of the range finder: 1e-3 of the truncation tolerance, never
+// looser than 1e-11 (so the result stays within 1e-10 of the exact truncated
+// SVD) nor tighter than FP64 round-off of the residual itself
+static double qb_target(double tol) { return std::max(std::min(1e-3 * tol, 1e-11), 4e-15); }
+
+static void finish_counts(Exec& ex, int k, int cap, int rin) {
+  ex.rounds++;
+  if (k == cap && rin > cap) ex.cap_hits++;
+}
+
+// (i) Factored route, R <= 112 and R <= min(n1, n2): QR of both cores
+// (TSQR), SVD of the R x R product of the triangular factors.
+static RoundInfo round_factored(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol,
+                                int cap, TT& Y) {
+  Scope sc(*ex.ar);
+  QRTree ta, tb;
+  tsqr(ex, A, n1, R, n1, ta);
+  tsqr(ex, B, n2, R, n2, tb);
+  double* M = ex.ar->get<double>((size_t)R * R);
+  // M = R_A R_B^T
+  gemm(ex, R, R, R, 1.0, ta.R, 1, R, tb.R, R, 1, 0.0, M, R);
+  double* US = ex.ar->get<double>((size_t)R * R);
+  double* V = ex.ar->get<double>((size_t)R * R);
+  double* sig = ex.ar->get<double>(R);
+  int* kd = ex.ar->get<int>(4);
+  double* tail = ex.ar->get<double>(2);
+  jacobi_svd(ex, M, R, tol, cap, US, V, sig, kd, tail);
+  int k = fetch_int(ex, kd);
+  if (ex.dry) k = std::min(cap, R);
+  double tl[2];
+  fetch_doubles(ex, tail, 2, tl);
+  tsqr_apply(ex, ta, US, k, R, Y.a, Y.n1);
+  tsqr_apply(ex, tb, V, k, R, Y.b, Y.n2);
+  Y.r = k;
+  finish_counts(ex, k, cap, R);
+  return RoundInfo{k, tl[0], tl[1], 0.0};
+}
+
+// (ii) Full-matrix routes on an explicit Y (n1 x n2): with s = min(n1, n2),
+// the working matrix W0 is Y (s = n1) or Y^T (s = n2).
+//   s <= 112: QR of W0^T (l x s) and SVD of R^T -- exact.
+//   s  > 112: randomized range finder with an explicit residual check
+//             ||W0 - Q Q^T W0||_F <= tau ||W0||_F, tau = qb_target(tol),
+//             then QR of (Q^T W0)^T and SVD of the p x p factor (p <= 112).
+RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int cap, TT& Y) {
+  Scope sc(*ex.ar);
+  const bool tr = n1 > n2;
+  const int s = tr ? n2 : n1, l = tr ? n1 : n2;
+  // W0(i, j), i < s, j < l
+  const long wrs = tr ? n1 : 1, wcs = tr ? 1 : n1;
+  double* Aw = tr ? Y.b : Y.a;  // s-side output core
+  double* Bw = tr ? Y.a : Y.b;  // l-side output core
+  double* kbuf = ex.ar->get<double>(4);
+  int* kd = ex.ar->get<int>(4);
+  double* tail = ex.ar->get<double>(2);
+  if (s <= 112) {
+    // W0^T (l x s) explicitly, col-major
+    double* WT = ex.ar->get<double>((size_t)l * s);
+    if (tr)
+      scaled_copy(ex, WT, Yf, (long)l * s, 1.0);  // Y itself is n1 x n2 = l x s
+    else
+      transpose(ex, Yf, n1, n2, n1, WT, l);
+    QRTree tw;
+    tsqr(ex, WT, l, s, l, tw);
+    double* M = ex.ar->get<double>((size_t)s * s);
+    transpose(ex, tw.R, s, s, s, M, s);  // M = R^T
+    double* US = ex.ar->get<double>((size_t)s * s);
+    double* V = ex.ar->get<double>((size_t)s * s);
+    double* sig = ex.ar->get<double>(s);
+    jacobi_svd(ex, M, s, tol, cap, US, V, sig, kd, tail);
+    int k = fetch_int(ex, kd);
+    if (ex.dry) k = std::min(cap, s);
+    double tl[2];
+    fetch_doubles(ex, tail, 2, tl);
+    // W0 = R^T Q_W^T = U S V^T Q_W^T: s-side core U S, l-side core Q_W V
+    scaled_copy(ex, Aw, US, (long)s * k, 1.0);
+    tsqr_apply(ex, tw, V, k, s, Bw, l);
+    Y.r = k;
+    finish_counts(ex, k, cap, s);
+    return RoundInfo{k, tl[0], tl[1], 0.0};
+  }
+  // ---- randomized range finder (s > 112)
+  const double tau = qb_target(tol);
+  sumsq(ex, Yf, n1, n2, n1, kbuf);
+  double nrm2[1];
+  fetch_doubles(ex, kbuf, 1, nrm2);
+  int p = std::min({112, s, ((std::max(2 * cap, cap + 16) + 7) / 8) * 8});
+  double* Om = ex.ar->get<double>((size_t)l * 112);
+  double* S = ex.ar->get<double>((size_t)s * 112);
+  double* Q = ex.ar->get<double>((size_t)s * 112);
+  double* WT = ex.ar->get<double>((size_t)l * 112);
+  double* E = ex.ar->get<double>((size_t)s * l);
+  double* I = ex.ar->get<double>((size_t)112 * 112);
+  double resid2 = 0.0;
+  for (int attempt = 0;; ++attempt) {
+    ex.qb_attempts++;
+    const size_t mk = ex.ar->mark();
+    if (!ex.dry)
+      TT_KERNEL(ex, K_OTHER, 0, 8.0 * l * p,
+                k_rademacher<<<grid_for((long)l * p), 256, 0, ex.s>>>(Om, (long)l * p, 0x7A3Dull + attempt));
+    // S = W0 Om (s x p)
+    gemm(ex, s, p, l, 1.0, Yf, wrs, wcs, Om, 1, l, 0.0, S, s);
+    QRTree ts;
+    tsqr(ex, S, s, p, s, ts);
+    // Q = Q_S [I_p; 0]
+    set_identity(ex, I, p);
+    tsqr_apply(ex, ts, I, p, p, Q, s);
+    // WT = W0^T Q (l x p)
+    gemm(ex, l, p, s, 1.0, Yf, wcs, wrs, Q, 1, s, 0.0, WT, l);
+    // E = W0 - Q WT^T
+    if (tr)
+      transpose(ex, Yf, n1, n2, n1, E, s);
+    else
+      scaled_copy(ex, E, Yf, (long)s * l, 1.0);
+    gemm(ex, s, l, p, -1.0, Q, 1, s, WT, l, 1, 1.0, E, s);
+    sumsq(ex, E, s, l, s, kbuf + 1);
+    double r2[1];
+    fetch_doubles(ex, kbuf + 1, 1, r2);
+    resid2 = r2[0];
+    const bool ok = resid2 <= tau * tau * nrm2[0];
+    if (ok || p >= std::min(112, s) || ex.dry) {
+      if (!ok && !ex.dry) ex.qb_uncertified++;
+      // keep S/ts scratch alive: release nothing allocated after mark
+      (void)mk;
+      break;
+    }
+    ex.ar->reset(mk);
+    p = std::min({112, s, 2 * p});
+  }
+  // SVD of Q^T W0 = WT^T = (Q_W R_W)^T = R_W^T Q_W^T
+  QRTree tw;
+  tsqr(ex, WT, l, p, l, tw);
+  double* M = ex.ar->get<double>((size_t)p * p);
+  transpose(ex, tw.R, p, p, p, M, p);
+  double* US = ex.ar->get<double>((size_t)p * p);
+  double* V = ex.ar->get<double>((size_t)p * p);
+  double* sig = ex.ar->get<double>(p);
+  jacobi_svd(ex, M, p, tol, cap, US, V, sig, kd, tail);
+  int k = fetch_int(ex, kd);
+  if (ex.dry) k = std::min(cap, p);
+  double tl[2];
+  fetch_doubles(ex, tail, 2, tl);
+  // s-side core Q (U S)_k, l-side core Q_W V_k
+  gemm(ex, s, k, p, 1.0, Q, 1, s, US, 1, p, 0.0, Aw, s);
+  tsqr_apply(ex, tw, V, k, p, Bw, l);
+  Y.r = k;
+  finish_counts(ex, k, cap, s);
+  return RoundInfo{k, std::sqrt(tl[0] * tl[0] + resid2), tl[1], std::sqrt(resid2)};
+}
+
+RoundInfo round_cores(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol, int cap,
+                      TT& Y) {
+  TT_REQUIRE(R >= 1 && cap >= 1 && Y.cap >= std::min(cap, std::max(1, std::min(n1, n2))), TT_ERR_ARG);
+  if (R <= 112 && R <= std::min(n1, n2)) return round_factored(ex, A, B, n1, n2, R, tol, cap, Y);
+  Scope sc(*ex.ar);
+  double* Yf = ex.ar->get<double>((size_t)n1 * n2);
+  gemm(ex, n1, n2, R, 1.0, A, 1, n1, B, n2, 1, 0.0, Yf, n1);
+  return round_full(ex, Yf, n1, n2, tol, cap, Y);
+}
+
+RoundInfo round_tt(Exec& ex, const TT& X, double tol, int cap, TT& Y) {
+  return round_cores(ex, X.a, X.b, X.n1, X.n2, X.r, tol, cap, Y);
+}
+
+RoundInfo round_sum(Exec& ex, const std::vector<Term>& terms, double tol, int cap, TT& Y) {
+  TT_REQUIRE(!terms.empty(), TT_ERR_ARG);
+  Scope sc(*ex.ar);
+  const int n1 = terms[0].x.n1, n2 = terms[0].x.n2;
+  const int R = total_rank(terms);
+  TT cat;
+  cat.n1 = n1;
+  cat.n2 = n2;
+  cat.cap = R;
+  cat.a = ex.ar->get<double>((size_t)n1 * R);
+  cat.b = ex.ar->get<double>((size_t)n2 * R);
+  tt_concat(ex, terms, cat);
+  return round_tt(ex, cat, tol, cap, Y);
+}
+
+RoundInfo round_hadamard(Exec& ex, const TT& X, const TT& Z, double tol, int cap, TT& Y) {
+  TT_REQUIRE(X.n1 == Z.n1 && X.n2 == Z.n2, TT_ERR_ARG);
+  Scope sc(*ex.ar);
+  const int n1 = X.n1, n2 = X.n2, R = X.r * Z.r;
+  if (R <= 112 && R <= std::min(n1, n2)) {
+    double* A = ex.ar->get<double>((size_t)n1 * R);
+    double* B = ex.ar->get<double>((size_t)n2 * R);
+    khatri_rao(ex, X.a, X.r, Z.a, Z.r, n1, A);
+    khatri_rao(ex, X.b, X.r, Z.b, Z.r, n2, B);
+    return round_cores(ex, A, B, n1, n2, R, tol, cap, Y);
+  }
+  double* Yf = ex.ar->get<double>((size_t)n1 * n2);
+  form_hadamard_full(ex, n1, n2, X.a, X.r, X.b, Z.a, Z.r, Z.b, Yf, n1);
+  return round_full(ex, Yf, n1, n2, tol, cap, Y);
+}
+
+// ============================================================== misc
+__global__ void k_set_identity(double* I, int p) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p * p; t += gridDim.x * blockDim.x)
+    I[t] = ((t % p) == (t / p)) ? 1.0 : 0.0;
+}
+void set_identity(Exec& ex, double* I, int p) {
+  if (ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, 0, 8.0 * p * p, k_set_identity<<<grid_for((long)p * p), 256, 0, ex.s>>>(I, p));
+}
+
+// sum_{i,j} X = (1^T A)(B^T 1) and ||X||_F^2 = sum (A^T A) o (B^T B): one CTA.
+__global__ void k_tt_sum_norm(const double* __restrict__ A, const double* __restrict__ B, int n1, int n2, int r,
+                              double* out) {
+  __shared__ double ca[128], cb[128];
+  __shared__ double red[33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = w; k < r; k += nw) {
+    double sa = 0.0, sb = 0.0;
+    for (int i = lane; i < n1; i += 32) sa += A[i + (size_t)k * n1];
+    for (int j = lane; j < n2; j += 32) sb += B[j + (size_t)k * n2];
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if (lane == 0) {
+      ca[k] = sa;
+      cb[k] = sb;
+    }
+  }
+  __syncthreads();
+  double s = 0.0;
+  for (int k = threadIdx.x; k < r; k += blockDim.x) s = fma(ca[k], cb[k], s);
+  // block reduce
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) red[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    out[0] = t;
+  }
+  __syncthreads();
+  // Frobenius: sum_{k,l} (A^T A)_{kl} (B^T B)_{kl}
+  double f = 0.0;
+  for (int kl = w; kl < r * r; kl += nw) {
+    const int k = kl % r, l2 = kl / r;
+    double ga = 0.0, gb = 0.0;
+    for (int i = lane; i < n1; i += 32) ga = fma(A[i + (size_t)k * n1], A[i + (size_t)l2 * n1], ga);
+    for (int j = lane; j < n2; j += 32) gb = fma(B[j + (size_t)k * n2], B[j + (size_t)l2 * n2], gb);
+    for (int o = 16; o > 0; o >>= 1) {
+      ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      gb += __shfl_xor_sync(0xffffffffu, gb, o);
+    }
+    if (lane == 0) f = fma(ga, gb, f);
+  }
+  __syncthreads();
+  if (lane == 0) red[w] = f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    out[1] = t > 0.0 ? sqrt(t) : 0.0;
+  }
+}
+
+void tt_sum_norm(Exec& ex, const TT& X, double* out_dev) {
+  TT_REQUIRE(X.r <= 128, TT_ERR_ARG);
+  if (ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, 2.0 * (X.n1 + X.n2) * (double)X.r * X.r, 8.0 * (X.n1 + X.n2) * (double)X.r,
+            k_tt_sum_norm<<<1, 1024, 0, ex.s>>>(X.a, X.b, X.n1, X.n2, X.r, out_dev));
+}
+
+}  // namespace ttfv

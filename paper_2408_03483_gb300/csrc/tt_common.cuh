@@ -1,0 +1,177 @@
+// Shared declarations of the TT finite-volume CUDA library (sm_103a, FP64 path).
+//
+// A 2-D TT X[i, j] = sum_k a[k * n1 + i] * b[k * n2 + j]: both cores column-major
+// with the mode index fastest (the paper's G1(i) and G2(j)^T, Sec. 3.1).
+#pragma once
+#include <cuda_runtime.h>
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tt_fv.h"
+
+namespace ttfv {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  tt_status code;
+};
+
+#define TT_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) throw ::ttfv::Error{TT_ERR_CUDA}; \
+  } while (0)
+#define TT_LAUNCH() TT_CUDA(cudaGetLastError())
+#define TT_REQUIRE(cond, code) \
+  do {                         \
+    if (!(cond)) throw ::ttfv::Error{code}; \
+  } while (0)
+
+// Device-side status bits (latched in a device word, read at sync points).
+enum : unsigned {
+  DEV_JACOBI_NOCONV = 1u,
+  DEV_MAXVOL_NOCONV = 2u,
+  DEV_SHAPE = 4u,
+};
+
+// ---------------------------------------------------------------- workspace
+// Bump allocator over caller-provided device memory (256-byte aligned).
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  size_t peak = 0;
+  bool dry = false;  // sizing pass: count only
+  template <typename T>
+  T* get(size_t n) {
+    size_t bytes = (n * sizeof(T) + 255) & ~size_t(255);
+    size_t o = off;
+    off += bytes;
+    if (off > peak) peak = off;
+    if (dry) return reinterpret_cast<T*>(uintptr_t(0x100) + o);
+    if (off > cap) throw Error{TT_ERR_OOM};
+    return reinterpret_cast<T*>(base + o);
+  }
+  size_t mark() const { return off; }
+  void reset(size_t m) { off = m; }
+};
+
+struct Scope {  // restores the arena on exit
+  Arena& a;
+  size_t m;
+  explicit Scope(Arena& ar) : a(ar), m(ar.mark()) {}
+  ~Scope() { a.reset(m); }
+};
+
+// ---------------------------------------------------------------- profiling
+// Kernel classes for the opt-in per-launch event timing (TT_K_* in the header).
+enum KClass : int {
+  K_GEMM = TT_K_GEMM,
+  K_FORM = TT_K_FORM,
+  K_QR = TT_K_QR,
+  K_QR_APPLY = TT_K_QR_APPLY,
+  K_JACOBI = TT_K_JACOBI,
+  K_MAXVOL = TT_K_MAXVOL,
+  K_EVAL = TT_K_EVAL,
+  K_STENCIL = TT_K_STENCIL,
+  K_OTHER = TT_K_OTHER,
+  K_NCLASS = TT_K_NCLASS
+};
+struct Prof {
+  bool on = false;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[K_NCLASS] = {}, flops[K_NCLASS] = {}, bytes[K_NCLASS] = {};
+  long long n[K_NCLASS] = {};
+};
+extern std::atomic<unsigned long long> g_launches;
+
+// A TT held by the library: device cores with host-known shape and rank.
+struct TT {
+  int n1 = 0, n2 = 0, r = 0, cap = 0;
+  double* a = nullptr;
+  double* b = nullptr;
+};
+
+// Execution context of one call chain.
+struct Exec {
+  cudaStream_t s = nullptr;
+  Arena* ar = nullptr;
+  unsigned* dev_status = nullptr;   // device status word
+  int* h_pinned = nullptr;          // small pinned host buffer for syncs
+  double* h_pinned_d = nullptr;
+  bool dry = false;                 // workspace sizing pass: no launches
+  // counters (host)
+  long long rounds = 0, qb_attempts = 0, qb_uncertified = 0, syncs = 0;
+  long long jacobi_sweeps = 0, cross_calls = 0, cross_sweeps = 0;
+  long long taylor_iters = 0, cap_hits = 0;
+  double flops = 0.0, bytes = 0.0;
+  Prof* prof = nullptr;             // per-class event timing when prof->on
+};
+
+// Bracket one kernel launch: counts it, checks the launch, adds its
+// algorithmic flops/bytes to the totals and, when profiling, times it.
+cudaEvent_t prof_begin(Exec& ex);
+void prof_end(Exec& ex, cudaEvent_t a, int cls, double flops, double bytes);
+void prof_flush(Exec& ex);  // after a stream sync: accumulate finished records
+#define TT_KERNEL(ex, cls, flops, bytes, ...)                     \
+  do {                                                            \
+    cudaEvent_t _tt_a = ::ttfv::prof_begin(ex);                   \
+    __VA_ARGS__;                                                  \
+    ::ttfv::prof_end(ex, _tt_a, cls, (double)(flops), (double)(bytes)); \
+  } while (0)
+
+// ---------------------------------------------------------------- helpers
+inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
+
+// Copy n ints/doubles from device to the pinned buffer and wait (a sync point).
+int fetch_int(Exec& ex, const int* d);
+void fetch_doubles(Exec& ex, const double* d, int n, double* out);
+
+// ---------------------------------------------------------------- kernels (la.cu)
+// C[i,j] = alpha * sum_k A(i,k) B(k,j) + beta * C[i,j]; A(i,k) = A[i*ars + k*acs] etc.
+void gemm(Exec& ex, int M, int N, int K, double alpha, const double* A, long ars, long acs,
+          const double* B, long brs, long bcs, double beta, double* C, long ldc);
+// Y[i,j] = (sum_k A1[i,k]B1[j,k]) * (sum_l A2[i,l]B2[j,l]); cores column-major.
+void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, const double* B1,
+                        const double* A2, int r2, const double* B2, double* Y, long ldy);
+// sum of squares of an m x n column-major matrix -> device double
+void sumsq(Exec& ex, const double* X, int m, int n, long ld, double* out);
+
+// Householder TSQR of a tall m x p matrix (m >= p, p <= 112).
+struct QRTree {
+  int m = 0, p = 0, levels = 0;
+  std::vector<int> mrows;      // rows of the input of each level
+  std::vector<int> mb;         // block rows per level
+  std::vector<int> nb;         // blocks per level
+  std::vector<double*> V;      // per level: nb*mb x p reflectors (unit diag implicit)
+  std::vector<double*> tau;    // per level: nb x p
+  double* R = nullptr;         // final p x p upper triangle (ld p)
+};
+void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t);
+// Out (m x k, ld ldo) = Q [C; 0] with C p x k (ld ldc).
+void tsqr_apply(Exec& ex, const QRTree& t, const double* C, int k, long ldc, double* Out, long ldo);
+
+// One-sided Jacobi SVD of a square p x p matrix M (ld p, p <= 112).  Writes
+// the singular values sorted descending to sig (device, p), U*S (p x p, ld p)
+// and V (p x p, ld p) column-sorted alike, and the truncation rank for
+// (tol, cap) to *k_out (device).  tail_out[0] = discarded Frobenius norm.
+void jacobi_svd(Exec& ex, const double* M, int p, double tol, int cap, double* US, double* V,
+                double* sig, int* k_out, double* tail_out);
+
+// Maximum-volume rows of U (n x r, ld n): LU-pivoted start then swaps until
+// max|B| <= 1 + delta (ties to the smallest row-major index).  I (device, r).
+void maxvol(Exec& ex, const double* U, int n, int r, double delta, int max_iter, int* I);
+
+// Elementwise helpers (ops.cu)
+void scaled_copy(Exec& ex, double* dst, const double* src, long n, double alpha);
+void fill(Exec& ex, double* dst, long n, double v);
+
+}  // namespace ttfv

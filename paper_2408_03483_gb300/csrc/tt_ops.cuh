@@ -1,0 +1,69 @@
+// TT-level operations shared by the solver, the cross and the C ABI.
+#pragma once
+#include <vector>
+
+#include "tt_common.cuh"
+
+namespace ttfv {
+
+constexpr int kMaxStencilOut = 8;
+constexpr int kMaxTaps = 10;
+
+struct StencilOut {
+  double* dst = nullptr;  // output core (column-major)
+  long ld = 0;            // its leading dimension
+  int row0 = 0;           // first output row (stacked blocks)
+  int ntaps = 0;
+  int shift[kMaxTaps] = {};
+  int base[kMaxTaps] = {};  // input row offset of the tap's block
+  double coef[kMaxTaps] = {};
+};
+struct StencilSet {
+  int nout = 0;
+  StencilOut out[kMaxStencilOut];
+};
+
+struct Term {
+  double c;
+  TT x;
+};
+
+struct RoundInfo {
+  int rank;
+  double err;    // discarded Frobenius norm (incl. range-finder residual)
+  double norm;   // Frobenius norm of the input
+  double resid;  // range-finder residual (0 on exact routes)
+};
+
+void stencil(Exec& ex, const StencilSet& st, const double* in, long ldin, int n, int r);
+void khatri_rao(Exec& ex, const double* X, int r1, const double* Y, int r2, int n, double* Z);
+void transpose(Exec& ex, const double* X, int m, int n, long ldx, double* Y, long ldy);
+void set_identity(Exec& ex, double* I, int p);
+void tt_concat(Exec& ex, const std::vector<Term>& terms, TT& out);
+int total_rank(const std::vector<Term>& terms);
+void tt_sum_norm(Exec& ex, const TT& X, double* out_dev);
+
+RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int cap, TT& Y);
+RoundInfo round_cores(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol, int cap,
+                      TT& Y);
+RoundInfo round_tt(Exec& ex, const TT& X, double tol, int cap, TT& Y);
+RoundInfo round_sum(Exec& ex, const std::vector<Term>& terms, double tol, int cap, TT& Y);
+RoundInfo round_hadamard(Exec& ex, const TT& X, const TT& Z, double tol, int cap, TT& Y);
+
+// Taylor-series reciprocal (Algorithm 1); returns iterations, sets *noconv.
+int reciprocal(Exec& ex, const TT& x, double tol, int cap, int max_iter, TT& y, bool* noconv);
+
+// Cross interpolation (cross.cu)
+struct CrossFn {
+  int fn = 0;
+  const TT* in = nullptr;
+  int nin = 0;
+  double prm[4] = {0, 0, 0, 0};
+};
+int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, int cap, int kick,
+          int max_sweeps, unsigned seed, TT& y);
+
+// Linear reconstruction on cores (fv.cu)
+void recon_linear(Exec& ex, const TT& x, int direction, int scheme, TT& qm, TT& qp);
+
+}  // namespace ttfv

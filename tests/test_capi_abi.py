@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function
+include/tt_fv.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared_functions():
+    with open(os.path.join(ROOT, "include", "tt_fv.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(tt_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_03483_gb300 import build, capi
+    if not os.path.exists(build.lib_path()):
+        build.build()
+    return capi.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("tt_fv_init", "tt_fv_step", "tt_fv_stage", "tt_round", "tt_cross", "tt_reciprocal"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2408_03483_gb300 import capi
+    names = _declared_functions()
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding covers exactly the header
+    assert sorted(capi.SIGNATURES) == names
+
+
+def test_workspace_queries_without_gpu(lib):
+    from paper_2408_03483_gb300 import capi
+    assert lib.tt_round_workspace_size(256, 768, 64, 32) > 0
+    assert lib.tt_round_workspace_size(0, 768, 64, 32) == 0
+    p = capi.tt_fv_params(1, 2, 256, 256, 1.0, 1.0, 9.81, 1.0, 0.0, 4.7e-4, 1e-8, 32, 0, 0, 4, 10, 50, 0)
+    assert lib.tt_fv_workspace_size(ctypes.byref(p)) > 0
+    bad = capi.tt_fv_params(1, 2, 256, 256, 1.0, 1.0, 9.81, 1.0, 0.0, -1.0, 1e-8, 32, 0, 0, 4, 10, 50, 0)
+    assert lib.tt_fv_workspace_size(ctypes.byref(bad)) == 0
+
+
+def test_argument_errors_return_codes(lib):
+    from paper_2408_03483_gb300 import capi
+    x = capi.tt2(0, 0, 0, 0, None, None)
+    y = capi.tt2(0, 0, 0, 0, None, None)
+    assert lib.tt_round(ctypes.byref(x), 1e-8, 4, ctypes.byref(y), None, None, 0, None) == capi.TT_ERR_ARG
+    h = ctypes.c_void_p()
+    assert lib.tt_fv_init(None, None, None, 0, None, ctypes.byref(h)) == capi.TT_ERR_ARG
+    assert lib.tt_fv_stage(None, 0) == capi.TT_ERR_ARG
