@@ -153,7 +153,10 @@ tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* out);
 void tt_fv_destroy(tt_fv_ctx* ctx);
 
 /* Enable (1) or disable (0) CUDA-event timing of every kernel launch of the
- * context, accumulated per kernel class; costs two event records per launch. */
+ * context, accumulated per kernel class.  While enabled, the stage's
+ * independent tasks run one after another on the context stream (so a
+ * launch's time is its own device time) and two events are recorded per
+ * launch: a profiled stage is slower than an unprofiled one. */
 tt_status tt_fv_profile(tt_fv_ctx* ctx, int32_t enable);
 /* Copy the accumulated per-class profile (TT_K_NCLASS entries) and, if
  * reset != 0, clear it. */

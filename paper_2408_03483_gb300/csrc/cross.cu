@@ -235,7 +235,7 @@ static void small_solve(Exec& ex, const double* P, int k, const double* G, int c
   if (ex.dry) return;
   const size_t smem = (size_t)k * (k + c) * 8;
   TT_REQUIRE(smem <= 220 * 1024, TT_ERR_ARG);
-  TT_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  smem_attr_once(k_small_solve);
   TT_KERNEL(ex, K_OTHER, 2.0 / 3.0 * k * (double)k * k + 2.0 * k * (double)k * c, 8.0 * k * (double)(k + 2 * c),
             k_small_solve<<<1, 1024, smem, ex.s>>>(P, k, G, c, X));
 }

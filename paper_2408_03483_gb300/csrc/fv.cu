@@ -151,6 +151,7 @@ struct Solver {
   int h_int[16];
   double h_dbl[16];
   Prof prof;
+  StreamPool pool;
   ~Solver() {
     for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
     for (const Prof::Rec& r : prof.pending) {
@@ -162,89 +163,89 @@ struct Solver {
 
 static int nq_of(int recon) { return recon == TT_UP3 ? 2 : 3; }
 
-// faces of one field for direction d (0: x, 1: y)
-static void face_tts(Solver& S, Exec& ex, const TT& q, int d, int fieldc, unsigned seed, TT& qm, TT& qp) {
-  const tt_fv_params& p = S.p;
-  const int n1 = q.n1, n2 = q.n2, nq = S.nq, cap = p.rank_cap;
+// Linear (Upwind3/Upwind5) faces of one field for direction d (0: x, 1: y)
+static void faces_linear(Solver& S, Exec& ex, const TT& q, int d, TT& qm, TT& qp) {
+  const int n1 = q.n1, n2 = q.n2, nq = S.nq;
   const int f1 = d == 0 ? n1 : nq * n1, f2 = d == 0 ? nq * n2 : n2;
-  const double dx = p.lx / p.nx, dy = p.ly / p.ny;
-  if (p.recon != TT_WENO5) {
-    qm.n1 = qp.n1 = f1;
-    qm.n2 = qp.n2 = f2;
-    qm.cap = qp.cap = q.r;
-    if (d == 0) {
-      qm.a = ex.ar->get<double>((size_t)n1 * q.r);
-      qp.a = ex.ar->get<double>((size_t)n1 * q.r);
-      qm.b = ex.ar->get<double>((size_t)f2 * q.r);
-    } else {
-      qm.b = ex.ar->get<double>((size_t)n2 * q.r);
-      qp.b = ex.ar->get<double>((size_t)n2 * q.r);
-      qm.a = ex.ar->get<double>((size_t)f1 * q.r);
-    }
-    recon_linear(ex, q, d, p.recon, qm, qp);
-    return;
+  qm.n1 = qp.n1 = f1;
+  qm.n2 = qp.n2 = f2;
+  qm.cap = qp.cap = q.r;
+  if (d == 0) {
+    qm.a = ex.ar->get<double>((size_t)n1 * q.r);
+    qp.a = ex.ar->get<double>((size_t)n1 * q.r);
+    qm.b = ex.ar->get<double>((size_t)f2 * q.r);
+  } else {
+    qm.b = ex.ar->get<double>((size_t)n2 * q.r);
+    qp.b = ex.ar->get<double>((size_t)n2 * q.r);
+    qm.a = ex.ar->get<double>((size_t)f1 * q.r);
   }
+  recon_linear(ex, q, d, S.p.recon, qm, qp);
+}
+
+// One side of the WENO5 faces of one field (Algorithms 2 and 3): Step 1 by
+// cross along the face normal, Step 2 by cross at all Gauss points; the
+// "-" side (k = 0) is then shifted by one cell along the normal (Qm).
+static void weno_side(Solver& S, Exec& ex, const TT& q, int d, int fieldc, int k, unsigned seed, TT& dst) {
+  const tt_fv_params& p = S.p;
+  const int n1 = q.n1, n2 = q.n2, cap = p.rank_cap;
+  const int f1 = d == 0 ? n1 : 3 * n1, f2 = d == 0 ? 3 * n2 : n2;
+  const double dx = p.lx / p.nx, dy = p.ly / p.ny;
   const double e1 = d == 0 ? dx * dx : dy * dy, e2 = d == 0 ? dy * dy : dx * dx;
   const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
   const unsigned seed_base = seed + 64u * d + 8u * fieldc;
-  for (int k = 0; k < 2; ++k) {
-    Scope sc(*ex.ar);
-    CrossFn f1n;
-    f1n.fn = TT_FN_WENO_S1;
-    f1n.in = &q;
-    f1n.nin = 1;
-    f1n.prm[0] = e1;
-    f1n.prm[1] = k == 0 ? -1.0 : 1.0;
-    f1n.prm[2] = d;
-    TT vt = alloc_tt(*ex.ar, n1, n2, cap);
-    cross(ex, f1n, n1, n2, q, p.tol, cap, kick, sweeps, seed_base + 4u * k, vt);
-    // initial guess of Step 2: the Step-1 result repeated over the Gauss points
-    TT x0 = d == 0 ? alloc_tt(*ex.ar, n1, 3 * n2, vt.r) : alloc_tt(*ex.ar, 3 * n1, n2, vt.r);
-    x0.r = vt.r;
-    for (int c = 0; c < vt.r; ++c) {
-      if (d == 0) {
-        scaled_copy(ex, x0.a + (size_t)c * n1, vt.a + (size_t)c * n1, n1, 1.0);
-        for (int m = 0; m < 3; ++m)
-          scaled_copy(ex, x0.b + (size_t)c * 3 * n2 + m * n2, vt.b + (size_t)c * n2, n2, 1.0);
-      } else {
-        scaled_copy(ex, x0.b + (size_t)c * n2, vt.b + (size_t)c * n2, n2, 1.0);
-        for (int m = 0; m < 3; ++m)
-          scaled_copy(ex, x0.a + (size_t)c * 3 * n1 + m * n1, vt.a + (size_t)c * n1, n1, 1.0);
-      }
-    }
-    CrossFn f2n;
-    f2n.fn = TT_FN_WENO_S2;
-    f2n.in = &vt;
-    f2n.nin = 1;
-    f2n.prm[0] = e2;
-    f2n.prm[1] = d == 0 ? 1.0 : 0.0;
-    f2n.prm[2] = 3;
-    TT tmp = alloc_tt(*ex.ar, f1, f2, cap);
-    cross(ex, f2n, f1, f2, x0, p.tol, cap, kick, sweeps, seed_base + 4u * k + 1u, tmp);
-    // qm / qp storage is allocated by the caller, outside this scope
-    TT& dst = k == 0 ? qm : qp;
-    if (k == 0) {
-      // Qm: cell i-1's right-face value -> shift the normal core by one
-      StencilSet st;
-      st.nout = 1;
-      double one = 1.0;
-      if (d == 0) {
-        st.out[0].dst = dst.a;
-        st.out[0].ld = f1;
-        add_taps(st.out[0], &one, 1, -1, 0);
-        stencil(ex, st, tmp.a, f1, f1, tmp.r);
-        scaled_copy(ex, dst.b, tmp.b, (long)f2 * tmp.r, 1.0);
-      } else {
-        st.out[0].dst = dst.b;
-        st.out[0].ld = f2;
-        add_taps(st.out[0], &one, 1, -1, 0);
-        stencil(ex, st, tmp.b, f2, f2, tmp.r);
-        scaled_copy(ex, dst.a, tmp.a, (long)f1 * tmp.r, 1.0);
-      }
-      dst.r = tmp.r;
+  Scope sc(*ex.ar);
+  CrossFn f1n;
+  f1n.fn = TT_FN_WENO_S1;
+  f1n.in = &q;
+  f1n.nin = 1;
+  f1n.prm[0] = e1;
+  f1n.prm[1] = k == 0 ? -1.0 : 1.0;
+  f1n.prm[2] = d;
+  TT vt = alloc_tt(*ex.ar, n1, n2, cap);
+  cross(ex, f1n, n1, n2, q, p.tol, cap, kick, sweeps, seed_base + 4u * k, vt);
+  // initial guess of Step 2: the Step-1 result repeated over the Gauss points
+  TT x0 = d == 0 ? alloc_tt(*ex.ar, n1, 3 * n2, vt.r) : alloc_tt(*ex.ar, 3 * n1, n2, vt.r);
+  x0.r = vt.r;
+  for (int c = 0; c < vt.r; ++c) {
+    if (d == 0) {
+      scaled_copy(ex, x0.a + (size_t)c * n1, vt.a + (size_t)c * n1, n1, 1.0);
+      for (int m = 0; m < 3; ++m)
+        scaled_copy(ex, x0.b + (size_t)c * 3 * n2 + m * n2, vt.b + (size_t)c * n2, n2, 1.0);
     } else {
-      copy_tt(ex, tmp, dst);
+      scaled_copy(ex, x0.b + (size_t)c * n2, vt.b + (size_t)c * n2, n2, 1.0);
+      for (int m = 0; m < 3; ++m)
+        scaled_copy(ex, x0.a + (size_t)c * 3 * n1 + m * n1, vt.a + (size_t)c * n1, n1, 1.0);
     }
+  }
+  CrossFn f2n;
+  f2n.fn = TT_FN_WENO_S2;
+  f2n.in = &vt;
+  f2n.nin = 1;
+  f2n.prm[0] = e2;
+  f2n.prm[1] = d == 0 ? 1.0 : 0.0;
+  f2n.prm[2] = 3;
+  TT tmp = alloc_tt(*ex.ar, f1, f2, cap);
+  cross(ex, f2n, f1, f2, x0, p.tol, cap, kick, sweeps, seed_base + 4u * k + 1u, tmp);
+  if (k == 0) {
+    StencilSet st;
+    st.nout = 1;
+    double one = 1.0;
+    if (d == 0) {
+      st.out[0].dst = dst.a;
+      st.out[0].ld = f1;
+      add_taps(st.out[0], &one, 1, -1, 0);
+      stencil(ex, st, tmp.a, f1, f1, tmp.r);
+      scaled_copy(ex, dst.b, tmp.b, (long)f2 * tmp.r, 1.0);
+    } else {
+      st.out[0].dst = dst.b;
+      st.out[0].ld = f2;
+      add_taps(st.out[0], &one, 1, -1, 0);
+      stencil(ex, st, tmp.b, f2, f2, tmp.r);
+      scaled_copy(ex, dst.a, tmp.a, (long)f1 * tmp.r, 1.0);
+    }
+    dst.r = tmp.r;
+  } else {
+    copy_tt(ex, tmp, dst);
   }
 }
 
@@ -266,56 +267,60 @@ static void flux_linear(Solver& S, const TT qm[3], const TT qp[3], int d, std::v
   }
 }
 
-// LLF flux of the nonlinear SWE with the Taylor reciprocal; results rounded
-static void flux_nonlinear(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int d, unsigned seed, TT Fh[3]) {
+// Nonlinear physical flux of one face side (Sec. 4.2): 1/h by Algorithm 1,
+// u = round(hu o 1/h), v = round(hv o 1/h), then F = (hu, round(round(hu o u)
+// + g/2 round(h o h)), round(hu o v)) for x faces and G = (hv, round(hv o u),
+// round(round(hv o v) + g/2 round(h o h))) for y faces.  F[0] is left to the caller.
+static void side_flux(Solver& S, Exec& ex, const TT Q[3], int d, TT F[3]) {
   const tt_fv_params& p = S.p;
   const double tol = p.tol, g = p.g;
   const int cap = p.rank_cap, mi = p.max_iter > 0 ? p.max_iter : 50;
-  const int n1 = qm[0].n1, n2 = qm[0].n2;
+  const int n1 = Q[0].n1, n2 = Q[0].n2;
+  Scope sc(*ex.ar);
+  TT rh = alloc_tt(*ex.ar, n1, n2, cap);
+  bool nc = false;
+  reciprocal(ex, Q[0], tol, cap, mi, rh, &nc);
+  TT_REQUIRE(!nc, TT_ERR_NOCONV);
+  TT u = alloc_tt(*ex.ar, n1, n2, cap), v = alloc_tt(*ex.ar, n1, n2, cap), hh = alloc_tt(*ex.ar, n1, n2, cap);
+  TT t1 = alloc_tt(*ex.ar, n1, n2, cap);
+  round_hadamard(ex, Q[1], rh, tol, cap, u);
+  round_hadamard(ex, Q[2], rh, tol, cap, v);
+  round_hadamard(ex, Q[0], Q[0], tol, cap, hh);
+  if (d == 0) {
+    round_hadamard(ex, Q[1], u, tol, cap, t1);
+    round_sum(ex, {Term{1.0, t1}, Term{0.5 * g, hh}}, tol, cap, F[1]);
+    round_hadamard(ex, Q[1], v, tol, cap, F[2]);
+  } else {
+    round_hadamard(ex, Q[2], u, tol, cap, F[1]);
+    round_hadamard(ex, Q[2], v, tol, cap, t1);
+    round_sum(ex, {Term{1.0, t1}, Term{0.5 * g, hh}}, tol, cap, F[2]);
+  }
+}
+
+// lambda = max(|u-| + sqrt(g h-), |u+| + sqrt(g h+)) on the faces by cross
+static void face_lambda(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int d, unsigned seed, TT& lam) {
+  const tt_fv_params& p = S.p;
   const int k = d == 0 ? 1 : 2;
-  TT F[2][3];
-  for (int side = 0; side < 2; ++side) {
-    const TT* Q = side == 0 ? qm : qp;
-    for (int c = 1; c < 3; ++c) F[side][c] = alloc_tt(*ex.ar, n1, n2, cap);
-    Scope sc(*ex.ar);
-    TT rh = alloc_tt(*ex.ar, n1, n2, cap);
-    bool nc = false;
-    reciprocal(ex, Q[0], tol, cap, mi, rh, &nc);
-    TT_REQUIRE(!nc, TT_ERR_NOCONV);
-    TT u = alloc_tt(*ex.ar, n1, n2, cap), v = alloc_tt(*ex.ar, n1, n2, cap), hh = alloc_tt(*ex.ar, n1, n2, cap);
-    TT t1 = alloc_tt(*ex.ar, n1, n2, cap);
-    round_hadamard(ex, Q[1], rh, tol, cap, u);
-    round_hadamard(ex, Q[2], rh, tol, cap, v);
-    round_hadamard(ex, Q[0], Q[0], tol, cap, hh);
-    if (d == 0) {
-      round_hadamard(ex, Q[1], u, tol, cap, t1);
-      round_sum(ex, {Term{1.0, t1}, Term{0.5 * g, hh}}, tol, cap, F[side][1]);
-      round_hadamard(ex, Q[1], v, tol, cap, F[side][2]);
-    } else {
-      round_hadamard(ex, Q[2], u, tol, cap, F[side][1]);
-      round_hadamard(ex, Q[2], v, tol, cap, t1);
-      round_sum(ex, {Term{1.0, t1}, Term{0.5 * g, hh}}, tol, cap, F[side][2]);
-    }
-    F[side][0] = Q[k];
-  }
-  TT lam = alloc_tt(*ex.ar, n1, n2, cap);
-  {
-    TT ins[4] = {qm[0], qm[k], qp[0], qp[k]};
-    CrossFn fl;
-    fl.fn = TT_FN_LLF_LAMBDA;
-    fl.in = ins;
-    fl.nin = 4;
-    fl.prm[0] = g;
-    const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
-    cross(ex, fl, n1, n2, qp[0], tol, cap, kick, sweeps, seed, lam);
-  }
-  for (int c = 0; c < 3; ++c) {
-    Scope sc(*ex.ar);
-    TT dd = alloc_tt(*ex.ar, n1, n2, cap), ld = alloc_tt(*ex.ar, n1, n2, cap);
-    round_sum(ex, {Term{1.0, qp[c]}, Term{-1.0, qm[c]}}, tol, cap, dd);
-    round_hadamard(ex, lam, dd, tol, cap, ld);
-    round_sum(ex, {Term{0.5, F[0][c]}, Term{0.5, F[1][c]}, Term{-0.5, ld}}, tol, cap, Fh[c]);
-  }
+  TT ins[4] = {qm[0], qm[k], qp[0], qp[k]};
+  CrossFn fl;
+  fl.fn = TT_FN_LLF_LAMBDA;
+  fl.in = ins;
+  fl.nin = 4;
+  fl.prm[0] = p.g;
+  const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
+  cross(ex, fl, qm[0].n1, qm[0].n2, qp[0], p.tol, p.rank_cap, kick, sweeps, seed, lam);
+}
+
+// LLF combination of one component: round(F-/2 + F+/2 - round(lambda o round(Q+ - Q-))/2)
+static void llf_component(Solver& S, Exec& ex, const TT& Fm, const TT& Fp, const TT& lam, const TT& qm,
+                          const TT& qp, TT& out) {
+  const double tol = S.p.tol;
+  const int cap = S.p.rank_cap;
+  Scope sc(*ex.ar);
+  TT dd = alloc_tt(*ex.ar, qm.n1, qm.n2, cap), ld = alloc_tt(*ex.ar, qm.n1, qm.n2, cap);
+  round_sum(ex, {Term{1.0, qp}, Term{-1.0, qm}}, tol, cap, dd);
+  round_hadamard(ex, lam, dd, tol, cap, ld);
+  round_sum(ex, {Term{0.5, Fm}, Term{0.5, Fp}, Term{-0.5, ld}}, tol, cap, out);
 }
 
 // sum_m w_m over the stacked index, then (T - 1)/h on the normal core:
@@ -348,47 +353,86 @@ static TT quad_and_difference(Solver& S, Exec& ex, const TT& Fh, int d) {
   return out;
 }
 
-// F(u) = round(u + dt L(u)) for the three fields (Eq. tt-forward-euler)
+// F(u) = round(u + dt L(u)) for the three fields (Eq. tt-forward-euler).
+// Independent pieces run as concurrent tasks: the 12 WENO face crosses, the
+// 4 side fluxes with the 2 lambda crosses, the 6 LLF combinations, the 3
+// final rounds.
 static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT out[3]) {
   Scope sc(*ex.ar);
   const tt_fv_params& p = S.p;
+  const int cap = p.rank_cap;
   std::vector<Term> terms[3];
   for (int c = 0; c < 3; ++c) terms[c].push_back(Term{1.0, Q[c]});
+  TT qm[2][3], qp[2][3];
+  int f1[2], f2[2];
   for (int d = 0; d < 2; ++d) {
-    TT qm[3], qp[3];
-    const int f1 = d == 0 ? p.nx : S.nq * p.nx, f2 = d == 0 ? S.nq * p.ny : p.ny;
-    for (int c = 0; c < 3; ++c) {
-      if (p.recon == TT_WENO5) {
-        qm[c] = alloc_tt(*ex.ar, f1, f2, p.rank_cap);
-        qp[c] = alloc_tt(*ex.ar, f1, f2, p.rank_cap);
+    f1[d] = d == 0 ? p.nx : S.nq * p.nx;
+    f2[d] = d == 0 ? S.nq * p.ny : p.ny;
+  }
+  if (p.recon == TT_WENO5) {
+    for (int d = 0; d < 2; ++d)
+      for (int c = 0; c < 3; ++c) {
+        qm[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+        qp[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
       }
-      face_tts(S, ex, Q[c], d, c, seed, qm[c], qp[c]);
-    }
+    parallel_tasks(ex, 12, [&](Exec& cx, int t) {
+      const int d = t / 6, c = (t / 2) % 3, k = t % 2;
+      weno_side(S, cx, Q[c], d, c, k, seed, k == 0 ? qm[d][c] : qp[d][c]);
+    });
+  } else {
+    for (int d = 0; d < 2; ++d)
+      for (int c = 0; c < 3; ++c) faces_linear(S, ex, Q[c], d, qm[d][c], qp[d][c]);
+  }
+  for (int d = 0; d < 2; ++d) {
     if (p.eqn == TT_LINEAR) {
       std::vector<Term> fl[3];
-      flux_linear(S, qm, qp, d, fl);
+      flux_linear(S, qm[d], qp[d], d, fl);
       for (int c = 0; c < 3; ++c) {
         const int R = total_rank(fl[c]);
-        TT cat = alloc_tt(*ex.ar, f1, f2, R);
+        TT cat = alloc_tt(*ex.ar, f1[d], f2[d], R);
         tt_concat(ex, fl[c], cat);
         TT D = quad_and_difference(S, ex, cat, d);
         terms[c].push_back(Term{-p.dt, D});
       }
-    } else {
-      TT Fh[3];
-      for (int c = 0; c < 3; ++c) Fh[c] = alloc_tt(*ex.ar, f1, f2, p.rank_cap);
-      flux_nonlinear(S, ex, qm, qp, d, seed + 64u * d + 40u, Fh);
+    }
+  }
+  if (p.eqn != TT_LINEAR) {
+    TT F[2][2][3], lam[2], Fh[2][3];
+    for (int d = 0; d < 2; ++d) {
+      for (int sd = 0; sd < 2; ++sd)
+        for (int c = 1; c < 3; ++c) F[d][sd][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      lam[d] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      for (int c = 0; c < 3; ++c) Fh[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+    }
+    parallel_tasks(ex, 6, [&](Exec& cx, int t) {
+      if (t < 4) {
+        const int d = t / 2, sd = t % 2;
+        side_flux(S, cx, sd == 0 ? qm[d] : qp[d], d, F[d][sd]);
+      } else {
+        const int d = t - 4;
+        face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, lam[d]);
+      }
+    });
+    for (int d = 0; d < 2; ++d) {
+      const int k = d == 0 ? 1 : 2;
+      F[d][0][0] = qm[d][k];
+      F[d][1][0] = qp[d][k];
+    }
+    parallel_tasks(ex, 6, [&](Exec& cx, int t) {
+      const int d = t / 3, c = t % 3;
+      llf_component(S, cx, F[d][0][c], F[d][1][c], lam[d], qm[d][c], qp[d][c], Fh[d][c]);
+    });
+    for (int d = 0; d < 2; ++d)
       for (int c = 0; c < 3; ++c) {
-        TT D = quad_and_difference(S, ex, Fh[c], d);
+        TT D = quad_and_difference(S, ex, Fh[d][c], d);
         terms[c].push_back(Term{-p.dt, D});
       }
-    }
   }
   if (p.f != 0.0) {
     terms[1].push_back(Term{p.dt * p.f, Q[2]});
     terms[2].push_back(Term{-p.dt * p.f, Q[1]});
   }
-  for (int c = 0; c < 3; ++c) round_sum(ex, terms[c], p.tol, p.rank_cap, out[c]);
+  parallel_tasks(ex, 3, [&](Exec& cx, int c) { round_sum(cx, terms[c], p.tol, cap, out[c]); });
 }
 
 // kick-index seed of a stage: depends on the stage and call site only, so a
@@ -405,13 +449,14 @@ static void run_stage(Solver& S, Exec& ex, int stage) {
   if (stage == 0) {
     for (int c = 0; c < 3; ++c) copy_tt(ex, f[c], S.Qs[c]);
   } else if (stage == 1) {
-    for (int c = 0; c < 3; ++c)
-      round_sum(ex, {Term{0.75, S.Qn[c]}, Term{0.25, f[c]}}, p.tol, p.rank_cap, S.Qs[c]);
+    parallel_tasks(ex, 3, [&](Exec& cx, int c) {
+      round_sum(cx, {Term{0.75, S.Qn[c]}, Term{0.25, f[c]}}, p.tol, p.rank_cap, S.Qs[c]);
+    });
   } else {
-    for (int c = 0; c < 3; ++c) {
-      round_sum(ex, {Term{1.0 / 3.0, S.Qn[c]}, Term{2.0 / 3.0, f[c]}}, p.tol, p.rank_cap, S.Qn[c]);
-      copy_tt(ex, S.Qn[c], S.Qs[c]);
-    }
+    parallel_tasks(ex, 3, [&](Exec& cx, int c) {
+      round_sum(cx, {Term{1.0 / 3.0, S.Qn[c]}, Term{2.0 / 3.0, f[c]}}, p.tol, p.rank_cap, S.Qn[c]);
+    });
+    for (int c = 0; c < 3; ++c) copy_tt(ex, S.Qn[c], S.Qs[c]);
     S.step_count++;
   }
   S.next_stage = (stage + 1) % 3;
@@ -559,6 +604,7 @@ tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws
   try {
     setup_exec(S.ex, S.ar, ws, ws_bytes, S.s, S.h_int, S.h_dbl, false);
     S.ex.prof = &S.prof;
+    S.ex.pool = &S.pool;
     for (int c = 0; c < 3; ++c) {
       S.Qn[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
       S.Qs[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);

@@ -221,35 +221,41 @@ void sumsq(Exec& ex, const double* X, int m, int n, long ld, double* out) {
 constexpr int QR_THREADS = 512;
 constexpr size_t QR_SMEM_MAX = 200 * 1024;
 
-__device__ void cta_householder_qr(double* A, int mb, int p, double* tau_out, double* red) {
+// Two barriers per column: warp 0 forms the reflector of column j (its norm
+// below the diagonal was computed by warp 0 while updating that column in
+// the previous step), then all warps update the trailing columns.
+__device__ void cta_householder_qr(double* A, int mb, int p, double* tau_out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ double s_tau;
+  double next_sigma = 0.0;  // warp 0: sum of squares of column j below row j
+  if (w == 0) {
+    double s = 0.0;
+    for (int i = 1 + lane; i < mb; i += 32) s = fma(A[i], A[i], s);
+    next_sigma = warp_sum(s);
+  }
   for (int j = 0; j < p; ++j) {
     double* col = A + (size_t)j * mb;
-    double s = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < mb; i += blockDim.x) s = fma(col[i], col[i], s);
-    const double sigma = block_sum(s, red);
-    const double alpha = col[j];
-    double tau = 0.0, scale = 0.0, beta = alpha;
-    if (sigma > 0.0) {
-      const double nrm = sqrt(fma(alpha, alpha, sigma));
-      beta = alpha >= 0.0 ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
+    if (w == 0) {
+      const double sigma = next_sigma, alpha = col[j];
+      double tau = 0.0, beta = alpha;
+      if (sigma > 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, sigma));
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        const double scale = 1.0 / (alpha - beta);
+        for (int i = j + 1 + lane; i < mb; i += 32) col[i] *= scale;
+      }
+      if (lane == 0) {
+        col[j] = beta;
+        s_tau = tau;
+        tau_out[j] = tau;
+      }
     }
     __syncthreads();
-    if (sigma > 0.0)
-      for (int i = j + 1 + threadIdx.x; i < mb; i += blockDim.x) col[i] *= scale;
-    if (threadIdx.x == 0) {
-      col[j] = beta;
-      s_tau = tau;
-      tau_out[j] = tau;
-    }
-    __syncthreads();
-    tau = s_tau;
-    if (tau != 0.0) {
-      for (int c = j + 1 + w; c < p; c += nw) {
-        double* cc = A + (size_t)c * mb;
+    const double tau = s_tau;
+    for (int c = j + 1 + w; c < p; c += nw) {
+      double* cc = A + (size_t)c * mb;
+      if (tau != 0.0) {
         double d = 0.0;
         for (int i = j + 1 + lane; i < mb; i += 32) d = fma(col[i], cc[i], d);
         d = warp_sum(d) + cc[j];
@@ -257,15 +263,20 @@ __device__ void cta_householder_qr(double* A, int mb, int p, double* tau_out, do
         if (lane == 0) cc[j] -= f;
         for (int i = j + 1 + lane; i < mb; i += 32) cc[i] = fma(-f, col[i], cc[i]);
       }
+      if (c == j + 1) {  // warp 0: norm of the next column below its diagonal
+        __syncwarp();
+        double s = 0.0;
+        for (int i = j + 2 + lane; i < mb; i += 32) s = fma(cc[i], cc[i], s);
+        next_sigma = warp_sum(s);
+      }
     }
     __syncthreads();
   }
 }
 
 __global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const double* __restrict__ X, int m, int p, long ldx,
-                                                          int mb, double* V, double* tau, double* Rst, long ldr) {
+                                                          int mb, double* V, double* tau, double* Rout) {
   extern __shared__ double sm[];
-  __shared__ double red[33];
   const int b = blockIdx.x, r0 = b * mb;
   double* A = sm;
   for (int t = threadIdx.x; t < mb * p; t += blockDim.x) {
@@ -273,20 +284,92 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const double* __restri
     A[t] = (r0 + i < m) ? X[(r0 + i) + (size_t)j * ldx] : 0.0;
   }
   __syncthreads();
-  cta_householder_qr(A, mb, p, tau + (size_t)b * p, red);
+  cta_householder_qr(A, mb, p, tau + (size_t)b * p);
   double* Vb = V + (size_t)b * mb * p;
   for (int t = threadIdx.x; t < mb * p; t += blockDim.x) Vb[t] = A[t];
+  double* Rb = Rout + (size_t)b * p * p;
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
     const int i = t % p, j = t / p;
-    Rst[(size_t)(b * p + i) + (size_t)j * ldr] = (i <= j) ? A[i + (size_t)j * mb] : 0.0;
+    Rb[t] = (i <= j) ? A[i + (size_t)j * mb] : 0.0;
   }
 }
 
-static int qr_block_rows(int p, int level) {
+// Merge of two stacked upper-triangular factors [T; B] (p x p each) by
+// Householder reflectors that touch row j of T and rows 0..j of B only:
+// (2/3) p^3 flops instead of the (10/3) p^3 of a dense 2p x p QR.  An odd
+// last input passes through unchanged (tau = 0).
+__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restrict__ Rin, int nin, int p,
+                                                         double* Rout, double* Vm, double* taum) {
+  extern __shared__ double sm[];
+  const int node = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* T = sm;
+  double* B = sm + (size_t)p * p;
+  const double* Rt = Rin + (size_t)(2 * node) * p * p;
+  double* Ro = Rout + (size_t)node * p * p;
+  double* Vo = Vm + (size_t)node * p * p;
+  double* to = taum + (size_t)node * p;
+  if (2 * node + 1 >= nin) {
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+      Ro[t] = Rt[t];
+      Vo[t] = 0.0;
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) to[j] = 0.0;
+    return;
+  }
+  const double* Rb = Rt + (size_t)p * p;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    T[t] = Rt[t];
+    B[t] = Rb[t];
+  }
+  __syncthreads();
+  __shared__ double s_tau;
+  for (int j = 0; j < p; ++j) {
+    double* bj = B + (size_t)j * p;
+    if (w == 0) {
+      double sg = 0.0;
+      for (int i = lane; i <= j; i += 32) sg = fma(bj[i], bj[i], sg);
+      sg = warp_sum(sg);
+      const double alpha = T[j + (size_t)j * p];
+      double tau = 0.0, beta = alpha;
+      if (sg > 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, sg));
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        const double scale = 1.0 / (alpha - beta);
+        for (int i = lane; i <= j; i += 32) bj[i] *= scale;
+      }
+      if (lane == 0) {
+        T[j + (size_t)j * p] = beta;
+        s_tau = tau;
+        to[j] = tau;
+      }
+    }
+    __syncthreads();
+    const double tau = s_tau;
+    if (tau != 0.0) {
+      for (int c = j + 1 + w; c < p; c += nw) {
+        double* bc = B + (size_t)c * p;
+        double d = 0.0;
+        for (int i = lane; i <= j; i += 32) d = fma(bj[i], bc[i], d);
+        d = warp_sum(d) + T[j + (size_t)c * p];
+        const double f = tau * d;
+        if (lane == 0) T[j + (size_t)c * p] -= f;
+        for (int i = lane; i <= j; i += 32) bc[i] = fma(-f, bj[i], bc[i]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int i = t % p, j = t / p;
+    Ro[t] = (i <= j) ? T[t] : 0.0;
+    Vo[t] = (i <= j) ? B[t] : 0.0;
+  }
+}
+
+static int qr_leaf_rows(int p) {
+  int mb = std::max(((p + 31) / 32) * 32, 64);
   const int lim = int(QR_SMEM_MAX / (8 * (size_t)p));
-  int mb = level == 0 ? std::max(2 * p, 128) : std::max(2 * p, std::min(4 * p, 256));
-  mb = std::min(mb, lim);
-  return std::max(mb, p);
+  return std::max(std::min(mb, lim), p);
 }
 
 void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t) {
@@ -294,52 +377,53 @@ void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t) {
   t = QRTree{};
   t.m = m;
   t.p = p;
-  const double* in = X;
-  long ldin = ldx;
-  int rows = m;
-  for (int level = 0;; ++level) {
-    TT_REQUIRE(level < 32, TT_ERR_ARG);
-    const int mb = std::max(qr_block_rows(p, level), p);
-    const int nb = ceil_div(rows, mb);
-    double* V = ex.ar->get<double>((size_t)nb * mb * p);
-    double* tau = ex.ar->get<double>((size_t)nb * p);
-    double* Rst = ex.ar->get<double>((size_t)nb * p * p);
-    t.mrows.push_back(rows);
-    t.mb.push_back(mb);
-    t.nb.push_back(nb);
-    t.V.push_back(V);
-    t.tau.push_back(tau);
-    if (!ex.dry) {
-      const size_t smem = (size_t)mb * p * 8;
-      TT_CUDA(cudaFuncSetAttribute(k_qr_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      // algorithmic work: Householder QR of the valid rows of each block
-      const double fl = 2.0 * rows * (double)p * p - nb * (2.0 / 3.0) * p * (double)p * p;
-      TT_KERNEL(ex, K_QR, std::max(fl, 0.0), 8.0 * ((double)rows * p * 2 + (double)nb * p * p),
-                k_qr_blocks<<<nb, QR_THREADS, smem, ex.s>>>(in, rows, p, ldin, mb, V, tau, Rst, (long)nb * p));
-    }
-    if (nb == 1) {
-      t.R = Rst;  // p x p with ld = p
-      t.levels = level + 1;
-      return;
-    }
-    in = Rst;
-    ldin = (long)nb * p;
-    rows = nb * p;
+  t.mb0 = qr_leaf_rows(p);
+  t.nb0 = ceil_div(m, t.mb0);
+  t.V0 = ex.ar->get<double>((size_t)t.nb0 * t.mb0 * p);
+  t.tau0 = ex.ar->get<double>((size_t)t.nb0 * p);
+  double* R = ex.ar->get<double>((size_t)t.nb0 * p * p);
+  if (!ex.dry) {
+    smem_attr_once(k_qr_blocks);
+    const size_t smem = (size_t)t.mb0 * p * 8;
+    const double fl = 2.0 * m * (double)p * p - t.nb0 * (2.0 / 3.0) * p * (double)p * p;
+    TT_KERNEL(ex, K_QR, std::max(fl, 0.0), 8.0 * ((double)m * p * 2 + (double)t.nb0 * p * p),
+              k_qr_blocks<<<t.nb0, QR_THREADS, smem, ex.s>>>(X, m, p, ldx, t.mb0, t.V0, t.tau0, R));
   }
+  int n = t.nb0;
+  while (n > 1) {
+    const int nodes = (n + 1) / 2;
+    double* Vm = ex.ar->get<double>((size_t)nodes * p * p);
+    double* tm = ex.ar->get<double>((size_t)nodes * p);
+    double* Rn = ex.ar->get<double>((size_t)nodes * p * p);
+    t.nin.push_back(n);
+    t.Vm.push_back(Vm);
+    t.taum.push_back(tm);
+    if (!ex.dry) {
+      smem_attr_once(k_qr_merge);
+      const size_t smem = 2 * (size_t)p * p * 8;
+      TT_KERNEL(ex, K_QR, (n / 2) * (2.0 / 3.0) * p * (double)p * p, 8.0 * 3.0 * nodes * p * (double)p,
+                k_qr_merge<<<nodes, QR_THREADS, smem, ex.s>>>(R, n, p, Rn, Vm, tm));
+    }
+    R = Rn;
+    n = nodes;
+  }
+  t.R = R;
 }
 
-// Apply the reflectors of each block (in reverse order) to [Zin_block; 0].
+// Apply the level-0 reflectors of each block (in reverse order) to
+// [Zin_block; 0], Zin_block = Zin + b*zstride (p x k, ld zld).
 __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const double* __restrict__ V,
                                                                 const double* __restrict__ tau, int mb, int p,
                                                                 int rows, int k, const double* __restrict__ Zin,
-                                                                long ldzi, int zin_rows_per_block,
-                                                                double* __restrict__ Zout, long ldzo) {
+                                                                long zstride, long zld, double* __restrict__ Zout,
+                                                                long ldzo) {
   extern __shared__ double sm[];
   const int b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* Z = sm;  // mb x k
+  const double* zb = Zin + (size_t)b * zstride;
   for (int t = threadIdx.x; t < mb * k; t += blockDim.x) {
     const int i = t % mb, j = t / mb;
-    Z[t] = (i < zin_rows_per_block) ? Zin[(size_t)(b * zin_rows_per_block + i) + (size_t)j * ldzi] : 0.0;
+    Z[t] = (i < p) ? zb[i + (size_t)j * zld] : 0.0;
   }
   __syncthreads();
   const double* Vb = V + (size_t)b * mb * p;
@@ -367,72 +451,250 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const double* __
   }
 }
 
-void tsqr_apply(Exec& ex, const QRTree& t, const double* C, int k, long ldc, double* Out, long ldo) {
-  TT_REQUIRE(k >= 1, TT_ERR_ARG);
-  Scope sc(*ex.ar);
-  const int p = t.p;
-  // top-down: the last level's single block takes [C; 0]
-  const double* zin = C;
-  long ldzi = ldc;
-  for (int l = t.levels - 1; l >= 0; --l) {
-    const int rows = t.mrows[l], mb = t.mb[l], nb = t.nb[l];
-    double* zout;
-    long ldzo;
-    if (l == 0) {
-      zout = Out;
-      ldzo = ldo;
-    } else {
-      zout = ex.ar->get<double>((size_t)rows * k);
-      ldzo = rows;
+// Reverse of a merge node: [top; bottom] = Q_node [Z; 0]; top goes to input
+// 2*node, bottom to input 2*node+1 (each p x k, ld p).
+__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(const double* __restrict__ Vm,
+                                                               const double* __restrict__ taum, int nin, int p,
+                                                               int k, const double* __restrict__ Zin, long zstride,
+                                                               long zld, double* __restrict__ Zout) {
+  extern __shared__ double sm[];
+  const int node = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* zb = Zin + (size_t)node * zstride;
+  double* top = Zout + (size_t)(2 * node) * p * k;
+  if (2 * node + 1 >= nin) {
+    for (int t = threadIdx.x; t < p * k; t += blockDim.x) top[t] = zb[(t % p) + (size_t)(t / p) * zld];
+    return;
+  }
+  double* T = sm;                  // p x k
+  double* B = sm + (size_t)p * k;  // p x k
+  for (int t = threadIdx.x; t < p * k; t += blockDim.x) {
+    T[t] = zb[(t % p) + (size_t)(t / p) * zld];
+    B[t] = 0.0;
+  }
+  __syncthreads();
+  const double* V = Vm + (size_t)node * p * p;
+  const double* tv = taum + (size_t)node * p;
+  for (int j = p - 1; j >= 0; --j) {
+    const double tj = tv[j];
+    if (tj != 0.0) {
+      const double* v = V + (size_t)j * p;
+      for (int c = w; c < k; c += nw) {
+        double* bc = B + (size_t)c * p;
+        double d = 0.0;
+        for (int i = lane; i <= j; i += 32) d = fma(v[i], bc[i], d);
+        d = warp_sum(d) + T[j + (size_t)c * p];
+        const double f = tj * d;
+        if (lane == 0) T[j + (size_t)c * p] -= f;
+        for (int i = lane; i <= j; i += 32) bc[i] = fma(-f, v[i], bc[i]);
+      }
     }
-    if (!ex.dry) {
-      const size_t smem = (size_t)mb * k * 8;
-      TT_REQUIRE(smem <= QR_SMEM_MAX + 16 * 1024, TT_ERR_ARG);
-      TT_CUDA(cudaFuncSetAttribute(k_qr_apply_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      TT_KERNEL(ex, K_QR_APPLY, 4.0 * rows * (double)p * k, 8.0 * ((double)rows * (p + k) + (double)nb * p * k),
-                k_qr_apply_blocks<<<nb, QR_THREADS, smem, ex.s>>>(t.V[l], t.tau[l], mb, p, rows, k, zin, ldzi, p,
-                                                                   zout, ldzo));
-    }
-    zin = zout;
-    ldzi = ldzo;
+    __syncthreads();
+  }
+  double* bot = top + (size_t)p * k;
+  for (int t = threadIdx.x; t < p * k; t += blockDim.x) {
+    top[t] = T[t];
+    bot[t] = B[t];
   }
 }
 
-// ============================================================== Jacobi SVD
-// One-sided (Hestenes) Jacobi on the columns of M, parallel round-robin
-// ordering, one warp per column pair, everything in shared memory.
-constexpr int JAC_THREADS = 1024;
-constexpr int JAC_MAX_SWEEPS = 40;
-
-__global__ void __launch_bounds__(JAC_THREADS) k_jacobi_svd(const double* __restrict__ Min, int p, double tol,
-                                                           int cap, double* US, double* Vout, double* sig,
-                                                           int* k_out, double* tail_out, unsigned* status,
-                                                           int* sweeps_out) {
-  extern __shared__ double sm[];
-  double* M = sm;                      // p x p
-  double* V = sm + (size_t)p * p;      // p x p
-  __shared__ double norms[128];
-  __shared__ int order[128];
-  __shared__ int s_rot;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-    M[t] = Min[t];
-    V[t] = ((t % p) == (t / p)) ? 1.0 : 0.0;
+void tsqr_apply(Exec& ex, const QRTree& t, const double* C, int k, long ldc, double* Out, long ldo) {
+  TT_REQUIRE(k >= 1 && k <= 128, TT_ERR_ARG);
+  Scope sc(*ex.ar);
+  const int p = t.p;
+  const double* zin = C;
+  long zstride = 0, zld = ldc;
+  for (int l = (int)t.nin.size() - 1; l >= 0; --l) {
+    const int nin = t.nin[l], nodes = (nin + 1) / 2;
+    double* zout = ex.ar->get<double>((size_t)nin * p * k);
+    if (!ex.dry) {
+      smem_attr_once(k_qr_apply_merge);
+      const size_t smem = 2 * (size_t)p * k * 8;
+      TT_KERNEL(ex, K_QR_APPLY, (nin / 2) * 2.0 * p * (double)p * k, 8.0 * ((double)nodes * p * p + 3.0 * nin * p * k),
+                k_qr_apply_merge<<<nodes, QR_THREADS, smem, ex.s>>>(t.Vm[l], t.taum[l], nin, p, k, zin, zstride,
+                                                                    zld, zout));
+    }
+    zin = zout;
+    zstride = (long)p * k;
+    zld = p;
   }
-  const int q = p + (p & 1);  // even number of players; index p is a dummy
+  if (!ex.dry) {
+    smem_attr_once(k_qr_apply_blocks);
+    const size_t smem = (size_t)t.mb0 * k * 8;
+    TT_REQUIRE(smem <= QR_SMEM_MAX + 16 * 1024, TT_ERR_ARG);
+    TT_KERNEL(ex, K_QR_APPLY, 4.0 * t.m * (double)p * k,
+              8.0 * ((double)t.m * (p + k) + (double)t.nb0 * p * k),
+              k_qr_apply_blocks<<<t.nb0, QR_THREADS, smem, ex.s>>>(t.V0, t.tau0, t.mb0, p, t.m, k, zin, zstride, zld,
+                                                                  Out, ldo));
+  }
+}
+
+// ============================================================== small SVD
+// SVD of a p x p matrix M (p <= 112) in one CTA, all in shared memory:
+//  1. Householder QR with column pivoting of M^T, stopped once the trailing
+//     Frobenius norm is <= defl ||M||_F (the deflated part joins the tail):
+//     M = P L Q^T with L = R^T (p x pd) whose columns are graded;
+//  2. one-sided (Hestenes) Jacobi on the pd columns of L, round-robin pairs,
+//     one warp per pair; columns below defl ||M||_F are left untouched;
+//  3. singular values = column norms, sorted; outputs P (L V) and Q V.
+constexpr int SVD_THREADS = 1024;
+constexpr int SVD_MAX_SWEEPS = 30;
+
+__global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restrict__ Min, int p, double tol, int cap,
+                                                          double defl, double* US, double* Vout, double* sig,
+                                                          int* info, double* tail_out, double* scr,
+                                                          unsigned* status) {
+  extern __shared__ double sm[];
+  double* A = sm;                  // p x p
+  double* J = sm + (size_t)p * p;  // p x p scratch, then pd x pd Jacobi V
+  __shared__ double cn[128];
+  __shared__ int piv[128];
+  __shared__ int order[128];
+  __shared__ double s_tau, s_fro2, s_trail;
+  __shared__ int s_jmax, s_stop, s_rot, s_k;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* HV = scr;                  // Householder vectors, p x p
+  double* htau = scr + (size_t)p * p;
+
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int i = t % p, j = t / p;
+    A[t] = Min[j + (size_t)i * p];  // A = M^T
+  }
+  for (int j = threadIdx.x; j < p; j += blockDim.x) piv[j] = j;
+  __syncthreads();
+  for (int j = w; j < p; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < p; i += 32) s = fma(A[i + (size_t)j * p], A[i + (size_t)j * p], s);
+    s = warp_sum(s);
+    if (lane == 0) cn[j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int j = 0; j < p; ++j) f += cn[j];
+    s_fro2 = f;
+  }
+  __syncthreads();
+  const double fro2 = s_fro2;
+  const double thr = defl * defl * fro2;
+  // ---- 1. QR with column pivoting of M^T, deflated
+  int pd = p;
+  for (int k = 0; k < p; ++k) {
+    if (w == 0) {
+      double best = -1.0, trail = 0.0;
+      int bj = k;
+      for (int j = k + lane; j < p; j += 32) {
+        trail += cn[j];
+        if (cn[j] > best) {
+          best = cn[j];
+          bj = j;
+        }
+      }
+      trail = warp_sum(trail);
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ob > best || (ob == best && oj < bj)) {
+          best = ob;
+          bj = oj;
+        }
+      }
+      if (lane == 0) {
+        s_jmax = bj;
+        s_stop = (trail <= thr) ? 1 : 0;
+        s_trail = trail;
+      }
+    }
+    __syncthreads();
+    if (s_stop) {
+      pd = k;
+      break;
+    }
+    const int jm = s_jmax;
+    if (jm != k) {
+      for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        const double x = A[i + (size_t)k * p];
+        A[i + (size_t)k * p] = A[i + (size_t)jm * p];
+        A[i + (size_t)jm * p] = x;
+      }
+      if (threadIdx.x == 0) {
+        const int t = piv[k];
+        piv[k] = piv[jm];
+        piv[jm] = t;
+        const double c = cn[k];
+        cn[k] = cn[jm];
+        cn[jm] = c;
+      }
+    }
+    __syncthreads();
+    double* col = A + (size_t)k * p;
+    if (w == 0) {
+      double sg = 0.0;
+      for (int i = k + 1 + lane; i < p; i += 32) sg = fma(col[i], col[i], sg);
+      sg = warp_sum(sg);
+      const double alpha = col[k];
+      double tau = 0.0, beta = alpha;
+      if (sg > 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, sg));
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        const double scale = 1.0 / (alpha - beta);
+        for (int i = k + 1 + lane; i < p; i += 32) col[i] *= scale;
+      }
+      if (lane == 0) {
+        col[k] = beta;
+        s_tau = tau;
+        htau[k] = tau;
+      }
+    }
+    __syncthreads();
+    const double tau = s_tau;
+    for (int c = k + 1 + w; c < p; c += nw) {
+      double* cc = A + (size_t)c * p;
+      if (tau != 0.0) {
+        double d = 0.0;
+        for (int i = k + 1 + lane; i < p; i += 32) d = fma(col[i], cc[i], d);
+        d = warp_sum(d) + cc[k];
+        const double f = tau * d;
+        if (lane == 0) cc[k] -= f;
+        for (int i = k + 1 + lane; i < p; i += 32) cc[i] = fma(-f, col[i], cc[i]);
+      }
+      __syncwarp();
+      double s2 = 0.0;  // exact trailing norm of the column below row k
+      for (int i = k + 1 + lane; i < p; i += 32) s2 = fma(cc[i], cc[i], s2);
+      s2 = warp_sum(s2);
+      if (lane == 0) cn[c] = s2;
+    }
+    __syncthreads();
+  }
+  const double qr_tail2 = (pd < p) ? s_trail : 0.0;
+  // save the reflectors (below-diagonal parts) for the right factor
+  for (int t = threadIdx.x; t < p * pd; t += blockDim.x) {
+    const int i = t % p, kk = t / p;
+    HV[t] = (i > kk) ? A[t] : 0.0;
+  }
+  // ---- 2. L = R^T (p x pd) into J, then back into A
+  for (int t = threadIdx.x; t < p * pd; t += blockDim.x) {
+    const int jr = t % p, i = t / p;
+    J[t] = (i <= jr) ? A[i + (size_t)jr * p] : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p * pd; t += blockDim.x) A[t] = J[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) J[t] = ((t % pd) == (t / pd)) ? 1.0 : 0.0;
+  __syncthreads();
+  const int q = pd + (pd & 1);
   const double eps = DBL_EPSILON * p;
   int sweep = 0;
-  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
+  for (; sweep < SVD_MAX_SWEEPS && pd > 1; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int step = 0; step < q - 1; ++step) {
       for (int pr = w; pr < q / 2; pr += nw) {
-        const int a = pr, bpos = q - 1 - pr;
-        const int i = (a == 0) ? 0 : 1 + ((a - 1 + step) % (q - 1));
-        const int j = 1 + ((bpos - 1 + step) % (q - 1));
-        if (i >= p || j >= p) continue;
-        double* ci = M + (size_t)i * p;
-        double* cj = M + (size_t)j * p;
+        const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
+        const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
+        if (i >= pd || j >= pd) continue;
+        double* ci = A + (size_t)i * p;
+        double* cj = A + (size_t)j * p;
         double al = 0.0, be = 0.0, ga = 0.0;
         for (int r = lane; r < p; r += 32) {
           const double x = ci[r], y = cj[r];
@@ -443,21 +705,21 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi_svd(const double* __rest
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (al == 0.0 || be == 0.0 || fabs(ga) <= eps * sqrt(al) * sqrt(be)) continue;
+        if (al <= thr || be <= thr || fabs(ga) <= eps * sqrt(al) * sqrt(be)) continue;
         const double zeta = (be - al) / (2.0 * ga);
         const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-        const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = c * t;
+        const double c = 1.0 / sqrt(fma(t, t, 1.0)), sn = c * t;
         for (int r = lane; r < p; r += 32) {
           const double x = ci[r], y = cj[r];
-          ci[r] = c * x - s * y;
-          cj[r] = s * x + c * y;
+          ci[r] = c * x - sn * y;
+          cj[r] = sn * x + c * y;
         }
-        double* vi = V + (size_t)i * p;
-        double* vj = V + (size_t)j * p;
-        for (int r = lane; r < p; r += 32) {
+        double* vi = J + (size_t)i * pd;
+        double* vj = J + (size_t)j * pd;
+        for (int r = lane; r < pd; r += 32) {
           const double x = vi[r], y = vj[r];
-          vi[r] = c * x - s * y;
-          vj[r] = s * x + c * y;
+          vi[r] = c * x - sn * y;
+          vj[r] = sn * x + c * y;
         }
         if (lane == 0) s_rot = 1;
       }
@@ -466,39 +728,27 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi_svd(const double* __rest
     if (s_rot == 0) break;
     __syncthreads();
   }
-  // column norms -> singular values; sort descending (ties by index)
-  for (int j = w; j < p; j += nw) {
+  // ---- 3. singular values, order, truncation
+  for (int j = w; j < pd; j += nw) {
     double s = 0.0;
-    for (int r = lane; r < p; r += 32) s = fma(M[r + (size_t)j * p], M[r + (size_t)j * p], s);
+    for (int r = lane; r < p; r += 32) s = fma(A[r + (size_t)j * p], A[r + (size_t)j * p], s);
     s = warp_sum(s);
-    if (lane == 0) norms[j] = sqrt(s);
+    if (lane == 0) cn[j] = sqrt(s);
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+  for (int j = threadIdx.x; j < pd; j += blockDim.x) {
     int rk = 0;
-    for (int l = 0; l < p; ++l) rk += (norms[l] > norms[j]) || (norms[l] == norms[j] && l < j);
+    for (int l = 0; l < pd; ++l) rk += (cn[l] > cn[j]) || (cn[l] == cn[j] && l < j);
     order[rk] = j;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-    const int r = t % p, c = t / p, src = order[c];
-    US[t] = M[r + (size_t)src * p];
-    Vout[t] = V[r + (size_t)src * p];
-  }
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int c = 0; c < p; ++c) {
-      const double s = norms[order[c]];
-      sig[c] = s;
-      tot = fma(s, s, tot);
-    }
-    // smallest k with tail(k) <= tol ||M||_F, at least 1, at most cap
-    int k = p;
-    double tail = 0.0;
-    const double bound = tol * tol * tot;
-    for (int c = p - 1; c >= 0; --c) {
-      const double s = norms[order[c]];
-      const double nt = fma(s, s, tail);
+    const double bound = tol * tol * fro2;
+    double tail = qr_tail2;
+    int k = pd;
+    for (int c = pd - 1; c >= 0; --c) {
+      const double sv = cn[order[c]];
+      const double nt = fma(sv, sv, tail);
       if (nt <= bound) {
         tail = nt;
         k = c;
@@ -506,33 +756,73 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi_svd(const double* __rest
         break;
       }
     }
-    if (tot == 0.0) k = 1;
     if (k < 1) k = 1;
     if (k > cap) k = cap;
-    double dis = 0.0;
-    for (int c = p - 1; c >= k; --c) {
-      const double s = norms[order[c]];
-      dis = fma(s, s, dis);
-    }
-    *k_out = k;
+    double dis = qr_tail2;
+    for (int c = pd - 1; c >= k; --c) dis = fma(cn[order[c]], cn[order[c]], dis);
+    for (int c = 0; c < p; ++c) sig[c] = c < pd ? cn[order[c]] : 0.0;
+    s_k = k;
+    info[0] = k;
+    info[1] = pd;
+    info[2] = sweep + 1;
     tail_out[0] = sqrt(dis);
-    tail_out[1] = sqrt(tot);
-    if (sweep >= JAC_MAX_SWEEPS) atomicOr(status, DEV_JACOBI_NOCONV);
-    if (sweeps_out) *sweeps_out = sweep + 1;
+    tail_out[1] = sqrt(fro2);
+    if (sweep >= SVD_MAX_SWEEPS) atomicOr(status, DEV_JACOBI_NOCONV);
+  }
+  __syncthreads();
+  const int k = s_k;
+  // US = P (L V): row piv[r] of US is row r of L V
+  for (int t = threadIdx.x; t < p * k; t += blockDim.x) {
+    const int r = t % p, c = t / p;
+    US[piv[r] + (size_t)c * p] = c < pd ? A[r + (size_t)order[c] * p] : 0.0;
+  }
+  // Vout = Q [V; 0]: one warp per column, reflectors applied last-to-first
+  for (int c = w; c < k; c += nw) {
+    double z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = lane + 32 * u;
+      z[u] = (c < pd && r < pd) ? J[r + (size_t)order[c] * pd] : ((c >= pd && r == c) ? 1.0 : 0.0);
+    }
+    for (int kk = pd - 1; kk >= 0; --kk) {
+      const double tk = htau[kk];
+      if (tk == 0.0) continue;
+      double d = 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = lane + 32 * u;
+        if (r < p && r >= kk) d = fma(r == kk ? 1.0 : HV[r + (size_t)kk * p], z[u], d);
+      }
+      d = warp_sum(d) * tk;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = lane + 32 * u;
+        if (r < p && r >= kk) z[u] = fma(-d, r == kk ? 1.0 : HV[r + (size_t)kk * p], z[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = lane + 32 * u;
+      if (r < p) Vout[r + (size_t)c * p] = z[u];
+    }
   }
 }
 
 void jacobi_svd(Exec& ex, const double* M, int p, double tol, int cap, double* US, double* V, double* sig,
                 int* k_out, double* tail_out) {
   TT_REQUIRE(p >= 1 && p <= 112, TT_ERR_ARG);
+  Scope sc(*ex.ar);
+  double* scr = ex.ar->get<double>((size_t)p * p + p);
   if (ex.dry) return;
   const size_t smem = 2 * (size_t)p * p * 8;
-  TT_CUDA(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // algorithmic work: a nominal 6 sweeps of p(p-1)/2 pair rotations, each
-  // three length-p dot products and four length-p column updates
-  TT_KERNEL(ex, K_JACOBI, 6.0 * (p * (p - 1) / 2.0) * 18.0 * p, 8.0 * 4.0 * p * (double)p,
-            k_jacobi_svd<<<1, JAC_THREADS, smem, ex.s>>>(M, p, tol, cap, US, V, sig, k_out, tail_out,
-                                                         ex.dev_status, nullptr));
+  smem_attr_once(k_svd_small);
+  // deflation level: far below the truncation tolerance and the 1e-10 parity bar
+  const double defl = std::max(std::min(1e-13, 1e-2 * tol), 1e-15);
+  // algorithmic work: pivoted QR (4/3 p^3) plus a nominal 3 Jacobi sweeps
+  TT_KERNEL(ex, K_JACOBI, 4.0 / 3.0 * p * (double)p * p + 3.0 * (p * (p - 1) / 2.0) * 18.0 * p,
+            8.0 * 4.0 * p * (double)p,
+            k_svd_small<<<1, SVD_THREADS, smem, ex.s>>>(M, p, tol, cap, defl, US, V, sig, k_out, tail_out, scr,
+                                                        ex.dev_status));
 }
 
 // ============================================================== maxvol
@@ -706,8 +996,7 @@ void maxvol(Exec& ex, const double* U, int n, int r, double delta, int max_iter,
   if (ex.dry) return;
   const size_t smem = (size_t)n;
   TT_REQUIRE(smem <= 200 * 1024, TT_ERR_ARG);
-  if (smem > 48 * 1024)
-    TT_CUDA(cudaFuncSetAttribute(k_maxvol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  smem_attr_once(k_maxvol);
   // algorithmic work: LU pivoting n r^2 plus B = U P^{-1} 2 n r^2
   TT_KERNEL(ex, K_MAXVOL, 3.0 * n * (double)r * r, 8.0 * 3.0 * n * (double)r,
             k_maxvol<<<1, MV_THREADS, smem, ex.s>>>(U, n, r, delta, max_iter, W, B, P, I, ex.dev_status));

@@ -7,6 +7,8 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <functional>
+#include <mutex>
 #include <vector>
 
 #include "../../include/tt_fv.h"
@@ -100,6 +102,15 @@ struct TT {
   double* b = nullptr;
 };
 
+// Streams and events for concurrent host tasks (owned by a solver context).
+struct StreamPool {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaStream_t stream(size_t i);
+  cudaEvent_t event(size_t i);
+  ~StreamPool();
+};
+
 // Execution context of one call chain.
 struct Exec {
   cudaStream_t s = nullptr;
@@ -114,7 +125,14 @@ struct Exec {
   long long taylor_iters = 0, cap_hits = 0;
   double flops = 0.0, bytes = 0.0;
   Prof* prof = nullptr;             // per-class event timing when prof->on
+  StreamPool* pool = nullptr;       // streams for parallel_tasks (null: run tasks in order)
 };
+
+// Run body(child, i) for i < ntasks as concurrent host threads, each on its
+// own stream (ordered after ex.s) with its own slice of the free arena; ex.s
+// then waits for every task.  Counters and profile records merge into ex.
+// Tasks must be independent.  The first task error is rethrown.
+void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>& body);
 
 // Bracket one kernel launch: counts it, checks the launch, adds its
 // algorithmic flops/bytes to the totals and, when profiling, times it.
@@ -129,6 +147,15 @@ void prof_flush(Exec& ex);  // after a stream sync: accumulate finished records
   } while (0)
 
 // ---------------------------------------------------------------- helpers
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per kernel and process (the attribute is global to the function, so it
+// must not be changed per launch while other host threads launch it).
+int smem_optin_max();
+cudaError_t smem_attr_once_impl(const void* fn);
+template <typename K>
+inline void smem_attr_once(K kernel) {
+  TT_CUDA(smem_attr_once_impl(reinterpret_cast<const void*>(kernel)));
+}
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
 
 // Copy n ints/doubles from device to the pinned buffer and wait (a sync point).
@@ -145,14 +172,16 @@ void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, cons
 // sum of squares of an m x n column-major matrix -> device double
 void sumsq(Exec& ex, const double* X, int m, int n, long ld, double* out);
 
-// Householder TSQR of a tall m x p matrix (m >= p, p <= 112).
+// Householder TSQR of a tall m x p matrix (p <= 112): row blocks of mb0
+// rows factored independently, then a binary tree of merges of stacked
+// triangular factors; Q is kept implicit.
 struct QRTree {
-  int m = 0, p = 0, levels = 0;
-  std::vector<int> mrows;      // rows of the input of each level
-  std::vector<int> mb;         // block rows per level
-  std::vector<int> nb;         // blocks per level
-  std::vector<double*> V;      // per level: nb*mb x p reflectors (unit diag implicit)
-  std::vector<double*> tau;    // per level: nb x p
+  int m = 0, p = 0, mb0 = 0, nb0 = 0;
+  double* V0 = nullptr;        // leaf reflectors: nb0 blocks of mb0 x p (unit diagonal implicit)
+  double* tau0 = nullptr;      // nb0 x p
+  std::vector<int> nin;        // inputs of each merge level (bottom-up)
+  std::vector<double*> Vm;     // per merge level: nodes x (p x p) bottom-block reflectors
+  std::vector<double*> taum;   // per merge level: nodes x p
   double* R = nullptr;         // final p x p upper triangle (ld p)
 };
 void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t);
