@@ -97,6 +97,13 @@ typedef struct {
   double flops;               /* algorithmic FP64 flops issued */
   double bytes;               /* algorithmic bytes moved by the core kernels */
   uint32_t device_status;     /* latched device error bits (0 = none) */
+  int64_t svd_calls;          /* small SVDs */
+  int64_t svd_p_sum;          /* sum of their sizes p */
+  int64_t svd_pd_sum;         /* sum of their deflated ranks */
+  int64_t svd_sweeps_sum;     /* sum of their Jacobi sweeps */
+  double section_ms[6];       /* host wall time per stage section: faces, side fluxes + lambda,
+                                 LLF combination, quadrature/difference, forward-Euler rounds,
+                                 SSP combination rounds */
 } tt_fv_stats;
 
 typedef struct tt_fv_ctx tt_fv_ctx;

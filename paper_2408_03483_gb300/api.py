@@ -184,7 +184,8 @@ class Solver:
     def stats(self):
         st = C.tt_fv_stats()
         C.check("tt_fv_stats_get", self.lib.tt_fv_stats_get(self.h, ctypes.byref(st)))
-        return {k: (list(getattr(st, k)) if k == "rank" else getattr(st, k)) for k, _ in st._fields_}
+        return {k: (list(getattr(st, k)) if k in ("rank", "section_ms") else getattr(st, k))
+                for k, _ in st._fields_}
 
     def profile(self, enable=True):
         C.check("tt_fv_profile", self.lib.tt_fv_profile(self.h, 1 if enable else 0))

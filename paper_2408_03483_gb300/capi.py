@@ -50,7 +50,9 @@ class tt_fv_stats(ctypes.Structure):
                 ("cross_sweeps", ctypes.c_int64), ("taylor_iters", ctypes.c_int64),
                 ("cap_hits", ctypes.c_int64), ("qb_attempts", ctypes.c_int64),
                 ("qb_uncertified", ctypes.c_int64), ("flops", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("device_status", ctypes.c_uint32)]
+                ("bytes", ctypes.c_double), ("device_status", ctypes.c_uint32),
+                ("svd_calls", ctypes.c_int64), ("svd_p_sum", ctypes.c_int64), ("svd_pd_sum", ctypes.c_int64),
+                ("svd_sweeps_sum", ctypes.c_int64), ("section_ms", ctypes.c_double * 6)]
 
 
 TT_K_NAMES = ["gemm", "form_hadamard", "qr", "qr_apply", "jacobi_svd", "maxvol", "cross_eval", "stencil",

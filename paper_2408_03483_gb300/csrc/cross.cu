@@ -161,11 +161,16 @@ __global__ void k_eval_rows(EvalArgs e, int n2, const int* __restrict__ I, int n
 }
 
 // ============================================================== small kernels
-// Wk = US[:, :k] with column j divided by sig[j] (e_j where sig[j] == 0)
+// Wk = US[:, :k] with column j divided by sig[j] (e_j where sig[j] == 0);
+// one reciprocal per column
 __global__ void k_unscale(const double* US, const double* sig, int p, int k, double* W) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p * k; t += gridDim.x * blockDim.x) {
-    const int i = t % p, j = t / p;
-    W[t] = sig[j] > 0.0 ? US[t] / sig[j] : (i == j ? 1.0 : 0.0);
+  for (int j = blockIdx.x; j < k; j += gridDim.x) {
+    __shared__ double inv;
+    if (threadIdx.x == 0) inv = sig[j] > 0.0 ? 1.0 / sig[j] : 0.0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+      W[i + (size_t)j * p] = sig[j] > 0.0 ? US[i + (size_t)j * p] * inv : (i == j ? 1.0 : 0.0);
+    __syncthreads();
   }
 }
 // G[a + b*k] = U[I[a] + b*n] (rows I of U, k x c)
@@ -182,6 +187,8 @@ __global__ void __launch_bounds__(1024) k_small_solve(const double* P, int k, co
   double* A = sm;  // k x (k + c), column-major with ld k
   const int w = k + c;
   __shared__ int piv;
+  __shared__ double s_inv;
+  __shared__ double inv_diag[128];
   for (int t = threadIdx.x; t < k * w; t += blockDim.x) {
     const int i = t % k, j = t / k;
     A[t] = j < k ? P[i + (size_t)j * k] : G[i + (size_t)(j - k) * k];
@@ -209,22 +216,31 @@ __global__ void __launch_bounds__(1024) k_small_solve(const double* P, int k, co
         A[pr + (size_t)j * k] = x;
       }
     __syncthreads();
-    const double d = A[col + (size_t)col * k];
+    if (threadIdx.x == 0) {
+      const double d = A[col + (size_t)col * k];
+      s_inv = d != 0.0 ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    const double invd = s_inv;
     for (long t = threadIdx.x; t < (long)(k - col - 1) * (w - col - 1); t += blockDim.x) {
       const int i = col + 1 + int(t % (k - col - 1)), j = col + 1 + int(t / (k - col - 1));
-      const double f = d != 0.0 ? A[i + (size_t)col * k] / d : 0.0;
+      const double f = A[i + (size_t)col * k] * invd;
       A[i + (size_t)j * k] = fma(-f, A[col + (size_t)j * k], A[i + (size_t)j * k]);
     }
     __syncthreads();
   }
   // back substitution, one thread per right-hand side column
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double d = A[i + (size_t)i * k];
+    inv_diag[i] = d != 0.0 ? 1.0 / d : 0.0;
+  }
+  __syncthreads();
   for (int j = threadIdx.x; j < c; j += blockDim.x) {
     double* x = A + (size_t)(k + j) * k;
     for (int i = k - 1; i >= 0; --i) {
       double s = x[i];
       for (int l = i + 1; l < k; ++l) s = fma(-A[i + (size_t)l * k], x[l], s);
-      const double d = A[i + (size_t)i * k];
-      x[i] = d != 0.0 ? s / d : 0.0;
+      x[i] = s * inv_diag[i];
     }
   }
   __syncthreads();
@@ -294,12 +310,12 @@ static int orth_left(Exec& ex, const double* C, int m, int c, double tol, int ca
   int* kd = ex.ar->get<int>(4);
   double* tail = ex.ar->get<double>(2);
   jacobi_svd(ex, t.R, c, tol, cap, US, V, sig, kd, tail);
-  int k = fetch_int(ex, kd);
+  int k = fetch_svd_info(ex, kd, c);
   if (ex.dry) k = std::min(cap, c);
   k = std::min(k, m);
   double* W = ex.ar->get<double>((size_t)c * k);
   if (!ex.dry)
-    TT_KERNEL(ex, K_OTHER, (double)c * k, 16.0 * c * k, k_unscale<<<ceil_div((long)c * k, 256), 256, 0, ex.s>>>(US, sig, c, k, W));
+    TT_KERNEL(ex, K_OTHER, (double)c * k, 16.0 * c * k, k_unscale<<<k, 128, 0, ex.s>>>(US, sig, c, k, W));
   tsqr_apply(ex, t, W, k, c, U, m);
   return k;
 }

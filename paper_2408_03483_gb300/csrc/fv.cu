@@ -16,6 +16,7 @@
 #include <cstring>
 #include <new>
 #include <algorithm>
+#include <chrono>
 
 #include "coeffs.cuh"
 #include "tt_ops.cuh"
@@ -152,6 +153,7 @@ struct Solver {
   double h_dbl[16];
   Prof prof;
   StreamPool pool;
+  double section_ms[6] = {};
   ~Solver() {
     for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
     for (const Prof::Rec& r : prof.pending) {
@@ -357,6 +359,15 @@ static TT quad_and_difference(Solver& S, Exec& ex, const TT& Fh, int d) {
 // Independent pieces run as concurrent tasks: the 12 WENO face crosses, the
 // 4 side fluxes with the 2 lambda crosses, the 6 LLF combinations, the 3
 // final rounds.
+struct SectionTimer {
+  double& acc;
+  std::chrono::steady_clock::time_point t0;
+  explicit SectionTimer(double& a) : acc(a), t0(std::chrono::steady_clock::now()) {}
+  ~SectionTimer() {
+    acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
 static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT out[3]) {
   Scope sc(*ex.ar);
   const tt_fv_params& p = S.p;
@@ -369,6 +380,7 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
     f1[d] = d == 0 ? p.nx : S.nq * p.nx;
     f2[d] = d == 0 ? S.nq * p.ny : p.ny;
   }
+  SectionTimer* st0 = new SectionTimer(S.section_ms[0]);
   if (p.recon == TT_WENO5) {
     for (int d = 0; d < 2; ++d)
       for (int c = 0; c < 3; ++c) {
@@ -383,6 +395,7 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
     for (int d = 0; d < 2; ++d)
       for (int c = 0; c < 3; ++c) faces_linear(S, ex, Q[c], d, qm[d][c], qp[d][c]);
   }
+  delete st0;
   for (int d = 0; d < 2; ++d) {
     if (p.eqn == TT_LINEAR) {
       std::vector<Term> fl[3];
@@ -404,6 +417,8 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
       lam[d] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
       for (int c = 0; c < 3; ++c) Fh[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
     }
+    {
+    SectionTimer st1(S.section_ms[1]);
     parallel_tasks(ex, 6, [&](Exec& cx, int t) {
       if (t < 4) {
         const int d = t / 2, sd = t % 2;
@@ -413,15 +428,20 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
         face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, lam[d]);
       }
     });
+    }
     for (int d = 0; d < 2; ++d) {
       const int k = d == 0 ? 1 : 2;
       F[d][0][0] = qm[d][k];
       F[d][1][0] = qp[d][k];
     }
-    parallel_tasks(ex, 6, [&](Exec& cx, int t) {
-      const int d = t / 3, c = t % 3;
-      llf_component(S, cx, F[d][0][c], F[d][1][c], lam[d], qm[d][c], qp[d][c], Fh[d][c]);
-    });
+    {
+      SectionTimer st2(S.section_ms[2]);
+      parallel_tasks(ex, 6, [&](Exec& cx, int t) {
+        const int d = t / 3, c = t % 3;
+        llf_component(S, cx, F[d][0][c], F[d][1][c], lam[d], qm[d][c], qp[d][c], Fh[d][c]);
+      });
+    }
+    SectionTimer st3(S.section_ms[3]);
     for (int d = 0; d < 2; ++d)
       for (int c = 0; c < 3; ++c) {
         TT D = quad_and_difference(S, ex, Fh[d][c], d);
@@ -432,6 +452,7 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
     terms[1].push_back(Term{p.dt * p.f, Q[2]});
     terms[2].push_back(Term{-p.dt * p.f, Q[1]});
   }
+  SectionTimer st4(S.section_ms[4]);
   parallel_tasks(ex, 3, [&](Exec& cx, int c) { round_sum(cx, terms[c], p.tol, cap, out[c]); });
 }
 
@@ -449,10 +470,12 @@ static void run_stage(Solver& S, Exec& ex, int stage) {
   if (stage == 0) {
     for (int c = 0; c < 3; ++c) copy_tt(ex, f[c], S.Qs[c]);
   } else if (stage == 1) {
+    SectionTimer st5(S.section_ms[5]);
     parallel_tasks(ex, 3, [&](Exec& cx, int c) {
       round_sum(cx, {Term{0.75, S.Qn[c]}, Term{0.25, f[c]}}, p.tol, p.rank_cap, S.Qs[c]);
     });
   } else {
+    SectionTimer st5(S.section_ms[5]);
     parallel_tasks(ex, 3, [&](Exec& cx, int c) {
       round_sum(cx, {Term{1.0 / 3.0, S.Qn[c]}, Term{2.0 / 3.0, f[c]}}, p.tol, p.rank_cap, S.Qn[c]);
     });
@@ -694,6 +717,11 @@ tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* o) {
   o->qb_uncertified = ex.qb_uncertified;
   o->flops = ex.flops;
   o->bytes = ex.bytes;
+  o->svd_calls = ex.svd_calls;
+  o->svd_p_sum = ex.svd_p;
+  o->svd_pd_sum = ex.svd_pd;
+  o->svd_sweeps_sum = ex.svd_sweeps;
+  for (int i = 0; i < 6; ++i) o->section_ms[i] = S.section_ms[i];
   unsigned st = 0;
   if (cudaMemcpyAsync(&st, ex.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, S.s) != cudaSuccess ||
       cudaStreamSynchronize(S.s) != cudaSuccess)

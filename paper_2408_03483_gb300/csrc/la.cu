@@ -47,6 +47,25 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
+// Householder reflector of x = [alpha; tail] with sigma = ||tail||^2 known in
+// every lane: beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, scale =
+// 1/(alpha - beta).  GB300 builds FP64 sqrt/division from its few FP64 FMA
+// units, so lane 0 alone evaluates them and broadcasts the results.
+__device__ __forceinline__ void householder_params(double alpha, double sigma, double& beta, double& tau,
+                                                   double& scale) {
+  double b = alpha, t = 0.0, sc = 0.0;
+  if ((threadIdx.x & 31) == 0 && sigma > 0.0) {
+    const double nrm = sqrt(fma(alpha, alpha, sigma));
+    b = alpha >= 0.0 ? -nrm : nrm;
+    const double d = alpha - b;
+    sc = 1.0 / d;
+    t = -d / b;
+  }
+  beta = __shfl_sync(0xffffffffu, b, 0);
+  tau = __shfl_sync(0xffffffffu, t, 0);
+  scale = __shfl_sync(0xffffffffu, sc, 0);
+}
+
 // ============================================================== GEMM
 // C = alpha * A B + beta * C with generic strides; tile 32x32, BK 16,
 // 256 threads x 4 outputs; deterministic split-K through a partial buffer.
@@ -237,14 +256,10 @@ __device__ void cta_householder_qr(double* A, int mb, int p, double* tau_out) {
     double* col = A + (size_t)j * mb;
     if (w == 0) {
       const double sigma = next_sigma, alpha = col[j];
-      double tau = 0.0, beta = alpha;
-      if (sigma > 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, sigma));
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        const double scale = 1.0 / (alpha - beta);
+      double tau, beta, scale;
+      householder_params(alpha, sigma, beta, tau, scale);
+      if (sigma > 0.0)
         for (int i = j + 1 + lane; i < mb; i += 32) col[i] *= scale;
-      }
       if (lane == 0) {
         col[j] = beta;
         s_tau = tau;
@@ -330,14 +345,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restric
       for (int i = lane; i <= j; i += 32) sg = fma(bj[i], bj[i], sg);
       sg = warp_sum(sg);
       const double alpha = T[j + (size_t)j * p];
-      double tau = 0.0, beta = alpha;
-      if (sg > 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, sg));
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        const double scale = 1.0 / (alpha - beta);
+      double tau, beta, scale;
+      householder_params(alpha, sg, beta, tau, scale);
+      if (sg > 0.0)
         for (int i = lane; i <= j; i += 32) bj[i] *= scale;
-      }
       if (lane == 0) {
         T[j + (size_t)j * p] = beta;
         s_tau = tau;
@@ -632,14 +643,10 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
       for (int i = k + 1 + lane; i < p; i += 32) sg = fma(col[i], col[i], sg);
       sg = warp_sum(sg);
       const double alpha = col[k];
-      double tau = 0.0, beta = alpha;
-      if (sg > 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, sg));
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        const double scale = 1.0 / (alpha - beta);
+      double tau, beta, scale;
+      householder_params(alpha, sg, beta, tau, scale);
+      if (sg > 0.0)
         for (int i = k + 1 + lane; i < p; i += 32) col[i] *= scale;
-      }
       if (lane == 0) {
         col[k] = beta;
         s_tau = tau;
@@ -683,7 +690,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) J[t] = ((t % pd) == (t / pd)) ? 1.0 : 0.0;
   __syncthreads();
   const int q = pd + (pd & 1);
-  const double eps = DBL_EPSILON * p;
+  const double eps = DBL_EPSILON * p, eps2 = eps * eps;
   int sweep = 0;
   for (; sweep < SVD_MAX_SWEEPS && pd > 1; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
@@ -705,10 +712,17 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (al <= thr || be <= thr || fabs(ga) <= eps * sqrt(al) * sqrt(be)) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-        const double c = 1.0 / sqrt(fma(t, t, 1.0)), sn = c * t;
+        // |ga| <= eps sqrt(al be), compared in squares (no FP64 roots per lane)
+        if (al <= thr || be <= thr || ga * ga <= eps2 * al * be) continue;
+        double c = 1.0, sn = 0.0;
+        if (lane == 0) {  // rotation angle in one lane, then broadcast
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          c = 1.0 / sqrt(fma(t, t, 1.0));
+          sn = c * t;
+        }
+        c = __shfl_sync(0xffffffffu, c, 0);
+        sn = __shfl_sync(0xffffffffu, sn, 0);
         for (int r = lane; r < p; r += 32) {
           const double x = ci[r], y = cj[r];
           ci[r] = c * x - sn * y;
@@ -873,6 +887,7 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
   __shared__ double rv[33];
   __shared__ long ri[33];
   __shared__ int piv[128];
+  __shared__ double s_inv;
   extern __shared__ unsigned char freeflag[];  // n bytes
   for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) W[t] = U[t];
   for (int i = threadIdx.x; i < n; i += blockDim.x) freeflag[i] = 1;
@@ -890,12 +905,15 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
     }
     __syncthreads();
     const double pv = W[pr + (size_t)k * n];
+    if (threadIdx.x == 0) s_inv = pv != 0.0 ? 1.0 / pv : 0.0;
+    __syncthreads();
+    const double ipv = s_inv;
     if (pv != 0.0 && k + 1 < r) {
       // column k is read only (it is not used again), columns k+1.. updated
       for (long t = threadIdx.x; t < (long)n * (r - k - 1); t += blockDim.x) {
         const int i = int(t % n), c = k + 1 + int(t / n);
         if (freeflag[i]) {
-          const double f = W[i + (size_t)k * n] / pv;
+          const double f = W[i + (size_t)k * n] * ipv;
           W[i + (size_t)c * n] = fma(-f, W[pr + (size_t)c * n], W[i + (size_t)c * n]);
         }
       }
@@ -935,9 +953,11 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
       }
     __syncthreads();
     const double d = P[k + (size_t)k * r];
+    if (threadIdx.x == 0) s_inv = d != 0.0 ? 1.0 / d : 0.0;
     __syncthreads();
+    const double invd = s_inv;
     if (d != 0.0) {
-      for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) P[k + (size_t)c * r] /= d;
+      for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) P[k + (size_t)c * r] *= invd;
     }
     __syncthreads();
     for (long t = threadIdx.x; t < (long)r * 2 * r; t += blockDim.x) {
@@ -972,14 +992,15 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
     best = block_argmax(best, rv, ri);
     if (best.v <= 1.0 + delta) break;
     const int bi = int(best.idx / r), bj = int(best.idx % r);
-    const double pivv = B[bi + (size_t)bj * n];
+    if (threadIdx.x == 0) s_inv = 1.0 / B[bi + (size_t)bj * n];
     // B -= B[:, j] (B[i, :] - e_j)^T / pivot ; use W as scratch for the column and row
     for (int i = threadIdx.x; i < n; i += blockDim.x) W[i] = B[i + (size_t)bj * n];
     for (int j = threadIdx.x; j < r; j += blockDim.x) W[n + j] = B[bi + (size_t)j * n] - (j == bj ? 1.0 : 0.0);
     __syncthreads();
+    const double ipiv = s_inv;
     for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) {
       const int i = int(t % n), j = int(t / n);
-      B[t] = fma(-W[i] / pivv, W[n + j], B[t]);
+      B[t] = fma(-W[i] * ipiv, W[n + j], B[t]);
     }
     if (threadIdx.x == 0) I[bj] = bi;
     __syncthreads();

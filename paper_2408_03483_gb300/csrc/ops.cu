@@ -183,6 +183,20 @@ int fetch_int(Exec& ex, const int* d) {
   prof_flush(ex);
   return ex.h_pinned[0];
 }
+int fetch_svd_info(Exec& ex, const int* d, int p) {
+  if (ex.dry) return -1;
+  TT_CUDA(cudaMemcpyAsync(ex.h_pinned, d, 3 * sizeof(int), cudaMemcpyDeviceToHost, ex.s));
+  TT_CUDA(cudaStreamSynchronize(ex.s));
+  ex.syncs++;
+  prof_flush(ex);
+  ex.svd_calls++;
+  ex.svd_p += p;
+  ex.svd_pd += ex.h_pinned[1];
+  ex.svd_sweeps += ex.h_pinned[2];
+  ex.jacobi_sweeps += ex.h_pinned[2];
+  return ex.h_pinned[0];
+}
+
 void fetch_doubles(Exec& ex, const double* d, int n, double* out) {
   if (ex.dry) {
     for (int i = 0; i < n; ++i) out[i] = 0.0;
@@ -243,7 +257,7 @@ static RoundInfo round_factored(Exec& ex, const double* A, const double* B, int 
   int* kd = ex.ar->get<int>(4);
   double* tail = ex.ar->get<double>(2);
   jacobi_svd(ex, M, R, tol, cap, US, V, sig, kd, tail);
-  int k = fetch_int(ex, kd);
+  int k = fetch_svd_info(ex, kd, R);
   if (ex.dry) k = std::min(cap, R);
   double tl[2];
   fetch_doubles(ex, tail, 2, tl);
@@ -286,7 +300,7 @@ RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int
     double* V = ex.ar->get<double>((size_t)s * s);
     double* sig = ex.ar->get<double>(s);
     jacobi_svd(ex, M, s, tol, cap, US, V, sig, kd, tail);
-    int k = fetch_int(ex, kd);
+    int k = fetch_svd_info(ex, kd, s);
     if (ex.dry) k = std::min(cap, s);
     double tl[2];
     fetch_doubles(ex, tail, 2, tl);
@@ -354,7 +368,7 @@ RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int
   double* V = ex.ar->get<double>((size_t)p * p);
   double* sig = ex.ar->get<double>(p);
   jacobi_svd(ex, M, p, tol, cap, US, V, sig, kd, tail);
-  int k = fetch_int(ex, kd);
+  int k = fetch_svd_info(ex, kd, p);
   if (ex.dry) k = std::min(cap, p);
   double tl[2];
   fetch_doubles(ex, tail, 2, tl);

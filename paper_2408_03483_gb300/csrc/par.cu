@@ -71,6 +71,10 @@ static void merge_counters(Exec& dst, const Exec& src) {
   dst.cross_sweeps += src.cross_sweeps;
   dst.taylor_iters += src.taylor_iters;
   dst.cap_hits += src.cap_hits;
+  dst.svd_calls += src.svd_calls;
+  dst.svd_p += src.svd_p;
+  dst.svd_pd += src.svd_pd;
+  dst.svd_sweeps += src.svd_sweeps;
   dst.flops += src.flops;
   dst.bytes += src.bytes;
 }
@@ -102,6 +106,7 @@ void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>&
       c.ex.ar = ex.dry ? &c.ar : ex.ar;
       c.ex.rounds = c.ex.qb_attempts = c.ex.qb_uncertified = c.ex.syncs = 0;
       c.ex.jacobi_sweeps = c.ex.cross_calls = c.ex.cross_sweeps = c.ex.taylor_iters = c.ex.cap_hits = 0;
+      c.ex.svd_calls = c.ex.svd_p = c.ex.svd_pd = c.ex.svd_sweeps = 0;
       c.ex.flops = c.ex.bytes = 0.0;
       body(c.ex, i);
       merge_counters(ex, c.ex);

@@ -123,6 +123,7 @@ struct Exec {
   long long rounds = 0, qb_attempts = 0, qb_uncertified = 0, syncs = 0;
   long long jacobi_sweeps = 0, cross_calls = 0, cross_sweeps = 0;
   long long taylor_iters = 0, cap_hits = 0;
+  long long svd_calls = 0, svd_p = 0, svd_pd = 0, svd_sweeps = 0;
   double flops = 0.0, bytes = 0.0;
   Prof* prof = nullptr;             // per-class event timing when prof->on
   StreamPool* pool = nullptr;       // streams for parallel_tasks (null: run tasks in order)
@@ -160,6 +161,9 @@ inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
 
 // Copy n ints/doubles from device to the pinned buffer and wait (a sync point).
 int fetch_int(Exec& ex, const int* d);
+// Reads the small-SVD info triple (k, deflated rank, sweeps) of a p x p SVD,
+// accounts it, and returns k.
+int fetch_svd_info(Exec& ex, const int* d, int p);
 void fetch_doubles(Exec& ex, const double* d, int n, double* out);
 
 // ---------------------------------------------------------------- kernels (la.cu)
