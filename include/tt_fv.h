@@ -182,6 +182,20 @@ size_t tt_round_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t 
 tt_status tt_round(const tt2* x, double tol, int32_t rank_cap, tt2* y, double* err_out,
                    void* ws, size_t ws_bytes, void* stream);
 
+/* tt_round without any device allocation, for callers that cannot allocate
+ * device memory (no cudaMalloc available to them, or a fixed memory footprint
+ * that must not grow).  The paper has no counterpart: this is a packaging
+ * variant of tt_round.  Same arguments and results as tt_round; the scratch is
+ * a 32 MiB array in this library's device memory (held by every GPU that loads
+ * the library until process exit) instead of a caller workspace, so sizes
+ * whose tt_round_workspace_size exceeds 32 MiB are rejected with TT_ERR_ARG.
+ * The first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  Every call
+ * shares the one array and overwrites it: calls that overlap on the GPU (two
+ * streams, two threads) race, so serialise them. */
+tt_status tt_round_noalloc(const tt2* x, double tol, int32_t rank_cap, tt2* y, double* err_out,
+                           void* stream);
+
 /* y = round(x o z, tol): the TT Hadamard product (Sec. 4.2, cores are
  * row-wise Kronecker products of rank x.rank * z.rank) followed by rounding. */
 size_t tt_round_hadamard_workspace_size(int32_t n1, int32_t n2, int32_t rank_x, int32_t rank_z,

@@ -86,6 +86,7 @@ SIGNATURES = {
     "tt_launch_count": (ctypes.c_uint64, []),
     "tt_round_workspace_size": (_sz, [_i32, _i32, _i32, _i32]),
     "tt_round": (ctypes.c_int, [_P(tt2), _d, _i32, _P(tt2), _P(_d), _vp, _sz, _vp]),
+    "tt_round_noalloc": (ctypes.c_int, [_P(tt2), _d, _i32, _P(tt2), _P(_d), _vp]),
     "tt_round_hadamard_workspace_size": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "tt_round_hadamard": (ctypes.c_int, [_P(tt2), _P(tt2), _d, _i32, _P(tt2), _vp, _sz, _vp]),
     "tt_cross_workspace_size": (_sz, [_i32, _i32, _i32, _i32, _i32]),
