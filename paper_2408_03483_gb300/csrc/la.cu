@@ -309,72 +309,125 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const double* __restri
   }
 }
 
-// Merge of two stacked upper-triangular factors [T; B] (p x p each) by
-// Householder reflectors that touch row j of T and rows 0..j of B only:
-// (2/3) p^3 flops instead of the (10/3) p^3 of a dense 2p x p QR.  An odd
-// last input passes through unchanged (tau = 0).
-__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restrict__ Rin, int nin, int p,
-                                                         double* Rout, double* Vm, double* taum) {
+// Merge of up to g stacked upper-triangular factors [T; B_1; ...; B_{g-1}]
+// (p x p each) by Householder reflectors that touch row j of T and rows 0..j
+// of each B_b only.  Reflectors are kept unnormalised: v = [alpha - beta at T
+// row j; B_b(0..j, j)], tau = -1 / (beta (alpha - beta)), so no scaling pass
+// is needed.  Columns are spread over lanes (lane = column within a group of
+// 32), the bottom blocks over warps; a node with one input passes it through.
+__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restrict__ Rin, int nin, int p, int g,
+                                                         double* Rout, double* Vm, double* vtop, double* taum) {
   extern __shared__ double sm[];
   const int node = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* T = sm;
-  double* B = sm + (size_t)p * p;
-  const double* Rt = Rin + (size_t)(2 * node) * p * p;
+  const int first = node * g, ng = min(g, nin - first);
   double* Ro = Rout + (size_t)node * p * p;
-  double* Vo = Vm + (size_t)node * p * p;
+  double* Vo = Vm + (size_t)node * g * p * p;  // bottom blocks 1..ng-1 at Vo + b*p*p
+  double* vt = vtop + (size_t)node * p;
   double* to = taum + (size_t)node * p;
-  if (2 * node + 1 >= nin) {
-    for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-      Ro[t] = Rt[t];
-      Vo[t] = 0.0;
+  const double* Ri = Rin + (size_t)first * p * p;
+  if (ng == 1) {
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) Ro[t] = Ri[t];
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+      to[j] = 0.0;
+      vt[j] = 0.0;
     }
-    for (int j = threadIdx.x; j < p; j += blockDim.x) to[j] = 0.0;
     return;
   }
-  const double* Rb = Rt + (size_t)p * p;
-  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-    T[t] = Rt[t];
-    B[t] = Rb[t];
+  double* T = sm;                       // block 0 (p x p)
+  double* part = sm + (size_t)ng * p * p;  // [slice][column] partial sums
+  __shared__ double s_tau, s_vj, s_sig;
+  for (int t = threadIdx.x; t < ng * p * p; t += blockDim.x) T[t] = Ri[t];
+  const int G = (p + 31) / 32;
+  const int S = max(1, nw / G);
+  const int grp = w % G, sl = w / G;
+  const int c = grp * 32 + lane;  // this lane's column
+  const bool active = (sl < S) && (c < p);
+  // norm below the diagonal of column 0: sum over bottoms of B_b[0,0]^2
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sg = 0.0;
+    for (int b = 1; b < ng; ++b) sg = fma(T[(size_t)b * p * p], T[(size_t)b * p * p], sg);
+    s_sig = sg;
   }
   __syncthreads();
-  __shared__ double s_tau;
   for (int j = 0; j < p; ++j) {
-    double* bj = B + (size_t)j * p;
-    if (w == 0) {
-      double sg = 0.0;
-      for (int i = lane; i <= j; i += 32) sg = fma(bj[i], bj[i], sg);
-      sg = warp_sum(sg);
-      const double alpha = T[j + (size_t)j * p];
-      double tau, beta, scale;
-      householder_params(alpha, sg, beta, tau, scale);
-      if (sg > 0.0)
-        for (int i = lane; i <= j; i += 32) bj[i] *= scale;
-      if (lane == 0) {
-        T[j + (size_t)j * p] = beta;
-        s_tau = tau;
-        to[j] = tau;
+    if (threadIdx.x == 0) {
+      const double sg = s_sig, alpha = T[j + (size_t)j * p];
+      double tau = 0.0, vj = 0.0, beta = alpha;
+      if (sg > 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, sg));
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        vj = alpha - beta;
+        tau = -1.0 / (beta * vj);
       }
+      s_tau = tau;
+      s_vj = vj;
+      to[j] = tau;
+      vt[j] = vj;
+      T[j + (size_t)j * p] = beta;
     }
     __syncthreads();
-    const double tau = s_tau;
+    const double tau = s_tau, vj = s_vj;
     if (tau != 0.0) {
-      for (int c = j + 1 + w; c < p; c += nw) {
-        double* bc = B + (size_t)c * p;
+      // partial dots of column c with v over this slice's bottom blocks
+      if (active && c > j) {
         double d = 0.0;
-        for (int i = lane; i <= j; i += 32) d = fma(bj[i], bc[i], d);
-        d = warp_sum(d) + T[j + (size_t)c * p];
-        const double f = tau * d;
-        if (lane == 0) T[j + (size_t)c * p] -= f;
-        for (int i = lane; i <= j; i += 32) bc[i] = fma(-f, bj[i], bc[i]);
+        for (int b = 1 + sl; b < ng; b += S) {
+          const double* Bb = T + (size_t)b * p * p;
+          for (int i = 0; i <= j; ++i) d = fma(Bb[i + (size_t)j * p], Bb[i + (size_t)c * p], d);
+        }
+        part[(size_t)sl * p + c] = d;
+      }
+      __syncthreads();
+      if (active && sl == 0 && c > j) {
+        double d = vj * T[j + (size_t)c * p];
+        for (int q = 0; q < S; ++q) d += part[(size_t)q * p + c];
+        part[c] = tau * d;  // f_c (slice 0 row of the partial table)
+      }
+      __syncthreads();
+      if (active && c > j) {
+        const double f = part[c];
+        if (sl == 0) T[j + (size_t)c * p] -= f * vj;
+        for (int b = 1 + sl; b < ng; b += S) {
+          double* Bb = T + (size_t)b * p * p;
+          for (int i = 0; i <= j; ++i) Bb[i + (size_t)c * p] = fma(-f, Bb[i + (size_t)j * p], Bb[i + (size_t)c * p]);
+        }
       }
     }
     __syncthreads();
+    // norm of column j+1 below its diagonal: bottoms' rows 0..j+1
+    if (j + 1 < p) {
+      if (active && c == j + 1) {
+        double sg = 0.0;
+        for (int b = 1 + sl; b < ng; b += S) {
+          const double* Bb = T + (size_t)b * p * p;
+          for (int i = 0; i <= j + 1; ++i) sg = fma(Bb[i + (size_t)c * p], Bb[i + (size_t)c * p], sg);
+        }
+        part[(size_t)sl * p + c] = sg;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double sg = 0.0;
+        for (int q = 0; q < S; ++q) sg += part[(size_t)q * p + j + 1];
+        s_sig = sg;
+      }
+      __syncthreads();
+    }
   }
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-    const int i = t % p, j = t / p;
-    Ro[t] = (i <= j) ? T[t] : 0.0;
-    Vo[t] = (i <= j) ? B[t] : 0.0;
+    const int i = t % p, jj = t / p;
+    Ro[t] = (i <= jj) ? T[t] : 0.0;
   }
+  for (int t = threadIdx.x; t < (ng - 1) * p * p; t += blockDim.x) {
+    const int i = t % p, jj = (t / p) % p;
+    Vo[(size_t)p * p + t] = (i <= jj) ? T[(size_t)p * p + t] : 0.0;
+  }
+}
+
+// fan-in of a merge node: as many triangles as fit in shared memory
+static int qr_merge_fanin(int p) {
+  const size_t per = (size_t)p * p * 8 + (size_t)16 * p * 8;
+  return std::max(2, int(QR_SMEM_MAX / per));
 }
 
 static int qr_leaf_rows(int p) {
@@ -401,23 +454,27 @@ void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t) {
               k_qr_blocks<<<t.nb0, QR_THREADS, smem, ex.s>>>(X, m, p, ldx, t.mb0, t.V0, t.tau0, R));
   }
   int n = t.nb0;
+  const int g = qr_merge_fanin(p);
   while (n > 1) {
-    const int nodes = (n + 1) / 2;
-    double* Vm = ex.ar->get<double>((size_t)nodes * p * p);
+    const int nodes = (n + g - 1) / g;
+    double* Vm = ex.ar->get<double>((size_t)nodes * g * p * p);
+    double* vt = ex.ar->get<double>((size_t)nodes * p);
     double* tm = ex.ar->get<double>((size_t)nodes * p);
     double* Rn = ex.ar->get<double>((size_t)nodes * p * p);
     t.nin.push_back(n);
     t.Vm.push_back(Vm);
+    t.vtop.push_back(vt);
     t.taum.push_back(tm);
     if (!ex.dry) {
       smem_attr_once(k_qr_merge);
-      const size_t smem = 2 * (size_t)p * p * 8;
-      TT_KERNEL(ex, K_QR, (n / 2) * (2.0 / 3.0) * p * (double)p * p, 8.0 * 3.0 * nodes * p * (double)p,
-                k_qr_merge<<<nodes, QR_THREADS, smem, ex.s>>>(R, n, p, Rn, Vm, tm));
+      const size_t smem = (size_t)std::min(g, n) * p * p * 8 + (size_t)16 * p * 8;
+      TT_KERNEL(ex, K_QR, (n - nodes) * (2.0 / 3.0) * p * (double)p * p, 8.0 * 3.0 * n * p * (double)p,
+                k_qr_merge<<<nodes, QR_THREADS, smem, ex.s>>>(R, n, p, g, Rn, Vm, vt, tm));
     }
     R = Rn;
     n = nodes;
   }
+  t.g = g;
   t.R = R;
 }
 
@@ -462,67 +519,85 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const double* __
   }
 }
 
-// Reverse of a merge node: [top; bottom] = Q_node [Z; 0]; top goes to input
-// 2*node, bottom to input 2*node+1 (each p x k, ld p).
+// Reverse of a merge node: [top; B_1; ...] = Q_node [Z; 0; ...]; the top goes
+// to input node*g, block b to input node*g + b (each p x k, ld p).
 __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(const double* __restrict__ Vm,
+                                                               const double* __restrict__ vtop,
                                                                const double* __restrict__ taum, int nin, int p,
-                                                               int k, const double* __restrict__ Zin, long zstride,
-                                                               long zld, double* __restrict__ Zout) {
+                                                               int g, int k, const double* __restrict__ Zin,
+                                                               long zstride, long zld, double* __restrict__ Zout) {
   extern __shared__ double sm[];
   const int node = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int first = node * g, ng = min(g, nin - first);
   const double* zb = Zin + (size_t)node * zstride;
-  double* top = Zout + (size_t)(2 * node) * p * k;
-  if (2 * node + 1 >= nin) {
-    for (int t = threadIdx.x; t < p * k; t += blockDim.x) top[t] = zb[(t % p) + (size_t)(t / p) * zld];
+  double* out = Zout + (size_t)first * p * k;
+  if (ng == 1) {
+    for (int t = threadIdx.x; t < p * k; t += blockDim.x) out[t] = zb[(t % p) + (size_t)(t / p) * zld];
     return;
   }
-  double* T = sm;                  // p x k
-  double* B = sm + (size_t)p * k;  // p x k
-  for (int t = threadIdx.x; t < p * k; t += blockDim.x) {
-    T[t] = zb[(t % p) + (size_t)(t / p) * zld];
-    B[t] = 0.0;
-  }
-  __syncthreads();
-  const double* V = Vm + (size_t)node * p * p;
+  double* Z = sm;                          // ng blocks of p x k
+  double* part = sm + (size_t)ng * p * k;  // [slice][column]
+  for (int t = threadIdx.x; t < p * k; t += blockDim.x) Z[t] = zb[(t % p) + (size_t)(t / p) * zld];
+  for (int t = threadIdx.x; t < (ng - 1) * p * k; t += blockDim.x) Z[(size_t)p * k + t] = 0.0;
+  const double* V = Vm + (size_t)node * g * p * p;
+  const double* vt = vtop + (size_t)node * p;
   const double* tv = taum + (size_t)node * p;
+  const int G = (k + 31) / 32;
+  const int S = max(1, nw / G);
+  const int grp = w % G, sl = w / G;
+  const int c = grp * 32 + lane;
+  const bool active = (sl < S) && (c < k);
+  __syncthreads();
   for (int j = p - 1; j >= 0; --j) {
     const double tj = tv[j];
-    if (tj != 0.0) {
-      const double* v = V + (size_t)j * p;
-      for (int c = w; c < k; c += nw) {
-        double* bc = B + (size_t)c * p;
-        double d = 0.0;
-        for (int i = lane; i <= j; i += 32) d = fma(v[i], bc[i], d);
-        d = warp_sum(d) + T[j + (size_t)c * p];
-        const double f = tj * d;
-        if (lane == 0) T[j + (size_t)c * p] -= f;
-        for (int i = lane; i <= j; i += 32) bc[i] = fma(-f, v[i], bc[i]);
+    if (tj == 0.0) continue;  // uniform across the block
+    const double vj = vt[j];
+    if (active) {
+      double d = 0.0;
+      for (int b = 1 + sl; b < ng; b += S) {
+        const double* Vb = V + (size_t)b * p * p + (size_t)j * p;
+        const double* Zb = Z + (size_t)b * p * k + (size_t)c * p;
+        for (int i = 0; i <= j; ++i) d = fma(Vb[i], Zb[i], d);
+      }
+      part[(size_t)sl * k + c] = d;
+    }
+    __syncthreads();
+    if (active && sl == 0) {
+      double d = vj * Z[j + (size_t)c * p];
+      for (int q = 0; q < S; ++q) d += part[(size_t)q * k + c];
+      part[c] = tj * d;
+    }
+    __syncthreads();
+    if (active) {
+      const double f = part[c];
+      if (sl == 0) Z[j + (size_t)c * p] -= f * vj;
+      for (int b = 1 + sl; b < ng; b += S) {
+        const double* Vb = V + (size_t)b * p * p + (size_t)j * p;
+        double* Zb = Z + (size_t)b * p * k + (size_t)c * p;
+        for (int i = 0; i <= j; ++i) Zb[i] = fma(-f, Vb[i], Zb[i]);
       }
     }
     __syncthreads();
   }
-  double* bot = top + (size_t)p * k;
-  for (int t = threadIdx.x; t < p * k; t += blockDim.x) {
-    top[t] = T[t];
-    bot[t] = B[t];
-  }
+  for (int t = threadIdx.x; t < ng * p * k; t += blockDim.x) out[t] = Z[t];
 }
 
 void tsqr_apply(Exec& ex, const QRTree& t, const double* C, int k, long ldc, double* Out, long ldo) {
-  TT_REQUIRE(k >= 1 && k <= 128, TT_ERR_ARG);
+  TT_REQUIRE(k >= 1 && k <= t.p, TT_ERR_ARG);
   Scope sc(*ex.ar);
   const int p = t.p;
   const double* zin = C;
   long zstride = 0, zld = ldc;
   for (int l = (int)t.nin.size() - 1; l >= 0; --l) {
-    const int nin = t.nin[l], nodes = (nin + 1) / 2;
+    const int nin = t.nin[l], nodes = (nin + t.g - 1) / t.g;
     double* zout = ex.ar->get<double>((size_t)nin * p * k);
     if (!ex.dry) {
       smem_attr_once(k_qr_apply_merge);
-      const size_t smem = 2 * (size_t)p * k * 8;
-      TT_KERNEL(ex, K_QR_APPLY, (nin / 2) * 2.0 * p * (double)p * k, 8.0 * ((double)nodes * p * p + 3.0 * nin * p * k),
-                k_qr_apply_merge<<<nodes, QR_THREADS, smem, ex.s>>>(t.Vm[l], t.taum[l], nin, p, k, zin, zstride,
-                                                                    zld, zout));
+      const size_t smem = (size_t)std::min(t.g, nin) * p * k * 8 + (size_t)16 * k * 8;
+      TT_KERNEL(ex, K_QR_APPLY, (nin - nodes) * 2.0 * p * (double)p * k,
+                8.0 * ((double)nin * p * p + 2.0 * nin * p * k),
+                k_qr_apply_merge<<<nodes, QR_THREADS, smem, ex.s>>>(t.Vm[l], t.vtop[l], t.taum[l], nin, p, t.g, k,
+                                                                    zin, zstride, zld, zout));
     }
     zin = zout;
     zstride = (long)p * k;
@@ -558,6 +633,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   double* A = sm;                  // p x p
   double* J = sm + (size_t)p * p;  // p x p scratch, then pd x pd Jacobi V
   __shared__ double cn[128];
+  __shared__ double cn0[128];  // norms at the last exact computation
   __shared__ int piv[128];
   __shared__ int order[128];
   __shared__ double s_tau, s_fro2, s_trail;
@@ -576,7 +652,10 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     double s = 0.0;
     for (int i = lane; i < p; i += 32) s = fma(A[i + (size_t)j * p], A[i + (size_t)j * p], s);
     s = warp_sum(s);
-    if (lane == 0) cn[j] = s;
+    if (lane == 0) {
+      cn[j] = s;
+      cn0[j] = s;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -634,6 +713,9 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
         const double c = cn[k];
         cn[k] = cn[jm];
         cn[jm] = c;
+        const double c0 = cn0[k];
+        cn0[k] = cn0[jm];
+        cn0[jm] = c0;
       }
     }
     __syncthreads();
@@ -666,10 +748,26 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
         for (int i = k + 1 + lane; i < p; i += 32) cc[i] = fma(-f, col[i], cc[i]);
       }
       __syncwarp();
-      double s2 = 0.0;  // exact trailing norm of the column below row k
-      for (int i = k + 1 + lane; i < p; i += 32) s2 = fma(cc[i], cc[i], s2);
-      s2 = warp_sum(s2);
-      if (lane == 0) cn[c] = s2;
+      // trailing norm below row k: downdate by the new row-k entry (one lane),
+      // recompute exactly only after heavy cancellation (as pivoted Householder
+      // QR codes do)
+      double s2 = 0.0;
+      int redo = 0;
+      if (lane == 0) {
+        s2 = fma(-cc[k], cc[k], cn[c]);
+        redo = (s2 <= 1e-6 * cn0[c]) ? 1 : 0;
+      }
+      redo = __shfl_sync(0xffffffffu, redo, 0);
+      if (redo) {
+        double e = 0.0;
+        for (int i = k + 1 + lane; i < p; i += 32) e = fma(cc[i], cc[i], e);
+        e = warp_sum(e);
+        if (lane == 0) {
+          s2 = e;
+          cn0[c] = e;
+        }
+      }
+      if (lane == 0) cn[c] = s2 > 0.0 ? s2 : 0.0;
     }
     __syncthreads();
   }
@@ -693,6 +791,14 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   const double eps = DBL_EPSILON * p, eps2 = eps * eps;
   int sweep = 0;
   for (; sweep < SVD_MAX_SWEEPS && pd > 1; ++sweep) {
+    // exact squared column norms at the start of the sweep; inside the sweep
+    // each rotation updates them as alpha - t gamma, beta + t gamma
+    for (int j = w; j < pd; j += nw) {
+      double sq = 0.0;
+      for (int r = lane; r < p; r += 32) sq = fma(A[r + (size_t)j * p], A[r + (size_t)j * p], sq);
+      sq = warp_sum(sq);
+      if (lane == 0) cn[j] = sq;
+    }
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int step = 0; step < q - 1; ++step) {
@@ -702,24 +808,20 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
         if (i >= pd || j >= pd) continue;
         double* ci = A + (size_t)i * p;
         double* cj = A + (size_t)j * p;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int r = lane; r < p; r += 32) {
-          const double x = ci[r], y = cj[r];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
+        double ga = 0.0;
+        for (int r = lane; r < p; r += 32) ga = fma(ci[r], cj[r], ga);
         ga = warp_sum(ga);
+        const double al = cn[i], be = cn[j];
         // |ga| <= eps sqrt(al be), compared in squares (no FP64 roots per lane)
         if (al <= thr || be <= thr || ga * ga <= eps2 * al * be) continue;
         double c = 1.0, sn = 0.0;
-        if (lane == 0) {  // rotation angle in one lane, then broadcast
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          c = 1.0 / sqrt(fma(t, t, 1.0));
+        if (lane == 0) {  // rotation in one lane, then broadcast
+          const double dd = be - al;
+          const double t = (dd >= 0.0 ? 2.0 * ga : -2.0 * ga) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * ga * ga)));
+          c = rsqrt(fma(t, t, 1.0));
           sn = c * t;
+          cn[i] = fma(-t, ga, al);
+          cn[j] = fma(t, ga, be);
         }
         c = __shfl_sync(0xffffffffu, c, 0);
         sn = __shfl_sync(0xffffffffu, sn, 0);

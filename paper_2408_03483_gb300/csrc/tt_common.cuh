@@ -177,14 +177,16 @@ void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, cons
 void sumsq(Exec& ex, const double* X, int m, int n, long ld, double* out);
 
 // Householder TSQR of a tall m x p matrix (p <= 112): row blocks of mb0
-// rows factored independently, then a binary tree of merges of stacked
-// triangular factors; Q is kept implicit.
+// rows factored independently, then a g-ary tree of merges of stacked
+// triangular factors (g as many as fit in shared memory); Q is kept implicit.
 struct QRTree {
   int m = 0, p = 0, mb0 = 0, nb0 = 0;
   double* V0 = nullptr;        // leaf reflectors: nb0 blocks of mb0 x p (unit diagonal implicit)
   double* tau0 = nullptr;      // nb0 x p
+  int g = 2;                   // fan-in of a merge node
   std::vector<int> nin;        // inputs of each merge level (bottom-up)
-  std::vector<double*> Vm;     // per merge level: nodes x (p x p) bottom-block reflectors
+  std::vector<double*> Vm;     // per merge level: nodes x g x (p x p) bottom-block reflectors
+  std::vector<double*> vtop;   // per merge level: nodes x p top entries (alpha - beta)
   std::vector<double*> taum;   // per merge level: nodes x p
   double* R = nullptr;         // final p x p upper triangle (ld p)
 };
