@@ -27,8 +27,14 @@ network: H1 = relu(X W1 + b1) (F -> 256), H2 = relu(H1 W2 + b2) (256 -> 256),
 s = H2 w3 + b3 (256 -> 1), one score per index.
 loss: mean over rows of the logistic loss softplus(s) - y s, y = 1 for an
 index in the converged pivot set of a plain cross, else 0.
-optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights;
-the forward pass reads the weights rounded to BF16 (round to nearest even).
+optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights.
+precision: every matrix product of the forward and backward passes reads its
+two operands rounded to BF16 (round to nearest, ties to even) and
+accumulates exactly here (in FP32 on the tensor cores); biases, activations,
+masks, the loss and the optimiser stay in higher precision.  The backward
+pass treats the roundings as the identity (the products' own operands are
+differentiated), so it is the exact gradient of the unrounded network when
+bf16=False.
 """
 import numpy as np
 
@@ -87,18 +93,25 @@ def init_params(seed):
                 w3=u(HIDDEN, (HIDDEN,)), b3=np.zeros(1, np.float32))
 
 
-def forward(P, X, round_weights=True):
-    """Scores and the cached activations; weights rounded to BF16 when
-    round_weights (the network's storage format), biases kept as given."""
-    W1 = bf16(P["W1"]) if round_weights else np.asarray(P["W1"], np.float64)
-    W2 = bf16(P["W2"]) if round_weights else np.asarray(P["W2"], np.float64)
-    w3 = bf16(P["w3"]) if round_weights else np.asarray(P["w3"], np.float64)
-    Z1 = X @ W1 + P["b1"]
+def mm(A, B, bf16_ops=True):
+    """A @ B with both operands rounded to BF16 first (when bf16_ops)."""
+    if bf16_ops:
+        return bf16(A) @ bf16(B)
+    return np.asarray(A, np.float64) @ np.asarray(B, np.float64)
+
+
+def forward(P, X, bf16_ops=True):
+    """Scores (m,) and the cached activations of rows X (m x F)."""
+    W1 = np.asarray(P["W1"], np.float64)
+    W2 = np.asarray(P["W2"], np.float64)
+    w3 = np.asarray(P["w3"], np.float64)
+    Z1 = mm(X, W1, bf16_ops) + np.asarray(P["b1"], np.float64)
     H1 = np.maximum(Z1, 0.0)
-    Z2 = H1 @ W2 + P["b2"]
+    Z2 = mm(H1, W2, bf16_ops) + np.asarray(P["b2"], np.float64)
     H2 = np.maximum(Z2, 0.0)
-    s = H2 @ w3 + float(P["b3"][0])
-    return s, dict(X=X, Z1=Z1, H1=H1, Z2=Z2, H2=H2, W1=W1, W2=W2, w3=w3)
+    s = mm(H2, w3[:, None], bf16_ops)[:, 0] + float(P["b3"][0])
+    return s, dict(X=np.asarray(X, np.float64), Z1=Z1, H1=H1, Z2=Z2, H2=H2, W1=W1, W2=W2, w3=w3,
+                   bf16_ops=bf16_ops)
 
 
 def loss(s, y):
@@ -107,20 +120,20 @@ def loss(s, y):
 
 
 def backward(s, y, cache):
-    """Gradients of the mean logistic loss w.r.t. W1, b1, W2, b2, w3, b3
-    (through the BF16-rounded weights, treated as the weights themselves)."""
+    """Gradients of the mean logistic loss w.r.t. W1, b1, W2, b2, w3, b3."""
+    o = cache["bf16_ops"]
     m = s.shape[0]
     ds = (1.0 / (1.0 + np.exp(-s)) - y) / m
     g = {}
-    g["w3"] = cache["H2"].T @ ds
+    g["w3"] = mm(cache["H2"].T, ds[:, None], o)[:, 0]
     g["b3"] = np.array([ds.sum()])
-    dH2 = np.outer(ds, cache["w3"])
+    dH2 = mm(ds[:, None], cache["w3"][None, :], o)
     dZ2 = dH2 * (cache["Z2"] > 0)
-    g["W2"] = cache["H1"].T @ dZ2
+    g["W2"] = mm(cache["H1"].T, dZ2, o)
     g["b2"] = dZ2.sum(axis=0)
-    dH1 = dZ2 @ cache["W2"].T
+    dH1 = mm(dZ2, cache["W2"].T, o)
     dZ1 = dH1 * (cache["Z1"] > 0)
-    g["W1"] = cache["X"].T @ dZ1
+    g["W1"] = mm(cache["X"].T, dZ1, o)
     g["b1"] = dZ1.sum(axis=0)
     return g
 

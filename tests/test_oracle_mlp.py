@@ -22,18 +22,14 @@ def test_loss_closed_forms():
     assert M.loss(np.array([-3.0]), np.array([1.0])) == pytest.approx(np.log1p(np.exp(3.0)), rel=1e-14)
 
 
-@pytest.mark.parametrize("round_weights", [False, True])
-def test_backward_matches_central_differences(round_weights):
+def test_backward_matches_central_differences():
+    # the unrounded network is smooth: its analytic gradient must match
+    # central differences of the loss
     rng = np.random.default_rng(3)
     X = rng.standard_normal((40, M.F_IN))
     y = (rng.random(40) < 0.3).astype(np.float64)
-    P = small_params(2)
-    # differentiate the network at exactly the weights the forward pass uses
-    Pd = {k: np.asarray(v, np.float64) for k, v in P.items()}
-    if round_weights:
-        for k in ("W1", "W2", "w3"):
-            Pd[k] = M.bf16(P[k])
-    s, cache = M.forward(Pd, X, round_weights=False)
+    Pd = {k: np.asarray(v, np.float64) for k, v in small_params(2).items()}
+    s, cache = M.forward(Pd, X, bf16_ops=False)
     g = M.backward(s, y, cache)
     h = 1e-6
     for k in Pd:
@@ -41,23 +37,40 @@ def test_backward_matches_central_differences(round_weights):
         for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
             old = flat[idx]
             flat[idx] = old + h
-            lp = M.loss(M.forward(Pd, X, round_weights=False)[0], y)
+            lp = M.loss(M.forward(Pd, X, bf16_ops=False)[0], y)
             flat[idx] = old - h
-            lm = M.loss(M.forward(Pd, X, round_weights=False)[0], y)
+            lm = M.loss(M.forward(Pd, X, bf16_ops=False)[0], y)
             flat[idx] = old
             fd = (lp - lm) / (2 * h)
             an = g[k].reshape(-1)[idx]
             assert abs(fd - an) <= 1e-6 * max(1e-3, abs(fd)), (k, idx, fd, an)
 
 
-def test_forward_uses_bf16_weights():
+def test_bf16_products_round_both_operands():
     rng = np.random.default_rng(4)
     X = rng.standard_normal((8, M.F_IN))
     P = small_params(5)
-    s_r, _ = M.forward(P, X, round_weights=True)
-    Pr = dict(P, W1=M.bf16(P["W1"]), W2=M.bf16(P["W2"]), w3=M.bf16(P["w3"]))
-    s_e, _ = M.forward(Pr, X, round_weights=False)
-    assert np.array_equal(s_r, s_e)
+    s_r, c_r = M.forward(P, X, bf16_ops=True)
+    # by hand: layer by layer with explicitly rounded operands
+    Z1 = M.bf16(X) @ M.bf16(P["W1"]) + P["b1"]
+    Z2 = M.bf16(np.maximum(Z1, 0)) @ M.bf16(P["W2"]) + P["b2"]
+    s = M.bf16(np.maximum(Z2, 0)) @ M.bf16(P["w3"]) + P["b3"][0]
+    assert np.allclose(s_r, s, rtol=1e-13, atol=1e-13)
+    # rounding moves the scores by no more than BF16 resolution of the operands
+    s_e, _ = M.forward(P, X, bf16_ops=False)
+    assert np.max(np.abs(s_r - s_e)) <= 2 * 2.0 ** -8 * np.max(np.abs(s_e)) + 1e-3
+
+
+def test_forward_closed_form():
+    # one active path: x0 = 2 -> 1.5 x0 = 3 -> 0.5 * 3 = 1.5 -> 2 * 1.5 + 0.25
+    # (every value exact in BF16); a negative input is cut by the first ReLU
+    P = {k: np.zeros_like(v) for k, v in M.init_params(0).items()}
+    P["W1"][0, 0], P["W2"][0, 0], P["w3"][0], P["b3"][0] = 1.5, 0.5, 2.0, 0.25
+    X = np.zeros((2, M.F_IN))
+    X[0, 0], X[1, 0] = 2.0, -2.0
+    for ops in (True, False):
+        s, _ = M.forward(P, X, bf16_ops=ops)
+        assert list(s) == [3.25, 0.25]
 
 
 def test_bf16_rounding_closed_forms():
