@@ -26,6 +26,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "equiv. cell-updates/s per RK step at fixed L2 err vs FP64 oracle; % roofline"
 UNIT = "cell-updates/s"
+# arithmetic of the rounding contractions per precision form (SVDs and cores stay FP64)
+DTYPES = {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16": "bf16x6"}
 WORKLOAD = "nonlinear256_weno5"
 # GB300 FP64: 2 FMA / clk / SM (4 flop), 152 SMs, 2070 MHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
@@ -38,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"],
+                    help="working precision of the rounding contractions (fp64: the plain path)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     return ap.parse_args()
@@ -142,7 +146,8 @@ def cpu_baseline(w, p, Q, nsteps):
     n = w["n"]
     cores = os.cpu_count()
     return {"value": n * n * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {nsteps} SSP-RK3 step(s) of the {w['n']}x{w['n']} WENO5 workload from its initial "
+            "sample": f"first {nsteps} SSP-RK3 step(s) of the {w['n']}x{w['n']} {w['scheme']} workload from its "
+                      f"initial "
                       f"state (ranks small, cheaper than later steps); numpy/OpenBLAS float64 on {cores} threads",
             "seconds": dt}, Qo
 
@@ -199,7 +204,7 @@ def run_ours(args):
     def new_solver(state):
         q0 = [api.DevTT.from_cores(A, B, cap=cap) for A, B in state]
         return api.Solver(q0, w["eqn"], w["scheme"], n, p["dt"], w["tol"], cap, g=p["g"], H=p["H"], f=p["f"],
-                          kick=4, max_sweeps=10, max_iter=50, seed=0)
+                          kick=4, max_sweeps=10, max_iter=50, seed=0, precision=args.precision)
 
     # ---- parity sample: first step from the initial state vs the oracle
     s0 = new_solver(Q)
@@ -220,6 +225,8 @@ def run_ours(args):
     clocks.start()
     launches0 = api.launch_count()
     step_ms = []
+    # profiler range = the timed steps (ncu --profile-from-start off records these only)
+    torch.cuda.profiler.start()
     wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1)
@@ -232,6 +239,7 @@ def run_ours(args):
         step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    torch.cuda.profiler.stop()
     launches = api.launch_count() - launches0
     clk = clocks.stop()
     # ---- per-kernel profile: further steps with every launch event-timed and
@@ -311,8 +319,9 @@ def run_ours(args):
                for k, v in prof.items() if v["launches"]}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "scheme": w["scheme"], "eqn": w["eqn"],
+                       "precision": args.precision,
                        "rank_cap": cap, "tol": w["tol"], "steps_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
                        "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
             "clocks": clk, "gpu_launches": launches, "roofline": roofline, "kernel_classes": classes,
@@ -333,10 +342,88 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- batched form
+def run_ensemble(args):
+    """The batched form: `ensembleK` = K seeded instances of uneven grid size,
+    rank cap and reconstruction advanced together (tt_fv_batch_*).  The
+    warm-up steps run the autotuner; one step = one SSP-RK3 step of every
+    instance; value = sum of n^2 over instances x steps / device time."""
+    import torch
+    from synth import ensemble, initial_tt
+    from paper_2408_03483_gb300 import api, capi
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    capi.load()
+    count = int(args.workload[len("ensemble"):] or 256)
+    ws = ensemble(count=count)
+    insts = []
+    for w in ws:
+        Q, p = initial_tt(w)
+        q0 = [api.DevTT.from_cores(A, B, cap=w["cap"]) for A, B in Q]
+        insts.append((q0, dict(eqn=w["eqn"], scheme=w["scheme"], n=w["n"], dt=p["dt"], tol=w["tol"],
+                               rank_cap=w["cap"], g=p["g"], H=p["H"], f=p["f"], seed=0)))
+    cells = sum(w["n"] ** 2 for w in ws)
+    prec = args.precision if args.precision != "fp64" else "fp64"
+    b = api.Batch(insts, precision=prec, workers=8)
+    stream = torch.cuda.current_stream()
+    # warm-up = the autotuner's trials: one step per (workers, inner tasks)
+    # candidate; workers = 1 with inner tasks is the plain one-instance path
+    cands = (1, 8, 16)
+    (bw, bi), rates = b.tune(workers=cands, steps_per_trial=1, with_rates=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = api.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = api.launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    dev = max(b.stats(i)["device_status"] for i in range(count))
+    b.close()
+    if rank != 0:
+        return
+    value = cells * args.steps * world / (total_ms / 1e3)
+    plain = rates.get((1, True))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": 2 * len(cands), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
+            "config": {"workload": args.workload, "instances": count, "cells": cells, "precision": prec,
+                       "schemes": {s: sum(w["scheme"] == s for w in ws) for s in ("up3", "up5", "weno5")},
+                       "sizes": sorted({w["n"] for w in ws}), "caps": [min(w["cap"] for w in ws),
+                                                                       max(w["cap"] for w in ws)],
+                       "l2": "inputs of each step are the previous step's outputs (no flush)",
+                       "parallelism": "replicas"},
+            "tuned": {"workers": bw, "inner_tasks": bi,
+                      "trial_rates": {f"w{w}_{'inner' if i else 'flat'}": r for (w, i), r in rates.items()}},
+            "vs_one_instance_at_a_time": (value / world / plain) if plain else None,
+            "clocks": clk, "gpu_launches": launches, "device_status": dev}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("ensemble"):
+        run_ensemble(args)
     else:
         run_ours(args)
 

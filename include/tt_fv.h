@@ -24,6 +24,9 @@
  *   argument (no work done); TT_ERR_OOM: workspace too small; TT_ERR_CUDA: a
  *   CUDA call failed; TT_ERR_NOCONV: an iteration hit its cap (Taylor
  *   reciprocal, Jacobi SVD); the output is then the last iterate.
+ *   TT_ERR_NONFINITE: a NaN or Inf reached a small SVD or maxvol (the
+ *   kernels then produce a harmless placeholder instead of indexing with
+ *   it); TT_ERR_TIMEOUT: a tensor-core kernel's bounded wait expired.
  *   Reaching a rank cap truncates to the cap and is counted, not an error.
  * - All arithmetic is IEEE FP64.
  */
@@ -44,7 +47,8 @@ typedef enum {
   TT_ERR_CUDA = 3,
   TT_ERR_NOCONV = 4,
   TT_ERR_TIMEOUT = 5,
-  TT_ERR_RANKCAP = 6
+  TT_ERR_RANKCAP = 6,
+  TT_ERR_NONFINITE = 7
 } tt_status;
 
 typedef struct {
@@ -57,7 +61,7 @@ typedef struct {
 
 enum { TT_LINEAR = 0, TT_NONLINEAR = 1 };          /* Eq. linear-SWE / nonlinear-SWE */
 enum { TT_UP3 = 0, TT_UP5 = 1, TT_WENO5 = 2 };      /* Sec. 2.3 reconstructions */
-enum { TT_FP64 = 0, TT_TF32 = 1, TT_BF16 = 2 };     /* contraction precision */
+enum { TT_FP64 = 0, TT_TF32 = 1, TT_BF16 = 2, TT_FP32 = 3 }; /* contraction precision */
 enum { TT_PIVOT_MAXVOL = 0, TT_PIVOT_LEARNED = 1 };
 
 /* Cross-interpolated functions (tt_cross `fn`). */
@@ -77,8 +81,9 @@ typedef struct {
   double dt;          /* time step */
   double tol;         /* relative Frobenius truncation tolerance of every round */
   int32_t rank_cap;   /* rank cap of every round */
-  int32_t precision;  /* TT_FP64 (only value accepted by this build) */
-  int32_t pivots;     /* TT_PIVOT_MAXVOL (only value accepted by this build) */
+  int32_t precision;  /* TT_FP64, or TT_FP32: the precision form (FP32 rounding contractions, FP64 SVDs) */
+  int32_t pivots;     /* TT_PIVOT_MAXVOL, or TT_PIVOT_LEARNED: crosses start from the pivots of the
+                         network set by tt_fv_set_pivot_net (maxvol start until one is set) */
   int32_t kick;       /* cross kick fibres per sweep (default 4 if <= 0) */
   int32_t max_sweeps; /* cross sweep cap (default 10 if <= 0) */
   int32_t max_iter;   /* Taylor reciprocal iteration cap (default 50 if <= 0) */
@@ -104,6 +109,8 @@ typedef struct {
   double section_ms[6];       /* host wall time per stage section: faces, side fluxes + lambda,
                                  LLF combination, quadrature/difference, forward-Euler rounds,
                                  SSP combination rounds */
+  int64_t learned_calls;      /* crosses started from the learned network's pivots */
+  int64_t learned_accepted;   /* ... whose first interpolation check passed (no maxvol fallback) */
 } tt_fv_stats;
 
 typedef struct tt_fv_ctx tt_fv_ctx;
@@ -181,6 +188,111 @@ uint64_t tt_launch_count(void);
 size_t tt_round_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap);
 tt_status tt_round(const tt2* x, double tol, int32_t rank_cap, tt2* y, double* err_out,
                    void* ws, size_t ws_bytes, void* stream);
+
+/* Learned-pivot form.  The paper's crosses (Sec. 3.3) refine pivots by maxvol
+ * sweeps from some start; this form starts them from the column indices that
+ * a 3-layer perceptron (12 -> 256 -> 256 -> 1, ReLU) scores highest from
+ * features of the cross's initial TT.  The sweeps still judge the sampled
+ * interpolation error against the tolerance, so plain maxvol refinement is
+ * the fallback whenever the proposal is not good enough.
+ *   tt_mlp: caller-owned device FP32 parameters: W1 12x256 and W2 256x256
+ *   row-major (W[in*256 + out]), b1, b2, w3 (256 each), b3 (1).  Every
+ *   product of the forward and backward passes runs on tcgen05 tensor cores
+ *   with both operands rounded to BF16 and FP32 accumulation.
+ *   tt_mlp_features: X (n2 x 12 column-major, ld n2, device float) = the index
+ *   features of x0's column mode (leverage of an orthonormal basis of x0->b
+ *   and of its 4 neighbours, standardised column mean and its first/second
+ *   differences, log curvature, column energy, sin/cos of the index angle).
+ *   tt_mlp_forward: scores s (m) of the rows of X (m x 12, ld m).
+ *   tt_mlp_grad: gradients of the mean logistic loss over labels y (m, 0/1)
+ *   into *grad (same shapes as net) and the loss into *loss (device double,
+ *   may be NULL).  tt_mlp_adam: one Adam step (0.9, 0.999, 1e-8) of net with
+ *   moment buffers m1, m2 (zero-initialised by the caller), step t >= 1.
+ *   tt_mlp_topk: the k (<= 128) highest scores' indices, ties to the smaller
+ *   index, written ascending to idx (device).
+ *   Workspace: tt_mlp_workspace_size(rows, rank) covers features of an
+ *   n2 = rows TT of that rank and forward/grad/topk over `rows` rows.
+ * Solver hooks: tt_fv_set_pivot_net points a TT_PIVOT_LEARNED solver at a
+ * network (NULL: back to the maxvol start); tt_fv_record_pivots(ctx, 1)
+ * starts capturing, for every cross, the features of its initial TT with
+ * label 1 on the converged column pivots (training data; adds a sync per
+ * cross), tt_fv_pivot_rows reports the captured rows and tt_fv_pivot_take
+ * copies them to host arrays X (rows x 12 row-major) and y (rows), then
+ * clears the capture. */
+typedef struct {
+  float* W1;
+  float* b1;
+  float* W2;
+  float* b2;
+  float* w3;
+  float* b3;
+} tt_mlp;
+size_t tt_mlp_workspace_size(int32_t rows, int32_t rank);
+tt_status tt_mlp_features(const tt2* x0, float* X, void* ws, size_t ws_bytes, void* stream);
+tt_status tt_mlp_forward(const tt_mlp* net, const float* X, int32_t m, float* s, void* ws, size_t ws_bytes,
+                         void* stream);
+tt_status tt_mlp_grad(const tt_mlp* net, const float* X, const float* y, int32_t m, const tt_mlp* grad,
+                      double* loss, void* ws, size_t ws_bytes, void* stream);
+tt_status tt_mlp_adam(const tt_mlp* net, const tt_mlp* grad, const tt_mlp* m1, const tt_mlp* m2, int32_t t,
+                      float lr, void* stream);
+tt_status tt_mlp_topk(const float* s, int32_t m, int32_t k, int32_t* idx, void* ws, size_t ws_bytes, void* stream);
+tt_status tt_fv_set_pivot_net(tt_fv_ctx* ctx, const tt_mlp* net);
+tt_status tt_fv_record_pivots(tt_fv_ctx* ctx, int32_t enable);
+int64_t tt_fv_pivot_rows(tt_fv_ctx* ctx);
+tt_status tt_fv_pivot_take(tt_fv_ctx* ctx, float* X, float* y, int64_t rows);
+
+/* Batched form: an ensemble of independent solver instances (uneven grid
+ * size, rank cap, reconstruction and precision) advanced together on one GPU.
+ *   p[count], q0[3*count]: per-instance parameters and initial fields, as for
+ *   tt_fv_init (copied at init).  ws: one caller workspace of at least
+ *   tt_fv_batch_workspace_size(p, count) bytes, sliced per instance.  Each
+ *   instance runs on its own stream, created by the batch; `stream` is the
+ *   caller's stream, ordered after all instance work at the end of every
+ *   tt_fv_batch_step.
+ * tt_fv_batch_step advances every instance by nsteps full SSP-RK3 steps: host
+ *   workers take instances longest-first (cost = the instance's previous step
+ *   time) so that several instances' kernels share the GPU.
+ * tt_fv_batch_configure sets the worker count and whether each instance also
+ *   runs its own independent stage tasks concurrently (inner_tasks != 0).
+ * tt_fv_batch_tune runs steps_per_trial real batch steps for each candidate
+ *   worker count, with inner tasks off and on, keeps the fastest setting and
+ *   reports it (the trial steps advance the ensemble); rates (may be NULL,
+ *   2*ncand doubles) receives each trial's cell updates per second, index
+ *   2*c + inner.
+ * tt_fv_batch_get / tt_fv_batch_stats_get: as tt_fv_get / tt_fv_stats_get for
+ *   instance i.  Errors: TT_ERR_ARG, TT_ERR_OOM (workspace too small), or the
+ *   first error an instance returned. */
+typedef struct tt_fv_batch tt_fv_batch;
+size_t tt_fv_batch_workspace_size(const tt_fv_params* p, int32_t count);
+tt_status tt_fv_batch_init(const tt_fv_params* p, int32_t count, const tt2* q0, void* ws, size_t ws_bytes,
+                           void* stream, tt_fv_batch** out);
+tt_status tt_fv_batch_configure(tt_fv_batch* b, int32_t workers, int32_t inner_tasks);
+tt_status tt_fv_batch_step(tt_fv_batch* b, int32_t nsteps);
+tt_status tt_fv_batch_tune(tt_fv_batch* b, const int32_t* workers, int32_t ncand, int32_t steps_per_trial,
+                           int32_t* best_workers, int32_t* best_inner, double* rates);
+tt_status tt_fv_batch_get(tt_fv_batch* b, int32_t i, tt2 q_out[3]);
+tt_status tt_fv_batch_stats_get(tt_fv_batch* b, int32_t i, tt_fv_stats* out);
+void tt_fv_batch_destroy(tt_fv_batch* b);
+
+/* Dense contraction C = alpha A B + beta C in the working precision of a
+ * precision form -- the core-times-factor and face-tensor products of TT
+ * rounding (Sec. 3.2) that the precision forms move off FP64.
+ *   A: m x k, B: k x n, C: m x n, FP64, column-major device arrays with
+ *   leading dimensions lda >= m, ldb >= k, ldc >= m (caller-owned; C is
+ *   overwritten, and read when beta != 0).
+ *   precision: TT_FP64 (FP64 CUDA cores), TT_FP32 (operands rounded to FP32,
+ *   FP32 CUDA-core products), TT_TF32 / TT_BF16 (tcgen05 tensor cores, FP32
+ *   accumulation).  split (TF32/BF16 only): nonzero decomposes each operand
+ *   into tensor-core parts (TF32: hi + lo, 3 products; BF16: hi + mid + lo,
+ *   6 products) whose sum reaches FP32 accuracy; 0 rounds each operand once.
+ *   The result is rounded to FP32 before alpha/beta are applied in FP64.
+ * Errors: TT_ERR_ARG for bad shapes/pointers/precision; TT_ERR_OOM if ws is
+ * smaller than tt_contract_workspace_size(); TT_ERR_TIMEOUT if a tensor-core
+ * kernel's bounded wait expired. */
+size_t tt_contract_workspace_size(int32_t precision, int32_t split, int32_t m, int32_t n, int32_t k);
+tt_status tt_contract(int32_t precision, int32_t split, int32_t m, int32_t n, int32_t k, double alpha,
+                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                      int64_t ldc, void* ws, size_t ws_bytes, void* stream);
 
 /* tt_round without any device allocation, for callers that cannot allocate
  * device memory (no cudaMalloc available to them, or a fixed memory footprint

@@ -10,18 +10,21 @@ import os
 
 from . import build as _build
 
-TT_OK, TT_ERR_ARG, TT_ERR_OOM, TT_ERR_CUDA, TT_ERR_NOCONV, TT_ERR_TIMEOUT, TT_ERR_RANKCAP = range(7)
+TT_OK, TT_ERR_ARG, TT_ERR_OOM, TT_ERR_CUDA, TT_ERR_NOCONV, TT_ERR_TIMEOUT, TT_ERR_RANKCAP, TT_ERR_NONFINITE = range(8)
 TT_LINEAR, TT_NONLINEAR = 0, 1
 TT_UP3, TT_UP5, TT_WENO5 = 0, 1, 2
-TT_FP64, TT_TF32, TT_BF16 = 0, 1, 2
+TT_FP64, TT_TF32, TT_BF16, TT_FP32 = 0, 1, 2, 3
 TT_PIVOT_MAXVOL, TT_PIVOT_LEARNED = 0, 1
 TT_FN_ENTRY, TT_FN_WENO_S1, TT_FN_WENO_S2, TT_FN_LLF_LAMBDA = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "TT_OK", 1: "TT_ERR_ARG", 2: "TT_ERR_OOM", 3: "TT_ERR_CUDA", 4: "TT_ERR_NOCONV",
-                5: "TT_ERR_TIMEOUT", 6: "TT_ERR_RANKCAP"}
+                5: "TT_ERR_TIMEOUT", 6: "TT_ERR_RANKCAP",
+                7: "TT_ERR_NONFINITE"}
 
 SCHEMES = {"up3": TT_UP3, "up5": TT_UP5, "weno5": TT_WENO5}
 EQNS = {"linear": TT_LINEAR, "nonlinear": TT_NONLINEAR}
+PRECISIONS = {"fp64": TT_FP64, "fp32": TT_FP32, "tf32": TT_TF32, "bf16": TT_BF16}
+PIVOTS = {"maxvol": 0, "learned": 1}
 
 
 class TTError(RuntimeError):
@@ -52,11 +55,16 @@ class tt_fv_stats(ctypes.Structure):
                 ("qb_uncertified", ctypes.c_int64), ("flops", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("device_status", ctypes.c_uint32),
                 ("svd_calls", ctypes.c_int64), ("svd_p_sum", ctypes.c_int64), ("svd_pd_sum", ctypes.c_int64),
-                ("svd_sweeps_sum", ctypes.c_int64), ("section_ms", ctypes.c_double * 6)]
+                ("svd_sweeps_sum", ctypes.c_int64), ("section_ms", ctypes.c_double * 6),
+                ("learned_calls", ctypes.c_int64), ("learned_accepted", ctypes.c_int64)]
 
 
 TT_K_NAMES = ["gemm", "form_hadamard", "qr", "qr_apply", "jacobi_svd", "maxvol", "cross_eval", "stencil",
               "other"]
+
+
+class tt_mlp(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]
 
 
 class tt_kernel_prof(ctypes.Structure):
@@ -86,6 +94,27 @@ SIGNATURES = {
     "tt_launch_count": (ctypes.c_uint64, []),
     "tt_round_workspace_size": (_sz, [_i32, _i32, _i32, _i32]),
     "tt_round": (ctypes.c_int, [_P(tt2), _d, _i32, _P(tt2), _P(_d), _vp, _sz, _vp]),
+    "tt_mlp_workspace_size": (_sz, [_i32, _i32]),
+    "tt_mlp_features": (ctypes.c_int, [_P(tt2), _vp, _vp, _sz, _vp]),
+    "tt_mlp_forward": (ctypes.c_int, [_P(tt_mlp), _vp, _i32, _vp, _vp, _sz, _vp]),
+    "tt_mlp_grad": (ctypes.c_int, [_P(tt_mlp), _vp, _vp, _i32, _P(tt_mlp), _vp, _vp, _sz, _vp]),
+    "tt_mlp_adam": (ctypes.c_int, [_P(tt_mlp), _P(tt_mlp), _P(tt_mlp), _P(tt_mlp), _i32, ctypes.c_float, _vp]),
+    "tt_mlp_topk": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _sz, _vp]),
+    "tt_fv_set_pivot_net": (ctypes.c_int, [_vp, _P(tt_mlp)]),
+    "tt_fv_record_pivots": (ctypes.c_int, [_vp, _i32]),
+    "tt_fv_pivot_rows": (ctypes.c_int64, [_vp]),
+    "tt_fv_pivot_take": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64]),
+    "tt_fv_batch_workspace_size": (_sz, [_P(tt_fv_params), _i32]),
+    "tt_fv_batch_init": (ctypes.c_int, [_P(tt_fv_params), _i32, _P(tt2), _vp, _sz, _vp, _P(_vp)]),
+    "tt_fv_batch_configure": (ctypes.c_int, [_vp, _i32, _i32]),
+    "tt_fv_batch_step": (ctypes.c_int, [_vp, _i32]),
+    "tt_fv_batch_tune": (ctypes.c_int, [_vp, _P(_i32), _i32, _i32, _P(_i32), _P(_i32), _P(_d)]),
+    "tt_fv_batch_get": (ctypes.c_int, [_vp, _i32, _P(tt2)]),
+    "tt_fv_batch_stats_get": (ctypes.c_int, [_vp, _i32, _P(tt_fv_stats)]),
+    "tt_fv_batch_destroy": (None, [_vp]),
+    "tt_contract_workspace_size": (_sz, [_i32, _i32, _i32, _i32, _i32]),
+    "tt_contract": (ctypes.c_int, [_i32, _i32, _i32, _i32, _i32, _d, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _d,
+                                   _vp, ctypes.c_int64, _vp, _sz, _vp]),
     "tt_round_noalloc": (ctypes.c_int, [_P(tt2), _d, _i32, _P(tt2), _P(_d), _vp]),
     "tt_round_hadamard_workspace_size": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "tt_round_hadamard": (ctypes.c_int, [_P(tt2), _P(tt2), _d, _i32, _P(tt2), _vp, _sz, _vp]),

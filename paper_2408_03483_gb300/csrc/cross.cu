@@ -344,6 +344,8 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
           unsigned seed, TT& y) {
   TT_REQUIRE(cap >= 1 && cap + kick <= 112 && x0.r >= 1 && x0.r <= 112, TT_ERR_ARG);
   TT_REQUIRE(x0.n2 == n2, TT_ERR_ARG);
+  // the precision forms judge interpolation no finer than their rounding
+  tol = effective_tol(ex, tol);
   ex.cross_calls++;
   Scope sc(*ex.ar);
   const EvalArgs ea = make_args(f);
@@ -364,10 +366,17 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
   int* dI = ex.ar->get<int>(cmax);
   int* dIprev = ex.ar->get<int>(cmax);
 
-  // 1. column pivots from the maxvol rows of an orthonormal basis of x0's second core
+  // 1. column pivots: proposed by the learned network when one is set,
+  // else the maxvol rows of an orthonormal basis of x0's second core
   std::vector<int> J;
   const int r0 = std::max(1, std::min({x0.r, cap, n1, n2}));
-  {
+  const bool learned = ex.pivot_net != nullptr && n2 > r0 && r0 <= 128;
+  bool first_check_converged = false;
+  if (learned) {
+    ex.learned_calls++;
+    mlp_propose(ex, *ex.pivot_net, x0, r0, dJ);
+    J = fetch_idx(ex, dJ, r0);
+  } else {
     Scope s2(*ex.ar);
     QRTree tb;
     tsqr(ex, x0.b, n2, x0.r, n2, tb);
@@ -423,7 +432,10 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
       double v[2];
       fetch_doubles(ex, nrm, 2, v);
       const double err = v[1] > 0.0 ? std::sqrt(v[0] / v[1]) : 0.0;
-      if (err <= tol) break;
+      if (err <= tol) {
+        first_check_converged = (s == 1);
+        break;
+      }
     }
     const int kc = orth_left(ex, C, n1, cj, tol, cap, Uc);
     maxvol(ex, Uc, n1, kc, 1e-2, 200, dI);
@@ -453,6 +465,10 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
     if (kr >= cap && std::set<int>(Jn.begin(), Jn.end()) == std::set<int>(J.begin(), J.end())) break;
     J = Jn;
   }
+  // the learned start is accepted when the first interpolation check on
+  // fresh fibres already passes; otherwise the maxvol sweeps above took over
+  if (learned && first_check_converged) ex.learned_accepted++;
+  if (ex.pivot_rec) record_pivots(ex, x0, J);
   // skeleton: A = Uc_prev (Uc_prev[I])^{-1}, B = F(I, :)^T = RT_prev[:, :k]
   {
     Scope s4(*ex.ar);

@@ -52,6 +52,7 @@ static TT const_tt(Exec& ex, int n1, int n2, double c) {
 
 // ============================================================== Algorithm 1
 int reciprocal(Exec& ex, const TT& x, double tol, int cap, int max_iter, TT& y, bool* noconv) {
+  tol = effective_tol(ex, tol);  // a precision form stops at its own rounding level
   Scope sc(*ex.ar);
   const int n1 = x.n1, n2 = x.n2;
   const double N = (double)n1 * n2;
@@ -154,14 +155,46 @@ struct Solver {
   Prof prof;
   StreamPool pool;
   double section_ms[6] = {};
-  ~Solver() {
-    for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
-    for (const Prof::Rec& r : prof.pending) {
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
-    }
-  }
+  MlpNet net;                      // learned-pivot network (caller-owned weights)
+  PivotRecorder* rec = nullptr;    // training-data capture, when enabled
+  ~Solver();
 };
+
+// Captured (features, label) rows of the crosses of one solver
+struct PivotRecorder {
+  std::mutex mu;
+  std::vector<float> X;  // rows x 12, row-major
+  std::vector<float> y;
+};
+
+Solver::~Solver() {
+  delete rec;
+  for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
+  for (const Prof::Rec& r : prof.pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+}
+
+void record_pivots(Exec& ex, const TT& x0, const std::vector<int>& J) {
+  if (ex.dry || !ex.pivot_rec) return;
+  const int n2 = x0.n2;
+  Scope sc(*ex.ar);
+  float* X = ex.ar->get<float>((size_t)n2 * kMlpFeatures);
+  mlp_features(ex, x0, X);
+  std::vector<float> h((size_t)n2 * kMlpFeatures);
+  TT_CUDA(cudaMemcpyAsync(h.data(), X, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, ex.s));
+  TT_CUDA(cudaStreamSynchronize(ex.s));
+  ex.syncs++;
+  std::vector<float> lab(n2, 0.0f);
+  for (int j : J)
+    if (j >= 0 && j < n2) lab[j] = 1.0f;
+  PivotRecorder& R = *ex.pivot_rec;
+  std::lock_guard<std::mutex> lk(R.mu);
+  for (int j = 0; j < n2; ++j)
+    for (int q = 0; q < kMlpFeatures; ++q) R.X.push_back(h[j + (size_t)q * n2]);
+  R.y.insert(R.y.end(), lab.begin(), lab.end());
+}
 
 static int nq_of(int recon) { return recon == TT_UP3 ? 2 : 3; }
 
@@ -492,6 +525,8 @@ static tt_status guard_status(Exec& ex) {
   TT_CUDA(cudaMemcpyAsync(&st, ex.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, ex.s));
   TT_CUDA(cudaStreamSynchronize(ex.s));
   prof_flush(ex);
+  if (st & DEV_TC_TIMEOUT) return TT_ERR_TIMEOUT;
+  if (st & DEV_NONFINITE) return TT_ERR_NONFINITE;
   if (st & DEV_JACOBI_NOCONV) return TT_ERR_NOCONV;
   return TT_OK;
 }
@@ -502,7 +537,8 @@ static bool valid_params(const tt_fv_params* p) {
   if (p->recon < TT_UP3 || p->recon > TT_WENO5) return false;
   if (p->nx < 8 || p->ny < 8 || p->rank_cap < 1 || p->rank_cap > 100) return false;
   if (!(p->tol >= 0.0) || !(p->dt > 0.0) || !(p->lx > 0.0) || !(p->ly > 0.0) || !(p->g > 0.0)) return false;
-  if (p->precision != TT_FP64 || p->pivots != TT_PIVOT_MAXVOL) return false;
+  if (p->precision < TT_FP64 || p->precision > TT_FP32) return false;
+  if (p->pivots != TT_PIVOT_MAXVOL && p->pivots != TT_PIVOT_LEARNED) return false;
   if (p->eqn == TT_LINEAR && !(p->H > 0.0)) return false;
   return true;
 }
@@ -579,9 +615,15 @@ struct tt_fv_ctx {
   Solver S;
 };
 
+namespace ttfv {
+// Batched form: whether an instance runs its independent stage tasks on its
+// own pool of streams (off: in order on the instance stream).
+void solver_task_pool(tt_fv_ctx* ctx, bool on) { ctx->S.ex.pool = on ? &ctx->S.pool : nullptr; }
+}  // namespace ttfv
+
 extern "C" {
 
-const char* tt_fv_version(void) { return "tt_fv 0.1 (sm_103a, FP64)"; }
+const char* tt_fv_version(void) { return "tt_fv 0.2 (sm_103a, FP64 path + FP32/TF32/BF16 precision forms)"; }
 
 static size_t solver_bytes(const tt_fv_params* p, bool with_state) {
   // dry run of one stage at the rank cap
@@ -592,6 +634,9 @@ static size_t solver_bytes(const tt_fv_params* p, bool with_state) {
   int hi[16];
   double hd[16];
   setup_exec(ex, S.ar, nullptr, 0, nullptr, hi, hd, true);
+  ex.precision = p->precision;
+  MlpNet dry_net;  // sizing pass: the proposal's scratch is counted, no weight is read
+  if (p->pivots == TT_PIVOT_LEARNED) ex.pivot_net = &dry_net;
   try {
     for (int c = 0; c < 3; ++c) {
       S.Qn[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
@@ -628,6 +673,7 @@ tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws
     setup_exec(S.ex, S.ar, ws, ws_bytes, S.s, S.h_int, S.h_dbl, false);
     S.ex.prof = &S.prof;
     S.ex.pool = &S.pool;
+    S.ex.precision = p->precision;
     for (int c = 0; c < 3; ++c) {
       S.Qn[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
       S.Qs[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
@@ -721,12 +767,61 @@ tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* o) {
   o->svd_p_sum = ex.svd_p;
   o->svd_pd_sum = ex.svd_pd;
   o->svd_sweeps_sum = ex.svd_sweeps;
+  o->learned_calls = ex.learned_calls;
+  o->learned_accepted = ex.learned_accepted;
   for (int i = 0; i < 6; ++i) o->section_ms[i] = S.section_ms[i];
   unsigned st = 0;
   if (cudaMemcpyAsync(&st, ex.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, S.s) != cudaSuccess ||
       cudaStreamSynchronize(S.s) != cudaSuccess)
     return TT_ERR_CUDA;
   o->device_status = st;
+  return TT_OK;
+}
+
+tt_status tt_fv_set_pivot_net(tt_fv_ctx* ctx, const tt_mlp* net) {
+  if (!ctx) return TT_ERR_ARG;
+  Solver& S = ctx->S;
+  if (!net) {
+    S.ex.pivot_net = nullptr;
+    return TT_OK;
+  }
+  if (S.p.pivots != TT_PIVOT_LEARNED || !net->W1 || !net->b1 || !net->W2 || !net->b2 || !net->w3 || !net->b3)
+    return TT_ERR_ARG;
+  S.net.W1 = net->W1;
+  S.net.b1 = net->b1;
+  S.net.W2 = net->W2;
+  S.net.b2 = net->b2;
+  S.net.w3 = net->w3;
+  S.net.b3 = net->b3;
+  S.ex.pivot_net = &S.net;
+  return TT_OK;
+}
+
+tt_status tt_fv_record_pivots(tt_fv_ctx* ctx, int32_t enable) {
+  if (!ctx) return TT_ERR_ARG;
+  Solver& S = ctx->S;
+  delete S.rec;
+  S.rec = enable ? new (std::nothrow) PivotRecorder() : nullptr;
+  if (enable && !S.rec) return TT_ERR_OOM;
+  S.ex.pivot_rec = S.rec;
+  return TT_OK;
+}
+
+int64_t tt_fv_pivot_rows(tt_fv_ctx* ctx) {
+  if (!ctx || !ctx->S.rec) return 0;
+  std::lock_guard<std::mutex> lk(ctx->S.rec->mu);
+  return (int64_t)ctx->S.rec->y.size();
+}
+
+tt_status tt_fv_pivot_take(tt_fv_ctx* ctx, float* X, float* y, int64_t rows) {
+  if (!ctx || !ctx->S.rec || !X || !y) return TT_ERR_ARG;
+  PivotRecorder& R = *ctx->S.rec;
+  std::lock_guard<std::mutex> lk(R.mu);
+  if (rows != (int64_t)R.y.size()) return TT_ERR_ARG;
+  std::memcpy(X, R.X.data(), sizeof(float) * R.X.size());
+  std::memcpy(y, R.y.data(), sizeof(float) * R.y.size());
+  R.X.clear();
+  R.y.clear();
   return TT_OK;
 }
 
@@ -817,6 +912,151 @@ tt_status tt_round_hadamard(const tt2* x, const tt2* z, double tol, int32_t rank
     TT X = to_tt(*x), Z = to_tt(*z), Y = to_tt(*y);
     round_hadamard(ex, X, Z, tol, rank_cap, Y);
     y->rank = Y.r;
+    return TT_OK;
+  });
+}
+
+// ---------------------------------------------------------------- dense contraction
+}  // extern "C"
+namespace ttfv {
+__global__ void k_pack_cols(const double* __restrict__ X, long ld, int m, int n, float* __restrict__ Y) {
+  const long total = (long)m * n;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x)
+    Y[t] = (float)X[(t % m) + (t / m) * ld];
+}
+__global__ void k_axpby_f32(int m, int n, double alpha, const float* __restrict__ P, double beta,
+                            double* __restrict__ C, long ldc) {
+  const long total = (long)m * n;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    double* c = C + (t % m) + (size_t)(t / m) * ldc;
+    *c = (beta == 0.0) ? alpha * (double)P[t] : fma(alpha, (double)P[t], beta * *c);
+  }
+}
+static void contract(Exec& ex, int precision, int split, int m, int n, int k, double alpha, const double* A, long lda,
+                     const double* B, long ldb, double beta, double* C, long ldc) {
+  if (precision == TT_FP64) {
+    gemm<double>(ex, m, n, k, alpha, A, 1, lda, B, 1, ldb, beta, C, ldc);
+    return;
+  }
+  Scope sc(*ex.ar);
+  float* P = ex.ar->get<float>((size_t)m * n);
+  if (precision == TT_FP32) {
+    float* A32 = ex.ar->get<float>((size_t)m * k);
+    float* B32 = ex.ar->get<float>((size_t)k * n);
+    if (!ex.dry) {
+      const int gA = std::max(1, std::min(ceil_div((long)m * k, 256), 1184));
+      const int gB = std::max(1, std::min(ceil_div((long)k * n, 256), 1184));
+      TT_KERNEL(ex, K_OTHER, 0, 12.0 * m * k, k_pack_cols<<<gA, 256, 0, ex.s>>>(A, lda, m, k, A32));
+      TT_KERNEL(ex, K_OTHER, 0, 12.0 * k * n, k_pack_cols<<<gB, 256, 0, ex.s>>>(B, ldb, k, n, B32));
+    }
+    gemm<float>(ex, m, n, k, 1.0f, A32, 1, m, B32, 1, k, 0.0f, P, m);
+  } else {
+    tc_gemm<double>(ex, precision, split != 0, m, n, k, 1.0f, A, 1, lda, B, 1, ldb, 0.0f, P, m);
+  }
+  if (ex.dry) return;
+  const long total = (long)m * n;
+  TT_KERNEL(ex, K_OTHER, 2.0 * total, 16.0 * total + 4.0 * total,
+            k_axpby_f32<<<std::max(1, std::min(ceil_div(total, 256), 1184)), 256, 0, ex.s>>>(m, n, alpha, P, beta,
+                                                                                               C, ldc));
+}
+}  // namespace ttfv
+extern "C" {
+
+size_t tt_contract_workspace_size(int32_t precision, int32_t split, int32_t m, int32_t n, int32_t k) {
+  if (precision < TT_FP64 || precision > TT_FP32 || m < 1 || n < 1 || k < 1) return 0;
+  return dry_bytes([&](Exec& ex) { contract(ex, precision, split, m, n, k, 1.0, nullptr, m, nullptr, k, 0.0,
+                                            nullptr, m); });
+}
+
+tt_status tt_contract(int32_t precision, int32_t split, int32_t m, int32_t n, int32_t k, double alpha,
+                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                      void* ws, size_t ws_bytes, void* stream) {
+  if (precision < TT_FP64 || precision > TT_FP32 || m < 1 || n < 1 || k < 1 || !A || !B || !C || lda < m ||
+      ldb < k || ldc < m)
+    return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    contract(ex, precision, split, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    return TT_OK;
+  });
+}
+
+// ---------------------------------------------------------------- learned-pivot network
+static bool valid_net(const tt_mlp* n) { return n && n->W1 && n->b1 && n->W2 && n->b2 && n->w3 && n->b3; }
+static MlpNet to_net(const tt_mlp* n) {
+  MlpNet m;
+  m.W1 = n->W1;
+  m.b1 = n->b1;
+  m.W2 = n->W2;
+  m.b2 = n->b2;
+  m.w3 = n->w3;
+  m.b3 = n->b3;
+  return m;
+}
+
+size_t tt_mlp_workspace_size(int32_t rows, int32_t rank) {
+  if (rows < 1 || rank < 1 || rank > 112) return 0;
+  return dry_bytes([&](Exec& ex) {
+    TT x0 = fake_tt(*ex.ar, rows, rows, rank);
+    float* X = ex.ar->get<float>((size_t)rows * kMlpFeatures);
+    float* y = ex.ar->get<float>((size_t)rows);
+    mlp_features(ex, x0, X);
+    MlpNet n, g;
+    mlp_grad(ex, n, X, y, rows, g, nullptr);
+    mlp_topk(ex, y, rows, std::min(rows, 112), nullptr);
+  });
+}
+
+tt_status tt_mlp_features(const tt2* x0, float* X, void* ws, size_t ws_bytes, void* stream) {
+  if (!valid_tt(x0) || x0->rank > 112 || !X) return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    mlp_features(ex, to_tt(*x0), X);
+    return TT_OK;
+  });
+}
+
+tt_status tt_mlp_forward(const tt_mlp* net, const float* X, int32_t m, float* s, void* ws, size_t ws_bytes,
+                         void* stream) {
+  if (!valid_net(net) || !X || !s || m < 1) return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    mlp_forward(ex, to_net(net), X, m, s);
+    return TT_OK;
+  });
+}
+
+tt_status tt_mlp_grad(const tt_mlp* net, const float* X, const float* y, int32_t m, const tt_mlp* grad, double* loss,
+                      void* ws, size_t ws_bytes, void* stream) {
+  if (!valid_net(net) || !valid_net(grad) || !X || !y || m < 1) return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    mlp_grad(ex, to_net(net), X, y, m, to_net(grad), loss);
+    return TT_OK;
+  });
+}
+
+tt_status tt_mlp_adam(const tt_mlp* net, const tt_mlp* grad, const tt_mlp* m1, const tt_mlp* m2, int32_t t, float lr,
+                      void* stream) {
+  if (!valid_net(net) || !valid_net(grad) || !valid_net(m1) || !valid_net(m2) || t < 1 || !(lr > 0.0f))
+    return TT_ERR_ARG;
+  Arena ar;
+  Exec ex;
+  int hi[16];
+  double hd[16];
+  try {
+    ar.dry = false;
+    ex.ar = &ar;
+    ex.s = static_cast<cudaStream_t>(stream);
+    ex.h_pinned = hi;
+    ex.h_pinned_d = hd;
+    mlp_adam(ex, to_net(net), to_net(grad), to_net(m1), to_net(m2), t, lr);
+  } catch (const Error& e) {
+    return e.code;
+  }
+  return TT_OK;
+}
+
+tt_status tt_mlp_topk(const float* s, int32_t m, int32_t k, int32_t* idx, void* ws, size_t ws_bytes, void* stream) {
+  if (!s || !idx || m < 1 || k < 1 || k > 128 || k > m) return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    mlp_topk(ex, s, m, k, idx);
     return TT_OK;
   });
 }

@@ -14,18 +14,8 @@
 
 namespace ttfv {
 
-static int g_sm_count = 0;
-static int sm_count() {
-  if (g_sm_count == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sm_count <= 0) g_sm_count = 152;
-  }
-  return g_sm_count;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename Real>
+__device__ __forceinline__ Real warp_sum(Real v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -47,18 +37,30 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
+// Smallest ||x|| for which a reflector is formed: below it ||x||^2 and the
+// products that scale the reflector leave the normal range (FP64: 1e-290,
+// FP32: 1e-34 for the squares), so the column is left as it is (tau = 0).
+// The entries skipped are at least 1e-145 (FP64) / 1e-17 (FP32) in absolute
+// size, far below the round-off of any block the rounding meets.
+template <typename Real>
+__host__ __device__ constexpr Real hh_safe_norm() {
+  return sizeof(Real) == 8 ? Real(1e-145) : Real(1e-17);
+}
+
 // Householder reflector of x = [alpha; tail] with sigma = ||tail||^2 known in
 // every lane: beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, scale =
 // 1/(alpha - beta).  GB300 builds FP64 sqrt/division from its few FP64 FMA
 // units, so lane 0 alone evaluates them and broadcasts the results.
-__device__ __forceinline__ void householder_params(double alpha, double sigma, double& beta, double& tau,
-                                                   double& scale) {
-  double b = alpha, t = 0.0, sc = 0.0;
-  if ((threadIdx.x & 31) == 0 && sigma > 0.0) {
-    const double nrm = sqrt(fma(alpha, alpha, sigma));
-    b = alpha >= 0.0 ? -nrm : nrm;
-    const double d = alpha - b;
-    sc = 1.0 / d;
+template <typename Real>
+__device__ __forceinline__ void householder_params(Real alpha, Real sigma, Real& beta, Real& tau,
+                                                   Real& scale) {
+  Real b = alpha, t = Real(0), sc = Real(0);
+  if ((threadIdx.x & 31) == 0 && sigma > Real(0) && fma(alpha, alpha, sigma) >= hh_safe_norm<Real>() *
+                                                                                 hh_safe_norm<Real>()) {
+    const Real nrm = sqrt(fma(alpha, alpha, sigma));
+    b = alpha >= Real(0) ? -nrm : nrm;
+    const Real d = alpha - b;
+    sc = Real(1) / d;
     t = -d / b;
   }
   beta = __shfl_sync(0xffffffffu, b, 0);
@@ -71,34 +73,35 @@ __device__ __forceinline__ void householder_params(double alpha, double sigma, d
 // 256 threads x 4 outputs; deterministic split-K through a partial buffer.
 constexpr int GB = 32, GK = 16;
 
+template <typename Real>
 __global__ void __launch_bounds__(256) k_gemm_partial(int M, int N, int K, int kchunk,
-                                                      const double* __restrict__ A, long ars, long acs,
-                                                      const double* __restrict__ B, long brs, long bcs,
-                                                      double* __restrict__ P) {
-  __shared__ double As[GK][GB + 1];
-  __shared__ double Bs[GK][GB + 1];
+                                                      const Real* __restrict__ A, long ars, long acs,
+                                                      const Real* __restrict__ B, long brs, long bcs,
+                                                      Real* __restrict__ P) {
+  __shared__ Real As[GK][GB + 1];
+  __shared__ Real Bs[GK][GB + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int i0 = blockIdx.x * GB, j0 = blockIdx.y * GB;
   const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  Real acc[2][2] = {{Real(0), Real(0)}, {Real(0), Real(0)}};
   for (int k0 = kb; k0 < ke; k0 += GK) {
     for (int t = threadIdx.x; t < GB * GK; t += 256) {
       int ii, kk;
       if (ars == 1) { ii = t % GB; kk = t / GB; } else { kk = t % GK; ii = t / GK; }
       const int gi = i0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < M && gk < ke) ? A[gi * ars + gk * acs] : 0.0;
+      As[kk][ii] = (gi < M && gk < ke) ? A[gi * ars + gk * acs] : Real(0);
     }
     for (int t = threadIdx.x; t < GB * GK; t += 256) {
       int jj, kk;
       if (brs == 1) { kk = t % GK; jj = t / GK; } else { jj = t % GB; kk = t / GB; }
       const int gj = j0 + jj, gk = k0 + kk;
-      Bs[kk][jj] = (gj < N && gk < ke) ? B[gk * brs + gj * bcs] : 0.0;
+      Bs[kk][jj] = (gj < N && gk < ke) ? B[gk * brs + gj * bcs] : Real(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      const double a0 = As[kk][tx], a1 = As[kk][tx + 16];
-      const double b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+      const Real a0 = As[kk][tx], a1 = As[kk][tx + 16];
+      const Real b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
       acc[0][0] = fma(a0, b0, acc[0][0]);
       acc[0][1] = fma(a0, b1, acc[0][1]);
       acc[1][0] = fma(a1, b0, acc[1][0]);
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(256) k_gemm_partial(int M, int N, int K, int k
     }
     __syncthreads();
   }
-  double* Pz = P + (size_t)blockIdx.z * M * N;
+  Real* Pz = P + (size_t)blockIdx.z * M * N;
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -116,52 +119,55 @@ __global__ void __launch_bounds__(256) k_gemm_partial(int M, int N, int K, int k
     }
 }
 
-__global__ void k_gemm_reduce(int M, int N, int nsplit, const double* __restrict__ P, double alpha,
-                              double beta, double* __restrict__ C, long ldc) {
+template <typename Real>
+__global__ void k_gemm_reduce(int M, int N, int nsplit, const Real* __restrict__ P, Real alpha, Real beta,
+                              Real* __restrict__ C, long ldc) {
   const long total = (long)M * N;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-    double s = 0.0;
+    Real s = Real(0);
     for (int z = 0; z < nsplit; ++z) s += P[t + (size_t)z * total];
     const int i = int(t % M), j = int(t / M);
-    double* c = C + i + (size_t)j * ldc;
-    *c = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *c);
+    Real* c = C + i + (size_t)j * ldc;
+    *c = (beta == Real(0)) ? alpha * s : fma(alpha, s, beta * *c);
   }
 }
 
-void gemm(Exec& ex, int M, int N, int K, double alpha, const double* A, long ars, long acs,
-          const double* B, long brs, long bcs, double beta, double* C, long ldc) {
+template <typename Real>
+void gemm(Exec& ex, int M, int N, int K, Real alpha, const Real* A, long ars, long acs, const Real* B, long brs, long bcs,
+          Real beta, Real* C, long ldc) {
   if (M <= 0 || N <= 0) return;
   const int tiles = ceil_div(M, GB) * ceil_div(N, GB);
   int nsplit = std::max(1, std::min(ceil_div(2 * sm_count(), tiles), ceil_div(std::max(K, 1), 64)));
   int kchunk = ceil_div(ceil_div(std::max(K, 1), nsplit), GK) * GK;
   nsplit = ceil_div(std::max(K, 1), kchunk);
   Scope sc(*ex.ar);
-  double* P = ex.ar->get<double>((size_t)nsplit * M * N);
+  Real* P = ex.ar->get<Real>((size_t)nsplit * M * N);
   if (ex.dry) return;
   dim3 grid(ceil_div(M, GB), ceil_div(N, GB), nsplit);
   const double mnk = 2.0 * M * N * (double)K;
-  TT_KERNEL(ex, K_GEMM, mnk, 8.0 * ((double)M * K + (double)K * N + (double)nsplit * M * N),
-            k_gemm_partial<<<grid, 256, 0, ex.s>>>(M, N, K, kchunk, A, ars, acs, B, brs, bcs, P));
+  TT_KERNEL(ex, K_GEMM, mnk, (double)sizeof(Real) * ((double)M * K + (double)K * N + (double)nsplit * M * N),
+            k_gemm_partial<Real><<<grid, 256, 0, ex.s>>>(M, N, K, kchunk, A, ars, acs, B, brs, bcs, P));
   const long total = (long)M * N;
   const int blocks = std::max(1, std::min(ceil_div(total, 256), 4 * sm_count()));
-  TT_KERNEL(ex, K_GEMM, (double)nsplit * total, 8.0 * total * (nsplit + (beta == 0.0 ? 1 : 2)),
-            k_gemm_reduce<<<blocks, 256, 0, ex.s>>>(M, N, nsplit, P, alpha, beta, C, ldc));
+  TT_KERNEL(ex, K_GEMM, (double)nsplit * total, (double)sizeof(Real) * total * (nsplit + (beta == Real(0) ? 1 : 2)),
+            k_gemm_reduce<Real><<<blocks, 256, 0, ex.s>>>(M, N, nsplit, P, alpha, beta, C, ldc));
 }
 
 // ============================================================== Hadamard slab
 // Y[i,j] = (A1 B1^T)[i,j] * (A2 B2^T)[i,j]: the full face tensor of a TT
 // Hadamard product, formed without the r1*r2-column Khatri-Rao cores.
 constexpr int HB = 32, HK = 16;
+template <typename Real>
 __global__ void __launch_bounds__(256) k_form_hadamard(int n1, int n2, const double* __restrict__ A1, int r1,
                                                        const double* __restrict__ B1,
                                                        const double* __restrict__ A2, int r2,
-                                                       const double* __restrict__ B2,
-                                                       double* __restrict__ Y, long ldy) {
-  __shared__ double As[HK][HB + 1];
-  __shared__ double Bs[HK][HB + 1];
+                                                       const double* __restrict__ B2, Real* __restrict__ Y,
+                                                       long ldy) {
+  __shared__ Real As[HK][HB + 1];
+  __shared__ Real Bs[HK][HB + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int i0 = blockIdx.x * HB, j0 = blockIdx.y * HB;
-  double acc[2][2][2] = {};
+  Real acc[2][2][2] = {};
   for (int f = 0; f < 2; ++f) {
     const double* A = f ? A2 : A1;
     const double* B = f ? B2 : B1;
@@ -170,14 +176,14 @@ __global__ void __launch_bounds__(256) k_form_hadamard(int n1, int n2, const dou
       for (int t = threadIdx.x; t < HB * HK; t += 256) {
         const int ii = t % HB, kk = t / HB;
         const int gi = i0 + ii, gj = j0 + ii, gk = k0 + kk;
-        As[kk][ii] = (gi < n1 && gk < r) ? A[gi + (size_t)gk * n1] : 0.0;
-        Bs[kk][ii] = (gj < n2 && gk < r) ? B[gj + (size_t)gk * n2] : 0.0;
+        As[kk][ii] = (gi < n1 && gk < r) ? Real(A[gi + (size_t)gk * n1]) : Real(0);
+        Bs[kk][ii] = (gj < n2 && gk < r) ? Real(B[gj + (size_t)gk * n2]) : Real(0);
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < HK; ++kk) {
-        const double a0 = As[kk][tx], a1 = As[kk][tx + 16];
-        const double b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+        const Real a0 = As[kk][tx], a1 = As[kk][tx + 16];
+        const Real b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
         acc[f][0][0] = fma(a0, b0, acc[f][0][0]);
         acc[f][0][1] = fma(a0, b1, acc[f][0][1]);
         acc[f][1][0] = fma(a1, b0, acc[f][1][0]);
@@ -195,22 +201,24 @@ __global__ void __launch_bounds__(256) k_form_hadamard(int n1, int n2, const dou
     }
 }
 
-void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, const double* B1,
-                        const double* A2, int r2, const double* B2, double* Y, long ldy) {
+template <typename Real>
+void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, const double* B1, const double* A2, int r2,
+                        const double* B2, Real* Y, long ldy) {
   if (ex.dry) return;
   dim3 grid(ceil_div(n1, HB), ceil_div(n2, HB));
   TT_KERNEL(ex, K_FORM, 2.0 * n1 * (double)n2 * (r1 + r2) + (double)n1 * n2,
-            8.0 * ((double)(n1 + n2) * (r1 + r2) + (double)n1 * n2),
-            k_form_hadamard<<<grid, 256, 0, ex.s>>>(n1, n2, A1, r1, B1, A2, r2, B2, Y, ldy));
+            8.0 * (double)(n1 + n2) * (r1 + r2) + (double)sizeof(Real) * n1 * n2,
+            k_form_hadamard<Real><<<grid, 256, 0, ex.s>>>(n1, n2, A1, r1, B1, A2, r2, B2, Y, ldy));
 }
 
 // ============================================================== sum of squares
-__global__ void k_sumsq_partial(const double* __restrict__ X, int m, int n, long ld, double* part) {
+template <typename Real>
+__global__ void k_sumsq_partial(const Real* __restrict__ X, int m, int n, long ld, double* part) {
   __shared__ double red[33];
   double s = 0.0;
   const long total = (long)m * n;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-    const double x = X[(t % m) + (t / m) * ld];
+    const double x = (double)X[(t % m) + (t / m) * ld];
     s = fma(x, x, s);
   }
   s = block_sum(s, red);
@@ -224,13 +232,14 @@ __global__ void k_sum_fixed(const double* part, int n, double* out) {
   if (threadIdx.x == 0) *out = s;
 }
 
-void sumsq(Exec& ex, const double* X, int m, int n, long ld, double* out) {
+template <typename Real>
+void sumsq(Exec& ex, const Real* X, int m, int n, long ld, double* out) {
   Scope sc(*ex.ar);
   const int blocks = std::max(1, std::min(ceil_div((long)m * n, 256), 2 * sm_count()));
   double* part = ex.ar->get<double>(blocks);
   if (ex.dry) return;
-  TT_KERNEL(ex, K_OTHER, 2.0 * m * (double)n, 8.0 * m * (double)n,
-            k_sumsq_partial<<<blocks, 256, 0, ex.s>>>(X, m, n, ld, part));
+  TT_KERNEL(ex, K_OTHER, 2.0 * m * (double)n, (double)sizeof(Real) * m * (double)n,
+            k_sumsq_partial<Real><<<blocks, 256, 0, ex.s>>>(X, m, n, ld, part));
   TT_KERNEL(ex, K_OTHER, blocks, 8.0 * blocks, k_sum_fixed<<<1, 256, 0, ex.s>>>(part, blocks, out));
 }
 
@@ -243,22 +252,23 @@ constexpr size_t QR_SMEM_MAX = 200 * 1024;
 // Two barriers per column: warp 0 forms the reflector of column j (its norm
 // below the diagonal was computed by warp 0 while updating that column in
 // the previous step), then all warps update the trailing columns.
-__device__ void cta_householder_qr(double* A, int mb, int p, double* tau_out) {
+template <typename Real>
+__device__ void cta_householder_qr(Real* A, int mb, int p, Real* tau_out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ double s_tau;
-  double next_sigma = 0.0;  // warp 0: sum of squares of column j below row j
+  __shared__ Real s_tau;
+  Real next_sigma = Real(0);  // warp 0: sum of squares of column j below row j
   if (w == 0) {
-    double s = 0.0;
+    Real s = Real(0);
     for (int i = 1 + lane; i < mb; i += 32) s = fma(A[i], A[i], s);
     next_sigma = warp_sum(s);
   }
   for (int j = 0; j < p; ++j) {
-    double* col = A + (size_t)j * mb;
+    Real* col = A + (size_t)j * mb;
     if (w == 0) {
-      const double sigma = next_sigma, alpha = col[j];
-      double tau, beta, scale;
+      const Real sigma = next_sigma, alpha = col[j];
+      Real tau, beta, scale;
       householder_params(alpha, sigma, beta, tau, scale);
-      if (sigma > 0.0)
+      if (sigma > Real(0))
         for (int i = j + 1 + lane; i < mb; i += 32) col[i] *= scale;
       if (lane == 0) {
         col[j] = beta;
@@ -267,20 +277,20 @@ __device__ void cta_householder_qr(double* A, int mb, int p, double* tau_out) {
       }
     }
     __syncthreads();
-    const double tau = s_tau;
+    const Real tau = s_tau;
     for (int c = j + 1 + w; c < p; c += nw) {
-      double* cc = A + (size_t)c * mb;
-      if (tau != 0.0) {
-        double d = 0.0;
+      Real* cc = A + (size_t)c * mb;
+      if (tau != Real(0)) {
+        Real d = Real(0);
         for (int i = j + 1 + lane; i < mb; i += 32) d = fma(col[i], cc[i], d);
         d = warp_sum(d) + cc[j];
-        const double f = tau * d;
+        const Real f = tau * d;
         if (lane == 0) cc[j] -= f;
         for (int i = j + 1 + lane; i < mb; i += 32) cc[i] = fma(-f, col[i], cc[i]);
       }
       if (c == j + 1) {  // warp 0: norm of the next column below its diagonal
         __syncwarp();
-        double s = 0.0;
+        Real s = Real(0);
         for (int i = j + 2 + lane; i < mb; i += 32) s = fma(cc[i], cc[i], s);
         next_sigma = warp_sum(s);
       }
@@ -289,23 +299,25 @@ __device__ void cta_householder_qr(double* A, int mb, int p, double* tau_out) {
   }
 }
 
-__global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const double* __restrict__ X, int m, int p, long ldx,
-                                                          int mb, double* V, double* tau, double* Rout) {
-  extern __shared__ double sm[];
+template <typename Real>
+__global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const Real* __restrict__ X, int m, int p, long ldx,
+                                                          int mb, Real* V, Real* tau, Real* Rout) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Real* sm = reinterpret_cast<Real*>(smraw);
   const int b = blockIdx.x, r0 = b * mb;
-  double* A = sm;
+  Real* A = sm;
   for (int t = threadIdx.x; t < mb * p; t += blockDim.x) {
     const int i = t % mb, j = t / mb;
-    A[t] = (r0 + i < m) ? X[(r0 + i) + (size_t)j * ldx] : 0.0;
+    A[t] = (r0 + i < m) ? X[(r0 + i) + (size_t)j * ldx] : Real(0);
   }
   __syncthreads();
-  cta_householder_qr(A, mb, p, tau + (size_t)b * p);
-  double* Vb = V + (size_t)b * mb * p;
+  cta_householder_qr<Real>(A, mb, p, tau + (size_t)b * p);
+  Real* Vb = V + (size_t)b * mb * p;
   for (int t = threadIdx.x; t < mb * p; t += blockDim.x) Vb[t] = A[t];
-  double* Rb = Rout + (size_t)b * p * p;
+  Real* Rb = Rout + (size_t)b * p * p;
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
     const int i = t % p, j = t / p;
-    Rb[t] = (i <= j) ? A[i + (size_t)j * mb] : 0.0;
+    Rb[t] = (i <= j) ? A[i + (size_t)j * mb] : Real(0);
   }
 }
 
@@ -315,27 +327,29 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const double* __restri
 // row j; B_b(0..j, j)], tau = -1 / (beta (alpha - beta)), so no scaling pass
 // is needed.  Columns are spread over lanes (lane = column within a group of
 // 32), the bottom blocks over warps; a node with one input passes it through.
-__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restrict__ Rin, int nin, int p, int g,
-                                                         double* Rout, double* Vm, double* vtop, double* taum) {
-  extern __shared__ double sm[];
+template <typename Real>
+__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const Real* __restrict__ Rin, int nin, int p, int g,
+                                                         Real* Rout, Real* Vm, Real* vtop, Real* taum) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Real* sm = reinterpret_cast<Real*>(smraw);
   const int node = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int first = node * g, ng = min(g, nin - first);
-  double* Ro = Rout + (size_t)node * p * p;
-  double* Vo = Vm + (size_t)node * g * p * p;  // bottom blocks 1..ng-1 at Vo + b*p*p
-  double* vt = vtop + (size_t)node * p;
-  double* to = taum + (size_t)node * p;
-  const double* Ri = Rin + (size_t)first * p * p;
+  Real* Ro = Rout + (size_t)node * p * p;
+  Real* Vo = Vm + (size_t)node * g * p * p;  // bottom blocks 1..ng-1 at Vo + b*p*p
+  Real* vt = vtop + (size_t)node * p;
+  Real* to = taum + (size_t)node * p;
+  const Real* Ri = Rin + (size_t)first * p * p;
   if (ng == 1) {
     for (int t = threadIdx.x; t < p * p; t += blockDim.x) Ro[t] = Ri[t];
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
-      to[j] = 0.0;
-      vt[j] = 0.0;
+      to[j] = Real(0);
+      vt[j] = Real(0);
     }
     return;
   }
-  double* T = sm;                       // block 0 (p x p)
-  double* part = sm + (size_t)ng * p * p;  // [slice][column] partial sums
-  __shared__ double s_tau, s_vj, s_sig;
+  Real* T = sm;                       // block 0 (p x p)
+  Real* part = sm + (size_t)ng * p * p;  // [slice][column] partial sums
+  __shared__ Real s_tau, s_vj, s_sig;
   for (int t = threadIdx.x; t < ng * p * p; t += blockDim.x) T[t] = Ri[t];
   const int G = (p + 31) / 32;
   const int S = max(1, nw / G);
@@ -345,20 +359,20 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restric
   // norm below the diagonal of column 0: sum over bottoms of B_b[0,0]^2
   __syncthreads();
   if (threadIdx.x == 0) {
-    double sg = 0.0;
+    Real sg = Real(0);
     for (int b = 1; b < ng; ++b) sg = fma(T[(size_t)b * p * p], T[(size_t)b * p * p], sg);
     s_sig = sg;
   }
   __syncthreads();
   for (int j = 0; j < p; ++j) {
     if (threadIdx.x == 0) {
-      const double sg = s_sig, alpha = T[j + (size_t)j * p];
-      double tau = 0.0, vj = 0.0, beta = alpha;
-      if (sg > 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, sg));
-        beta = alpha >= 0.0 ? -nrm : nrm;
+      const Real sg = s_sig, alpha = T[j + (size_t)j * p];
+      Real tau = Real(0), vj = Real(0), beta = alpha;
+      if (sg > Real(0) && fma(alpha, alpha, sg) >= hh_safe_norm<Real>() * hh_safe_norm<Real>()) {
+        const Real nrm = sqrt(fma(alpha, alpha, sg));
+        beta = alpha >= Real(0) ? -nrm : nrm;
         vj = alpha - beta;
-        tau = -1.0 / (beta * vj);
+        tau = Real(-1) / (beta * vj);
       }
       s_tau = tau;
       s_vj = vj;
@@ -367,29 +381,29 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restric
       T[j + (size_t)j * p] = beta;
     }
     __syncthreads();
-    const double tau = s_tau, vj = s_vj;
-    if (tau != 0.0) {
+    const Real tau = s_tau, vj = s_vj;
+    if (tau != Real(0)) {
       // partial dots of column c with v over this slice's bottom blocks
       if (active && c > j) {
-        double d = 0.0;
+        Real d = Real(0);
         for (int b = 1 + sl; b < ng; b += S) {
-          const double* Bb = T + (size_t)b * p * p;
+          const Real* Bb = T + (size_t)b * p * p;
           for (int i = 0; i <= j; ++i) d = fma(Bb[i + (size_t)j * p], Bb[i + (size_t)c * p], d);
         }
         part[(size_t)sl * p + c] = d;
       }
       __syncthreads();
       if (active && sl == 0 && c > j) {
-        double d = vj * T[j + (size_t)c * p];
+        Real d = vj * T[j + (size_t)c * p];
         for (int q = 0; q < S; ++q) d += part[(size_t)q * p + c];
         part[c] = tau * d;  // f_c (slice 0 row of the partial table)
       }
       __syncthreads();
       if (active && c > j) {
-        const double f = part[c];
+        const Real f = part[c];
         if (sl == 0) T[j + (size_t)c * p] -= f * vj;
         for (int b = 1 + sl; b < ng; b += S) {
-          double* Bb = T + (size_t)b * p * p;
+          Real* Bb = T + (size_t)b * p * p;
           for (int i = 0; i <= j; ++i) Bb[i + (size_t)c * p] = fma(-f, Bb[i + (size_t)j * p], Bb[i + (size_t)c * p]);
         }
       }
@@ -398,16 +412,16 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restric
     // norm of column j+1 below its diagonal: bottoms' rows 0..j+1
     if (j + 1 < p) {
       if (active && c == j + 1) {
-        double sg = 0.0;
+        Real sg = Real(0);
         for (int b = 1 + sl; b < ng; b += S) {
-          const double* Bb = T + (size_t)b * p * p;
+          const Real* Bb = T + (size_t)b * p * p;
           for (int i = 0; i <= j + 1; ++i) sg = fma(Bb[i + (size_t)c * p], Bb[i + (size_t)c * p], sg);
         }
         part[(size_t)sl * p + c] = sg;
       }
       __syncthreads();
       if (threadIdx.x == 0) {
-        double sg = 0.0;
+        Real sg = Real(0);
         for (int q = 0; q < S; ++q) sg += part[(size_t)q * p + j + 1];
         s_sig = sg;
       }
@@ -416,60 +430,61 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const double* __restric
   }
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
     const int i = t % p, jj = t / p;
-    Ro[t] = (i <= jj) ? T[t] : 0.0;
+    Ro[t] = (i <= jj) ? T[t] : Real(0);
   }
   for (int t = threadIdx.x; t < (ng - 1) * p * p; t += blockDim.x) {
     const int i = t % p, jj = (t / p) % p;
-    Vo[(size_t)p * p + t] = (i <= jj) ? T[(size_t)p * p + t] : 0.0;
+    Vo[(size_t)p * p + t] = (i <= jj) ? T[(size_t)p * p + t] : Real(0);
   }
 }
 
 // fan-in of a merge node: as many triangles as fit in shared memory
-static int qr_merge_fanin(int p) {
-  const size_t per = (size_t)p * p * 8 + (size_t)16 * p * 8;
+static int qr_merge_fanin(int p, size_t elem) {
+  const size_t per = ((size_t)p * p + (size_t)16 * p) * elem;
   return std::max(2, int(QR_SMEM_MAX / per));
 }
 
-static int qr_leaf_rows(int p) {
+static int qr_leaf_rows(int p, size_t elem) {
   int mb = std::max(((p + 31) / 32) * 32, 64);
-  const int lim = int(QR_SMEM_MAX / (8 * (size_t)p));
+  const int lim = int(QR_SMEM_MAX / (elem * (size_t)p));
   return std::max(std::min(mb, lim), p);
 }
 
-void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t) {
+template <typename Real>
+void tsqr(Exec& ex, const Real* X, int m, int p, long ldx, QRTreeT<Real>& t) {
   TT_REQUIRE(p >= 1 && p <= 112 && m >= 1, TT_ERR_ARG);
-  t = QRTree{};
+  t = QRTreeT<Real>{};
   t.m = m;
   t.p = p;
-  t.mb0 = qr_leaf_rows(p);
+  t.mb0 = qr_leaf_rows(p, sizeof(Real));
   t.nb0 = ceil_div(m, t.mb0);
-  t.V0 = ex.ar->get<double>((size_t)t.nb0 * t.mb0 * p);
-  t.tau0 = ex.ar->get<double>((size_t)t.nb0 * p);
-  double* R = ex.ar->get<double>((size_t)t.nb0 * p * p);
+  t.V0 = ex.ar->get<Real>((size_t)t.nb0 * t.mb0 * p);
+  t.tau0 = ex.ar->get<Real>((size_t)t.nb0 * p);
+  Real* R = ex.ar->get<Real>((size_t)t.nb0 * p * p);
   if (!ex.dry) {
-    smem_attr_once(k_qr_blocks);
-    const size_t smem = (size_t)t.mb0 * p * 8;
+    smem_attr_once(k_qr_blocks<Real>);
+    const size_t smem = (size_t)t.mb0 * p * sizeof(Real);
     const double fl = 2.0 * m * (double)p * p - t.nb0 * (2.0 / 3.0) * p * (double)p * p;
-    TT_KERNEL(ex, K_QR, std::max(fl, 0.0), 8.0 * ((double)m * p * 2 + (double)t.nb0 * p * p),
-              k_qr_blocks<<<t.nb0, QR_THREADS, smem, ex.s>>>(X, m, p, ldx, t.mb0, t.V0, t.tau0, R));
+    TT_KERNEL(ex, K_QR, std::max(fl, 0.0), (double)sizeof(Real) * ((double)m * p * 2 + (double)t.nb0 * p * p),
+              k_qr_blocks<Real><<<t.nb0, QR_THREADS, smem, ex.s>>>(X, m, p, ldx, t.mb0, t.V0, t.tau0, R));
   }
   int n = t.nb0;
-  const int g = qr_merge_fanin(p);
+  const int g = qr_merge_fanin(p, sizeof(Real));
   while (n > 1) {
     const int nodes = (n + g - 1) / g;
-    double* Vm = ex.ar->get<double>((size_t)nodes * g * p * p);
-    double* vt = ex.ar->get<double>((size_t)nodes * p);
-    double* tm = ex.ar->get<double>((size_t)nodes * p);
-    double* Rn = ex.ar->get<double>((size_t)nodes * p * p);
+    Real* Vm = ex.ar->get<Real>((size_t)nodes * g * p * p);
+    Real* vt = ex.ar->get<Real>((size_t)nodes * p);
+    Real* tm = ex.ar->get<Real>((size_t)nodes * p);
+    Real* Rn = ex.ar->get<Real>((size_t)nodes * p * p);
     t.nin.push_back(n);
     t.Vm.push_back(Vm);
     t.vtop.push_back(vt);
     t.taum.push_back(tm);
     if (!ex.dry) {
-      smem_attr_once(k_qr_merge);
-      const size_t smem = (size_t)std::min(g, n) * p * p * 8 + (size_t)16 * p * 8;
-      TT_KERNEL(ex, K_QR, (n - nodes) * (2.0 / 3.0) * p * (double)p * p, 8.0 * 3.0 * n * p * (double)p,
-                k_qr_merge<<<nodes, QR_THREADS, smem, ex.s>>>(R, n, p, g, Rn, Vm, vt, tm));
+      smem_attr_once(k_qr_merge<Real>);
+      const size_t smem = ((size_t)std::min(g, n) * p * p + (size_t)16 * p) * sizeof(Real);
+      TT_KERNEL(ex, K_QR, (n - nodes) * (2.0 / 3.0) * p * (double)p * p, (double)sizeof(Real) * 3.0 * n * p * (double)p,
+                k_qr_merge<Real><<<nodes, QR_THREADS, smem, ex.s>>>(R, n, p, g, Rn, Vm, vt, tm));
     }
     R = Rn;
     n = nodes;
@@ -480,32 +495,34 @@ void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t) {
 
 // Apply the level-0 reflectors of each block (in reverse order) to
 // [Zin_block; 0], Zin_block = Zin + b*zstride (p x k, ld zld).
-__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const double* __restrict__ V,
-                                                                const double* __restrict__ tau, int mb, int p,
-                                                                int rows, int k, const double* __restrict__ Zin,
-                                                                long zstride, long zld, double* __restrict__ Zout,
+template <typename Real>
+__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const Real* __restrict__ V,
+                                                                const Real* __restrict__ tau, int mb, int p,
+                                                                int rows, int k, const Real* __restrict__ Zin,
+                                                                long zstride, long zld, Real* __restrict__ Zout,
                                                                 long ldzo) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Real* sm = reinterpret_cast<Real*>(smraw);
   const int b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* Z = sm;  // mb x k
-  const double* zb = Zin + (size_t)b * zstride;
+  Real* Z = sm;  // mb x k
+  const Real* zb = Zin + (size_t)b * zstride;
   for (int t = threadIdx.x; t < mb * k; t += blockDim.x) {
     const int i = t % mb, j = t / mb;
-    Z[t] = (i < p) ? zb[i + (size_t)j * zld] : 0.0;
+    Z[t] = (i < p) ? zb[i + (size_t)j * zld] : Real(0);
   }
   __syncthreads();
-  const double* Vb = V + (size_t)b * mb * p;
-  const double* tb = tau + (size_t)b * p;
+  const Real* Vb = V + (size_t)b * mb * p;
+  const Real* tb = tau + (size_t)b * p;
   for (int jr = p - 1; jr >= 0; --jr) {
-    const double tj = tb[jr];
-    if (tj != 0.0) {
-      const double* v = Vb + (size_t)jr * mb;
+    const Real tj = tb[jr];
+    if (tj != Real(0)) {
+      const Real* v = Vb + (size_t)jr * mb;
       for (int c = w; c < k; c += nw) {
-        double* zc = Z + (size_t)c * mb;
-        double d = 0.0;
+        Real* zc = Z + (size_t)c * mb;
+        Real d = Real(0);
         for (int i = jr + 1 + lane; i < mb; i += 32) d = fma(v[i], zc[i], d);
         d = warp_sum(d) + zc[jr];
-        const double f = tj * d;
+        const Real f = tj * d;
         if (lane == 0) zc[jr] -= f;
         for (int i = jr + 1 + lane; i < mb; i += 32) zc[i] = fma(-f, v[i], zc[i]);
       }
@@ -521,27 +538,29 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const double* __
 
 // Reverse of a merge node: [top; B_1; ...] = Q_node [Z; 0; ...]; the top goes
 // to input node*g, block b to input node*g + b (each p x k, ld p).
-__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(const double* __restrict__ Vm,
-                                                               const double* __restrict__ vtop,
-                                                               const double* __restrict__ taum, int nin, int p,
-                                                               int g, int k, const double* __restrict__ Zin,
-                                                               long zstride, long zld, double* __restrict__ Zout) {
-  extern __shared__ double sm[];
+template <typename Real>
+__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(const Real* __restrict__ Vm,
+                                                               const Real* __restrict__ vtop,
+                                                               const Real* __restrict__ taum, int nin, int p,
+                                                               int g, int k, const Real* __restrict__ Zin,
+                                                               long zstride, long zld, Real* __restrict__ Zout) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Real* sm = reinterpret_cast<Real*>(smraw);
   const int node = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int first = node * g, ng = min(g, nin - first);
-  const double* zb = Zin + (size_t)node * zstride;
-  double* out = Zout + (size_t)first * p * k;
+  const Real* zb = Zin + (size_t)node * zstride;
+  Real* out = Zout + (size_t)first * p * k;
   if (ng == 1) {
     for (int t = threadIdx.x; t < p * k; t += blockDim.x) out[t] = zb[(t % p) + (size_t)(t / p) * zld];
     return;
   }
-  double* Z = sm;                          // ng blocks of p x k
-  double* part = sm + (size_t)ng * p * k;  // [slice][column]
+  Real* Z = sm;                          // ng blocks of p x k
+  Real* part = sm + (size_t)ng * p * k;  // [slice][column]
   for (int t = threadIdx.x; t < p * k; t += blockDim.x) Z[t] = zb[(t % p) + (size_t)(t / p) * zld];
-  for (int t = threadIdx.x; t < (ng - 1) * p * k; t += blockDim.x) Z[(size_t)p * k + t] = 0.0;
-  const double* V = Vm + (size_t)node * g * p * p;
-  const double* vt = vtop + (size_t)node * p;
-  const double* tv = taum + (size_t)node * p;
+  for (int t = threadIdx.x; t < (ng - 1) * p * k; t += blockDim.x) Z[(size_t)p * k + t] = Real(0);
+  const Real* V = Vm + (size_t)node * g * p * p;
+  const Real* vt = vtop + (size_t)node * p;
+  const Real* tv = taum + (size_t)node * p;
   const int G = (k + 31) / 32;
   const int S = max(1, nw / G);
   const int grp = w % G, sl = w / G;
@@ -549,31 +568,31 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(const double* __r
   const bool active = (sl < S) && (c < k);
   __syncthreads();
   for (int j = p - 1; j >= 0; --j) {
-    const double tj = tv[j];
-    if (tj == 0.0) continue;  // uniform across the block
-    const double vj = vt[j];
+    const Real tj = tv[j];
+    if (tj == Real(0)) continue;  // uniform across the block
+    const Real vj = vt[j];
     if (active) {
-      double d = 0.0;
+      Real d = Real(0);
       for (int b = 1 + sl; b < ng; b += S) {
-        const double* Vb = V + (size_t)b * p * p + (size_t)j * p;
-        const double* Zb = Z + (size_t)b * p * k + (size_t)c * p;
+        const Real* Vb = V + (size_t)b * p * p + (size_t)j * p;
+        const Real* Zb = Z + (size_t)b * p * k + (size_t)c * p;
         for (int i = 0; i <= j; ++i) d = fma(Vb[i], Zb[i], d);
       }
       part[(size_t)sl * k + c] = d;
     }
     __syncthreads();
     if (active && sl == 0) {
-      double d = vj * Z[j + (size_t)c * p];
+      Real d = vj * Z[j + (size_t)c * p];
       for (int q = 0; q < S; ++q) d += part[(size_t)q * k + c];
       part[c] = tj * d;
     }
     __syncthreads();
     if (active) {
-      const double f = part[c];
+      const Real f = part[c];
       if (sl == 0) Z[j + (size_t)c * p] -= f * vj;
       for (int b = 1 + sl; b < ng; b += S) {
-        const double* Vb = V + (size_t)b * p * p + (size_t)j * p;
-        double* Zb = Z + (size_t)b * p * k + (size_t)c * p;
+        const Real* Vb = V + (size_t)b * p * p + (size_t)j * p;
+        Real* Zb = Z + (size_t)b * p * k + (size_t)c * p;
         for (int i = 0; i <= j; ++i) Zb[i] = fma(-f, Vb[i], Zb[i]);
       }
     }
@@ -582,21 +601,22 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(const double* __r
   for (int t = threadIdx.x; t < ng * p * k; t += blockDim.x) out[t] = Z[t];
 }
 
-void tsqr_apply(Exec& ex, const QRTree& t, const double* C, int k, long ldc, double* Out, long ldo) {
+template <typename Real>
+void tsqr_apply(Exec& ex, const QRTreeT<Real>& t, const Real* C, int k, long ldc, Real* Out, long ldo) {
   TT_REQUIRE(k >= 1 && k <= t.p, TT_ERR_ARG);
   Scope sc(*ex.ar);
   const int p = t.p;
-  const double* zin = C;
+  const Real* zin = C;
   long zstride = 0, zld = ldc;
   for (int l = (int)t.nin.size() - 1; l >= 0; --l) {
     const int nin = t.nin[l], nodes = (nin + t.g - 1) / t.g;
-    double* zout = ex.ar->get<double>((size_t)nin * p * k);
+    Real* zout = ex.ar->get<Real>((size_t)nin * p * k);
     if (!ex.dry) {
-      smem_attr_once(k_qr_apply_merge);
-      const size_t smem = (size_t)std::min(t.g, nin) * p * k * 8 + (size_t)16 * k * 8;
+      smem_attr_once(k_qr_apply_merge<Real>);
+      const size_t smem = ((size_t)std::min(t.g, nin) * p * k + (size_t)16 * k) * sizeof(Real);
       TT_KERNEL(ex, K_QR_APPLY, (nin - nodes) * 2.0 * p * (double)p * k,
-                8.0 * ((double)nin * p * p + 2.0 * nin * p * k),
-                k_qr_apply_merge<<<nodes, QR_THREADS, smem, ex.s>>>(t.Vm[l], t.vtop[l], t.taum[l], nin, p, t.g, k,
+                (double)sizeof(Real) * ((double)nin * p * p + 2.0 * nin * p * k),
+                k_qr_apply_merge<Real><<<nodes, QR_THREADS, smem, ex.s>>>(t.Vm[l], t.vtop[l], t.taum[l], nin, p, t.g, k,
                                                                     zin, zstride, zld, zout));
     }
     zin = zout;
@@ -604,15 +624,32 @@ void tsqr_apply(Exec& ex, const QRTree& t, const double* C, int k, long ldc, dou
     zld = p;
   }
   if (!ex.dry) {
-    smem_attr_once(k_qr_apply_blocks);
-    const size_t smem = (size_t)t.mb0 * k * 8;
+    smem_attr_once(k_qr_apply_blocks<Real>);
+    const size_t smem = (size_t)t.mb0 * k * sizeof(Real);
     TT_REQUIRE(smem <= QR_SMEM_MAX + 16 * 1024, TT_ERR_ARG);
     TT_KERNEL(ex, K_QR_APPLY, 4.0 * t.m * (double)p * k,
-              8.0 * ((double)t.m * (p + k) + (double)t.nb0 * p * k),
-              k_qr_apply_blocks<<<t.nb0, QR_THREADS, smem, ex.s>>>(t.V0, t.tau0, t.mb0, p, t.m, k, zin, zstride, zld,
+              (double)sizeof(Real) * ((double)t.m * (p + k) + (double)t.nb0 * p * k),
+              k_qr_apply_blocks<Real><<<t.nb0, QR_THREADS, smem, ex.s>>>(t.V0, t.tau0, t.mb0, p, t.m, k, zin, zstride, zld,
                                                                   Out, ldo));
   }
 }
+
+
+// ---- explicit instantiations: FP64 path and the FP32 precision form
+template void gemm<double>(Exec&, int, int, int, double, const double*, long, long, const double*, long, long, double,
+                           double*, long);
+template void gemm<float>(Exec&, int, int, int, float, const float*, long, long, const float*, long, long, float,
+                          float*, long);
+template void form_hadamard_full<double>(Exec&, int, int, const double*, int, const double*, const double*, int,
+                                         const double*, double*, long);
+template void form_hadamard_full<float>(Exec&, int, int, const double*, int, const double*, const double*, int,
+                                        const double*, float*, long);
+template void sumsq<double>(Exec&, const double*, int, int, long, double*);
+template void sumsq<float>(Exec&, const float*, int, int, long, double*);
+template void tsqr<double>(Exec&, const double*, int, int, long, QRTreeT<double>&);
+template void tsqr<float>(Exec&, const float*, int, int, long, QRTreeT<float>&);
+template void tsqr_apply<double>(Exec&, const QRTreeT<double>&, const double*, int, long, double*, long);
+template void tsqr_apply<float>(Exec&, const QRTreeT<float>&, const float*, int, long, float*, long);
 
 // ============================================================== small SVD
 // SVD of a p x p matrix M (p <= 112) in one CTA, all in shared memory:
@@ -665,6 +702,24 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   }
   __syncthreads();
   const double fro2 = s_fro2;
+  if (!isfinite(fro2)) {
+    // NaN/Inf input: flag it and return a rank-1 zero factorisation instead
+    // of letting non-finite norms drive the pivot and sort indices
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+      US[t] = 0.0;
+      Vout[t] = ((t % p) == (t / p)) ? 1.0 : 0.0;
+    }
+    for (int c = threadIdx.x; c < p; c += blockDim.x) sig[c] = 0.0;
+    if (threadIdx.x == 0) {
+      info[0] = 1;
+      info[1] = 0;
+      info[2] = 0;
+      tail_out[0] = 0.0;
+      tail_out[1] = 0.0;
+      atomicOr(status, DEV_NONFINITE);
+    }
+    return;
+  }
   const double thr = defl * defl * fro2;
   // ---- 1. QR with column pivoting of M^T, deflated
   int pd = p;
@@ -853,8 +908,14 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   }
   __syncthreads();
   for (int j = threadIdx.x; j < pd; j += blockDim.x) {
+    // ranking by (value desc, index asc) with non-finite values mapped to -1,
+    // a strict total order, so order[] is always a permutation of 0..pd-1
+    const double vj = isfinite(cn[j]) ? cn[j] : -1.0;
     int rk = 0;
-    for (int l = 0; l < pd; ++l) rk += (cn[l] > cn[j]) || (cn[l] == cn[j] && l < j);
+    for (int l = 0; l < pd; ++l) {
+      const double vl = isfinite(cn[l]) ? cn[l] : -1.0;
+      rk += (vl > vj) || (vl == vj && l < j);
+    }
     order[rk] = j;
   }
   __syncthreads();
@@ -998,7 +1059,15 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
   for (int k = 0; k < r; ++k) {
     ArgMax best{-1.0, 0x7fffffffffffffffL};
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-      if (freeflag[i]) best = amax_better(best, ArgMax{fabs(W[i + (size_t)k * n]), (long)i});
+      if (freeflag[i]) {
+        // a NaN entry counts as 0 (and is flagged), so a free row is always chosen
+        double v = fabs(W[i + (size_t)k * n]);
+        if (!(v >= 0.0)) {
+          v = 0.0;
+          atomicOr(status, DEV_NONFINITE);
+        }
+        best = amax_better(best, ArgMax{v, (long)i});
+      }
     best = block_argmax(best, rv, ri);
     const int pr = (int)best.idx;
     if (threadIdx.x == 0) {

@@ -3,7 +3,11 @@
 // TT sums by core concatenation, Khatri-Rao Hadamard cores, and TT rounding
 // (Sec. 3.2) by three exact routes chosen from the shape.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <algorithm>
+
+#include <vector>
 
 #include "tt_ops.cuh"
 
@@ -46,9 +50,25 @@ cudaEvent_t prof_begin(Exec& ex) {
   return a;
 }
 
-void prof_end(Exec& ex, cudaEvent_t a, int cls, double flops, double bytes) {
-  TT_CUDA(cudaGetLastError());
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+// TT_DEBUG_SYNC=1 in the environment: wait for every kernel and report the
+// first one that fails (its launch expression and index) on stderr.
+bool debug_sync() {
+  static const bool on = [] {
+    const char* v = std::getenv("TT_DEBUG_SYNC");
+    return v && v[0] && v[0] != '0';
+  }();
+  return on;
+}
+
+void prof_end(Exec& ex, cudaEvent_t a, int cls, double flops, double bytes, const char* what) {
+  const unsigned long long idx = g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && debug_sync()) e = cudaStreamSynchronize(ex.s);
+  if (e != cudaSuccess) {
+    if (debug_sync())
+      std::fprintf(stderr, "tt_fv: launch %llu (class %d) failed: %s\n  %s\n", idx, cls, cudaGetErrorString(e), what);
+    throw Error{TT_ERR_CUDA};
+  }
   ex.flops += flops;
   ex.bytes += bytes;
   if (!a) return;
@@ -79,6 +99,26 @@ void prof_flush(Exec& ex) {
     pf.pool.push_back(r.b);
   }
   pf.pending.clear();
+}
+
+template <typename T>
+static void debug_finite_t(Exec& ex, const T* d, long n, const char* what, int a, int b, int c) {
+  if (!debug_sync() || ex.dry || n <= 0) return;
+  std::vector<T> h((size_t)n);
+  TT_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost, ex.s));
+  TT_CUDA(cudaStreamSynchronize(ex.s));
+  for (long i = 0; i < n; ++i)
+    if (!std::isfinite((double)h[i])) {
+      std::fprintf(stderr, "tt_fv: non-finite %s (%d, %d, %d) at entry %ld of %ld: %g\n", what, a, b, c, i, n,
+                   (double)h[i]);
+      throw Error{TT_ERR_NONFINITE};
+    }
+}
+void debug_finite(Exec& ex, const double* d, long n, const char* what, int a, int b, int c) {
+  debug_finite_t(ex, d, n, what, a, b, c);
+}
+void debug_finite(Exec& ex, const float* d, long n, const char* what, int a, int b, int c) {
+  debug_finite_t(ex, d, n, what, a, b, c);
 }
 
 // ============================================================== core stencils
@@ -148,18 +188,15 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
-__global__ void k_rademacher(double* __restrict__ O, long n, unsigned long long seed) {
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
-    O[t] = (splitmix64(seed * 0x100000000ull + (unsigned long long)t) >> 63) ? 1.0 : -1.0;
-}
 
 // ============================================================== transposes
-__global__ void k_transpose(const double* __restrict__ X, int m, int n, long ldx, double* __restrict__ Y, long ldy) {
-  __shared__ double tile[32][33];
+template <typename Real>
+__global__ void k_transpose(const Real* __restrict__ X, int m, int n, long ldx, Real* __restrict__ Y, long ldy) {
+  __shared__ Real tile[32][33];
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
   for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
     const int i = i0 + threadIdx.x, j = j0 + dy;
-    tile[dy][threadIdx.x] = (i < m && j < n) ? X[i + (size_t)j * ldx] : 0.0;
+    tile[dy][threadIdx.x] = (i < m && j < n) ? X[i + (size_t)j * ldx] : Real(0);
   }
   __syncthreads();
   for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
@@ -168,11 +205,15 @@ __global__ void k_transpose(const double* __restrict__ X, int m, int n, long ldx
   }
 }
 // Y (n x m) = X^T for X (m x n)
-void transpose(Exec& ex, const double* X, int m, int n, long ldx, double* Y, long ldy) {
+template <typename Real>
+void transpose(Exec& ex, const Real* X, int m, int n, long ldx, Real* Y, long ldy) {
   if (ex.dry) return;
   dim3 grid(ceil_div(m, 32), ceil_div(n, 32));
-  TT_KERNEL(ex, K_OTHER, 0, 16.0 * m * (double)n, k_transpose<<<grid, dim3(32, 8), 0, ex.s>>>(X, m, n, ldx, Y, ldy));
+  TT_KERNEL(ex, K_OTHER, 0, 2.0 * sizeof(Real) * m * (double)n,
+            k_transpose<Real><<<grid, dim3(32, 8), 0, ex.s>>>(X, m, n, ldx, Y, ldy));
 }
+template void transpose<double>(Exec&, const double*, int, int, long, double*, long);
+template void transpose<float>(Exec&, const float*, int, int, long, float*, long);
 
 // ============================================================== sync helpers
 int fetch_int(Exec& ex, const int* d) {
@@ -229,11 +270,107 @@ int total_rank(const std::vector<Term>& terms) {
   return r;
 }
 
+// ============================================================== precision helpers
+// The FP32 precision form runs the dense rounding contractions (formation,
+// range-finder products, TSQR and its applications) on FP32 working copies;
+// the small SVD and the output cores stay FP64.
+template <typename D, typename S>
+__global__ void k_convert(D* __restrict__ dst, const S* __restrict__ src, long n) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    dst[t] = D(src[t]);
+}
+template <typename D, typename S>
+static void convert(Exec& ex, D* dst, const S* src, long n) {
+  if (n <= 0 || ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, 0, (double)(sizeof(D) + sizeof(S)) * n,
+            (k_convert<D, S><<<grid_for(n), 256, 0, ex.s>>>(dst, src, n)));
+}
+// X (n values, FP64) as a Real array: X itself for double, else a converted copy
+template <typename Real>
+static const Real* as_real(Exec& ex, const double* X, long n) {
+  if constexpr (std::is_same<Real, double>::value) {
+    return X;
+  } else {
+    Real* y = ex.ar->get<Real>((size_t)n);
+    convert(ex, y, X, n);
+    return y;
+  }
+}
+template <typename Real>
+static const double* as_double(Exec& ex, const Real* X, long n) {
+  if constexpr (std::is_same<Real, double>::value) {
+    return X;
+  } else {
+    double* y = ex.ar->get<double>((size_t)n);
+    convert(ex, y, X, n);
+    return y;
+  }
+}
+// Q [C; 0] into the FP64 core Out (m x k, ld m)
+template <typename Real>
+static void apply_to_core(Exec& ex, const QRTreeT<Real>& t, const double* C, int k, long ldc, double* Out) {
+  if constexpr (std::is_same<Real, double>::value) {
+    tsqr_apply(ex, t, C, k, ldc, Out, (long)t.m);
+  } else {
+    Scope sc(*ex.ar);
+    const Real* Cr = as_real<Real>(ex, C, ldc * k);
+    Real* O = ex.ar->get<Real>((size_t)t.m * k);
+    tsqr_apply(ex, t, Cr, k, ldc, O, (long)t.m);
+    convert(ex, Out, O, (long)t.m * k);
+  }
+}
+
+// Working-precision product C = alpha A B + beta C of the rounding routes:
+// FP64 and FP32 on CUDA cores; under TT_TF32 / TT_BF16 the larger FP32
+// products go to the tensor cores (split operands, FP32-accurate).
+template <typename Real>
+static void lp_gemm(Exec& ex, int M, int N, int K, Real alpha, const Real* A, long ars, long acs, const Real* B,
+                    long brs, long bcs, Real beta, Real* C, long ldc) {
+  if constexpr (std::is_same<Real, float>::value) {
+    if ((ex.precision == TT_TF32 || ex.precision == TT_BF16) && M >= 128 && K >= 32 &&
+        (double)M * N * K >= 4.0e6) {
+      tc_gemm<float>(ex, ex.precision, true, M, N, K, alpha, A, ars, acs, B, brs, bcs, beta, C, ldc);
+      return;
+    }
+  }
+  gemm<Real>(ex, M, N, K, alpha, A, ars, acs, B, brs, bcs, beta, C, ldc);
+}
+
+template <typename Real>
+__global__ void k_rademacher(Real* __restrict__ O, long n, unsigned long long seed) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    O[t] = (splitmix64(seed * 0x100000000ull + (unsigned long long)t) >> 63) ? Real(1) : Real(-1);
+}
+template <typename Real>
+__global__ void k_set_identity(Real* I, int p) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p * p; t += gridDim.x * blockDim.x)
+    I[t] = ((t % p) == (t / p)) ? Real(1) : Real(0);
+}
+template <typename Real>
+static void set_identity_t(Exec& ex, Real* I, int p) {
+  if (ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, 0, (double)sizeof(Real) * p * p,
+            k_set_identity<Real><<<grid_for((long)p * p), 256, 0, ex.s>>>(I, p));
+}
+void set_identity(Exec& ex, double* I, int p) { set_identity_t<double>(ex, I, p); }
+
 // ============================================================== rounding
 // residual target of the range finder: 1e-3 of the truncation tolerance, never
 // looser than 1e-11 (so the result stays within 1e-10 of the exact truncated
 // SVD) nor tighter than FP64 round-off of the residual itself
 static double qb_target(double tol) { return std::max(std::min(1e-3 * tol, 1e-11), 4e-15); }
+// FP32 working precision: the residual W0 - Q Q^T W0 formed in FP32 carries
+// round-off of a few units of 2^-24 relative to ||W0||, so the range finder
+// certifies at 4e-7, and truncation below 1e-6 would keep round-off directions
+constexpr double kFp32QbFloor = 4e-7;
+constexpr double kFp32TolFloor = 1e-6;
+template <typename Real>
+static double qb_target_t(double tol) {
+  return std::is_same<Real, double>::value ? qb_target(tol) : std::max(qb_target(tol), kFp32QbFloor);
+}
+double effective_tol(const Exec& ex, double tol) {
+  return ex.precision == TT_FP64 ? tol : std::max(tol, kFp32TolFloor);
+}
 
 static void finish_counts(Exec& ex, int k, int cap, int rin) {
   ex.rounds++;
@@ -242,15 +379,20 @@ static void finish_counts(Exec& ex, int k, int cap, int rin) {
 
 // (i) Factored route, R <= 112 and R <= min(n1, n2): QR of both cores
 // (TSQR), SVD of the R x R product of the triangular factors.
+template <typename Real>
 static RoundInfo round_factored(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol,
                                 int cap, TT& Y) {
   Scope sc(*ex.ar);
-  QRTree ta, tb;
-  tsqr(ex, A, n1, R, n1, ta);
-  tsqr(ex, B, n2, R, n2, tb);
-  double* M = ex.ar->get<double>((size_t)R * R);
+  const Real* Ar = as_real<Real>(ex, A, (long)n1 * R);
+  const Real* Br = as_real<Real>(ex, B, (long)n2 * R);
+  QRTreeT<Real> ta, tb;
+  tsqr(ex, Ar, n1, R, n1, ta);
+  tsqr(ex, Br, n2, R, n2, tb);
+  Real* Mr = ex.ar->get<Real>((size_t)R * R);
   // M = R_A R_B^T
-  gemm(ex, R, R, R, 1.0, ta.R, 1, R, tb.R, R, 1, 0.0, M, R);
+  gemm<Real>(ex, R, R, R, Real(1), ta.R, 1, R, tb.R, R, 1, Real(0), Mr, R);
+  const double* M = as_double(ex, Mr, (long)R * R);
+  debug_finite(ex, M, (long)R * R, "factored-route core M (n1, n2, R)", n1, n2, R);
   double* US = ex.ar->get<double>((size_t)R * R);
   double* V = ex.ar->get<double>((size_t)R * R);
   double* sig = ex.ar->get<double>(R);
@@ -261,8 +403,8 @@ static RoundInfo round_factored(Exec& ex, const double* A, const double* B, int 
   if (ex.dry) k = std::min(cap, R);
   double tl[2];
   fetch_doubles(ex, tail, 2, tl);
-  tsqr_apply(ex, ta, US, k, R, Y.a, Y.n1);
-  tsqr_apply(ex, tb, V, k, R, Y.b, Y.n2);
+  apply_to_core(ex, ta, US, k, R, Y.a);
+  apply_to_core(ex, tb, V, k, R, Y.b);
   Y.r = k;
   finish_counts(ex, k, cap, R);
   return RoundInfo{k, tl[0], tl[1], 0.0};
@@ -274,7 +416,8 @@ static RoundInfo round_factored(Exec& ex, const double* A, const double* B, int 
 //   s  > 112: randomized range finder with an explicit residual check
 //             ||W0 - Q Q^T W0||_F <= tau ||W0||_F, tau = qb_target(tol),
 //             then QR of (Q^T W0)^T and SVD of the p x p factor (p <= 112).
-RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int cap, TT& Y) {
+template <typename Real>
+static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double tol, int cap, TT& Y) {
   Scope sc(*ex.ar);
   const bool tr = n1 > n2;
   const int s = tr ? n2 : n1, l = tr ? n1 : n2;
@@ -287,15 +430,17 @@ RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int
   double* tail = ex.ar->get<double>(2);
   if (s <= 112) {
     // W0^T (l x s) explicitly, col-major
-    double* WT = ex.ar->get<double>((size_t)l * s);
+    Real* WT = ex.ar->get<Real>((size_t)l * s);
     if (tr)
-      scaled_copy(ex, WT, Yf, (long)l * s, 1.0);  // Y itself is n1 x n2 = l x s
+      convert(ex, WT, Yf, (long)l * s);  // Y itself is n1 x n2 = l x s
     else
       transpose(ex, Yf, n1, n2, n1, WT, l);
-    QRTree tw;
+    QRTreeT<Real> tw;
     tsqr(ex, WT, l, s, l, tw);
-    double* M = ex.ar->get<double>((size_t)s * s);
-    transpose(ex, tw.R, s, s, s, M, s);  // M = R^T
+    Real* Mr = ex.ar->get<Real>((size_t)s * s);
+    transpose(ex, tw.R, s, s, s, Mr, s);  // M = R^T
+    const double* M = as_double(ex, Mr, (long)s * s);
+    debug_finite(ex, M, (long)s * s, "direct-route core M (n1, n2, s)", n1, n2, s);
     double* US = ex.ar->get<double>((size_t)s * s);
     double* V = ex.ar->get<double>((size_t)s * s);
     double* sig = ex.ar->get<double>(s);
@@ -306,45 +451,45 @@ RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int
     fetch_doubles(ex, tail, 2, tl);
     // W0 = R^T Q_W^T = U S V^T Q_W^T: s-side core U S, l-side core Q_W V
     scaled_copy(ex, Aw, US, (long)s * k, 1.0);
-    tsqr_apply(ex, tw, V, k, s, Bw, l);
+    apply_to_core(ex, tw, V, k, s, Bw);
     Y.r = k;
     finish_counts(ex, k, cap, s);
     return RoundInfo{k, tl[0], tl[1], 0.0};
   }
   // ---- randomized range finder (s > 112)
-  const double tau = qb_target(tol);
+  const double tau = qb_target_t<Real>(tol);
   sumsq(ex, Yf, n1, n2, n1, kbuf);
   double nrm2[1];
   fetch_doubles(ex, kbuf, 1, nrm2);
   int p = std::min({112, s, ((std::max(2 * cap, cap + 16) + 7) / 8) * 8});
-  double* Om = ex.ar->get<double>((size_t)l * 112);
-  double* S = ex.ar->get<double>((size_t)s * 112);
-  double* Q = ex.ar->get<double>((size_t)s * 112);
-  double* WT = ex.ar->get<double>((size_t)l * 112);
-  double* E = ex.ar->get<double>((size_t)s * l);
-  double* I = ex.ar->get<double>((size_t)112 * 112);
+  Real* Om = ex.ar->get<Real>((size_t)l * 112);
+  Real* S = ex.ar->get<Real>((size_t)s * 112);
+  Real* Q = ex.ar->get<Real>((size_t)s * 112);
+  Real* WT = ex.ar->get<Real>((size_t)l * 112);
+  Real* E = ex.ar->get<Real>((size_t)s * l);
+  Real* I = ex.ar->get<Real>((size_t)112 * 112);
   double resid2 = 0.0;
   for (int attempt = 0;; ++attempt) {
     ex.qb_attempts++;
     const size_t mk = ex.ar->mark();
     if (!ex.dry)
-      TT_KERNEL(ex, K_OTHER, 0, 8.0 * l * p,
-                k_rademacher<<<grid_for((long)l * p), 256, 0, ex.s>>>(Om, (long)l * p, 0x7A3Dull + attempt));
+      TT_KERNEL(ex, K_OTHER, 0, (double)sizeof(Real) * l * p,
+                k_rademacher<Real><<<grid_for((long)l * p), 256, 0, ex.s>>>(Om, (long)l * p, 0x7A3Dull + attempt));
     // S = W0 Om (s x p)
-    gemm(ex, s, p, l, 1.0, Yf, wrs, wcs, Om, 1, l, 0.0, S, s);
-    QRTree ts;
+    lp_gemm<Real>(ex, s, p, l, Real(1), Yf, wrs, wcs, Om, 1, l, Real(0), S, s);
+    QRTreeT<Real> ts;
     tsqr(ex, S, s, p, s, ts);
     // Q = Q_S [I_p; 0]
-    set_identity(ex, I, p);
+    set_identity_t(ex, I, p);
     tsqr_apply(ex, ts, I, p, p, Q, s);
     // WT = W0^T Q (l x p)
-    gemm(ex, l, p, s, 1.0, Yf, wcs, wrs, Q, 1, s, 0.0, WT, l);
+    lp_gemm<Real>(ex, l, p, s, Real(1), Yf, wcs, wrs, Q, 1, s, Real(0), WT, l);
     // E = W0 - Q WT^T
     if (tr)
       transpose(ex, Yf, n1, n2, n1, E, s);
     else
-      scaled_copy(ex, E, Yf, (long)s * l, 1.0);
-    gemm(ex, s, l, p, -1.0, Q, 1, s, WT, l, 1, 1.0, E, s);
+      convert(ex, E, Yf, (long)s * l);
+    lp_gemm<Real>(ex, s, l, p, Real(-1), Q, 1, s, WT, l, 1, Real(1), E, s);
     sumsq(ex, E, s, l, s, kbuf + 1);
     double r2[1];
     fetch_doubles(ex, kbuf + 1, 1, r2);
@@ -360,10 +505,12 @@ RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int
     p = std::min({112, s, 2 * p});
   }
   // SVD of Q^T W0 = WT^T = (Q_W R_W)^T = R_W^T Q_W^T
-  QRTree tw;
+  QRTreeT<Real> tw;
   tsqr(ex, WT, l, p, l, tw);
-  double* M = ex.ar->get<double>((size_t)p * p);
-  transpose(ex, tw.R, p, p, p, M, p);
+  Real* Mr = ex.ar->get<Real>((size_t)p * p);
+  transpose(ex, tw.R, p, p, p, Mr, p);
+  const double* M = as_double(ex, Mr, (long)p * p);
+  debug_finite(ex, M, (long)p * p, "range-finder core M (n1, n2, p)", n1, n2, p);
   double* US = ex.ar->get<double>((size_t)p * p);
   double* V = ex.ar->get<double>((size_t)p * p);
   double* sig = ex.ar->get<double>(p);
@@ -373,21 +520,53 @@ RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int
   double tl[2];
   fetch_doubles(ex, tail, 2, tl);
   // s-side core Q (U S)_k, l-side core Q_W V_k
-  gemm(ex, s, k, p, 1.0, Q, 1, s, US, 1, p, 0.0, Aw, s);
-  tsqr_apply(ex, tw, V, k, p, Bw, l);
+  if constexpr (std::is_same<Real, double>::value) {
+    gemm(ex, s, k, p, 1.0, Q, 1, s, US, 1, p, 0.0, Aw, s);
+  } else {
+    const Real* USr = as_real<Real>(ex, US, (long)p * k);
+    Real* Ar = ex.ar->get<Real>((size_t)s * k);
+    lp_gemm<Real>(ex, s, k, p, Real(1), Q, 1, s, USr, 1, p, Real(0), Ar, s);
+    convert(ex, Aw, Ar, (long)s * k);
+  }
+  apply_to_core(ex, tw, V, k, p, Bw);
   Y.r = k;
   finish_counts(ex, k, cap, s);
   return RoundInfo{k, std::sqrt(tl[0] * tl[0] + resid2), tl[1], std::sqrt(resid2)};
 }
 
+RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int cap, TT& Y) {
+  tol = effective_tol(ex, tol);
+  if (ex.precision == TT_FP64) return round_full_t<double>(ex, Yf, n1, n2, tol, cap, Y);
+  Scope sc(*ex.ar);
+  return round_full_t<float>(ex, as_real<float>(ex, Yf, (long)n1 * n2), n1, n2, tol, cap, Y);
+}
+
+template <typename Real>
+static RoundInfo round_cores_t(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol,
+                               int cap, TT& Y) {
+  if (R <= 112 && R <= std::min(n1, n2)) return round_factored<Real>(ex, A, B, n1, n2, R, tol, cap, Y);
+  Scope sc(*ex.ar);
+  Real* Yf = ex.ar->get<Real>((size_t)n1 * n2);
+  if constexpr (std::is_same<Real, float>::value) {
+    if (ex.precision == TT_TF32 || ex.precision == TT_BF16) {
+      tc_gemm<double>(ex, ex.precision, true, n1, n2, R, 1.0f, A, 1, n1, B, n2, 1, 0.0f, Yf, n1);
+      return round_full_t<Real>(ex, Yf, n1, n2, tol, cap, Y);
+    }
+  }
+  const Real* Ar = as_real<Real>(ex, A, (long)n1 * R);
+  const Real* Br = as_real<Real>(ex, B, (long)n2 * R);
+  gemm<Real>(ex, n1, n2, R, Real(1), Ar, 1, n1, Br, n2, 1, Real(0), Yf, n1);
+  return round_full_t<Real>(ex, Yf, n1, n2, tol, cap, Y);
+}
+
 RoundInfo round_cores(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol, int cap,
                       TT& Y) {
   TT_REQUIRE(R >= 1 && cap >= 1 && Y.cap >= std::min(cap, std::max(1, std::min(n1, n2))), TT_ERR_ARG);
-  if (R <= 112 && R <= std::min(n1, n2)) return round_factored(ex, A, B, n1, n2, R, tol, cap, Y);
-  Scope sc(*ex.ar);
-  double* Yf = ex.ar->get<double>((size_t)n1 * n2);
-  gemm(ex, n1, n2, R, 1.0, A, 1, n1, B, n2, 1, 0.0, Yf, n1);
-  return round_full(ex, Yf, n1, n2, tol, cap, Y);
+  debug_finite(ex, A, (long)n1 * R, "round_cores A (n1, n2, R)", n1, n2, R);
+  debug_finite(ex, B, (long)n2 * R, "round_cores B (n1, n2, R)", n1, n2, R);
+  tol = effective_tol(ex, tol);
+  if (ex.precision == TT_FP64) return round_cores_t<double>(ex, A, B, n1, n2, R, tol, cap, Y);
+  return round_cores_t<float>(ex, A, B, n1, n2, R, tol, cap, Y);
 }
 
 RoundInfo round_tt(Exec& ex, const TT& X, double tol, int cap, TT& Y) {
@@ -411,6 +590,10 @@ RoundInfo round_sum(Exec& ex, const std::vector<Term>& terms, double tol, int ca
 
 RoundInfo round_hadamard(Exec& ex, const TT& X, const TT& Z, double tol, int cap, TT& Y) {
   TT_REQUIRE(X.n1 == Z.n1 && X.n2 == Z.n2, TT_ERR_ARG);
+  debug_finite(ex, X.a, (long)X.n1 * X.r, "round_hadamard X.a (n1, n2, r)", X.n1, X.n2, X.r);
+  debug_finite(ex, X.b, (long)X.n2 * X.r, "round_hadamard X.b (n1, n2, r)", X.n1, X.n2, X.r);
+  debug_finite(ex, Z.a, (long)Z.n1 * Z.r, "round_hadamard Z.a (n1, n2, r)", Z.n1, Z.n2, Z.r);
+  debug_finite(ex, Z.b, (long)Z.n2 * Z.r, "round_hadamard Z.b (n1, n2, r)", Z.n1, Z.n2, Z.r);
   Scope sc(*ex.ar);
   const int n1 = X.n1, n2 = X.n2, R = X.r * Z.r;
   if (R <= 112 && R <= std::min(n1, n2)) {
@@ -420,21 +603,18 @@ RoundInfo round_hadamard(Exec& ex, const TT& X, const TT& Z, double tol, int cap
     khatri_rao(ex, X.b, X.r, Z.b, Z.r, n2, B);
     return round_cores(ex, A, B, n1, n2, R, tol, cap, Y);
   }
-  double* Yf = ex.ar->get<double>((size_t)n1 * n2);
+  tol = effective_tol(ex, tol);
+  if (ex.precision == TT_FP64) {
+    double* Yf = ex.ar->get<double>((size_t)n1 * n2);
+    form_hadamard_full(ex, n1, n2, X.a, X.r, X.b, Z.a, Z.r, Z.b, Yf, n1);
+    return round_full_t<double>(ex, Yf, n1, n2, tol, cap, Y);
+  }
+  float* Yf = ex.ar->get<float>((size_t)n1 * n2);
   form_hadamard_full(ex, n1, n2, X.a, X.r, X.b, Z.a, Z.r, Z.b, Yf, n1);
-  return round_full(ex, Yf, n1, n2, tol, cap, Y);
+  return round_full_t<float>(ex, Yf, n1, n2, tol, cap, Y);
 }
 
 // ============================================================== misc
-__global__ void k_set_identity(double* I, int p) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p * p; t += gridDim.x * blockDim.x)
-    I[t] = ((t % p) == (t / p)) ? 1.0 : 0.0;
-}
-void set_identity(Exec& ex, double* I, int p) {
-  if (ex.dry) return;
-  TT_KERNEL(ex, K_OTHER, 0, 8.0 * p * p, k_set_identity<<<grid_for((long)p * p), 256, 0, ex.s>>>(I, p));
-}
-
 // sum_{i,j} X = (1^T A)(B^T 1) and ||X||_F^2 = sum (A^T A) o (B^T B): one CTA.
 __global__ void k_tt_sum_norm(const double* __restrict__ A, const double* __restrict__ B, int n1, int n2, int r,
                               double* out) {

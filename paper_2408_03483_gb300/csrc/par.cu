@@ -9,6 +9,19 @@
 
 namespace ttfv {
 
+int sm_count() {
+  static std::once_flag once;
+  static int n = 152;
+  std::call_once(once, [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+  });
+  return n;
+}
+
+
 int smem_optin_max() {
   static int v = 0;
   static std::once_flag once;
@@ -63,6 +76,8 @@ StreamPool::~StreamPool() {
 
 static void merge_counters(Exec& dst, const Exec& src) {
   dst.rounds += src.rounds;
+  dst.learned_calls += src.learned_calls;
+  dst.learned_accepted += src.learned_accepted;
   dst.qb_attempts += src.qb_attempts;
   dst.qb_uncertified += src.qb_uncertified;
   dst.syncs += src.syncs;
@@ -107,6 +122,7 @@ void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>&
       c.ex.rounds = c.ex.qb_attempts = c.ex.qb_uncertified = c.ex.syncs = 0;
       c.ex.jacobi_sweeps = c.ex.cross_calls = c.ex.cross_sweeps = c.ex.taylor_iters = c.ex.cap_hits = 0;
       c.ex.svd_calls = c.ex.svd_p = c.ex.svd_pd = c.ex.svd_sweeps = 0;
+      c.ex.learned_calls = c.ex.learned_accepted = 0;
       c.ex.flops = c.ex.bytes = 0.0;
       body(c.ex, i);
       merge_counters(ex, c.ex);
@@ -131,6 +147,9 @@ void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>&
     c.ex.s = ex.pool->stream((size_t)i);
     c.ex.ar = &c.ar;
     c.ex.dev_status = ex.dev_status;
+    c.ex.precision = ex.precision;
+    c.ex.pivot_net = ex.pivot_net;
+    c.ex.pivot_rec = ex.pivot_rec;
     c.ex.h_pinned = c.hi;
     c.ex.h_pinned_d = c.hd;
     c.prof.on = ex.prof && ex.prof->on;

@@ -36,6 +36,8 @@ enum : unsigned {
   DEV_JACOBI_NOCONV = 1u,
   DEV_MAXVOL_NOCONV = 2u,
   DEV_SHAPE = 4u,
+  DEV_TC_TIMEOUT = 8u,  // a tensor-core kernel gave up waiting on an mbarrier
+  DEV_NONFINITE = 16u,  // a small SVD received a NaN/Inf matrix (result zeroed)
 };
 
 // ---------------------------------------------------------------- workspace
@@ -111,6 +113,12 @@ struct StreamPool {
   ~StreamPool();
 };
 
+// Device parameters of the learned-pivot network (FP32 masters; mlp.cu)
+struct MlpNet {
+  float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *w3 = nullptr, *b3 = nullptr;
+};
+struct PivotRecorder;  // training-data capture of the crosses (fv.cu)
+
 // Execution context of one call chain.
 struct Exec {
   cudaStream_t s = nullptr;
@@ -119,11 +127,15 @@ struct Exec {
   int* h_pinned = nullptr;          // small pinned host buffer for syncs
   double* h_pinned_d = nullptr;
   bool dry = false;                 // workspace sizing pass: no launches
+  int precision = TT_FP64;          // tt_precision of the rounding contractions
+  const MlpNet* pivot_net = nullptr;  // learned initial cross pivots (null: maxvol start)
+  PivotRecorder* pivot_rec = nullptr; // capture (features, converged pivots) of each cross
   // counters (host)
   long long rounds = 0, qb_attempts = 0, qb_uncertified = 0, syncs = 0;
   long long jacobi_sweeps = 0, cross_calls = 0, cross_sweeps = 0;
   long long taylor_iters = 0, cap_hits = 0;
   long long svd_calls = 0, svd_p = 0, svd_pd = 0, svd_sweeps = 0;
+  long long learned_calls = 0, learned_accepted = 0;
   double flops = 0.0, bytes = 0.0;
   Prof* prof = nullptr;             // per-class event timing when prof->on
   StreamPool* pool = nullptr;       // streams for parallel_tasks (null: run tasks in order)
@@ -138,13 +150,13 @@ void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>&
 // Bracket one kernel launch: counts it, checks the launch, adds its
 // algorithmic flops/bytes to the totals and, when profiling, times it.
 cudaEvent_t prof_begin(Exec& ex);
-void prof_end(Exec& ex, cudaEvent_t a, int cls, double flops, double bytes);
+void prof_end(Exec& ex, cudaEvent_t a, int cls, double flops, double bytes, const char* what);
 void prof_flush(Exec& ex);  // after a stream sync: accumulate finished records
 #define TT_KERNEL(ex, cls, flops, bytes, ...)                     \
   do {                                                            \
     cudaEvent_t _tt_a = ::ttfv::prof_begin(ex);                   \
     __VA_ARGS__;                                                  \
-    ::ttfv::prof_end(ex, _tt_a, cls, (double)(flops), (double)(bytes)); \
+    ::ttfv::prof_end(ex, _tt_a, cls, (double)(flops), (double)(bytes), #__VA_ARGS__); \
   } while (0)
 
 // ---------------------------------------------------------------- helpers
@@ -152,6 +164,8 @@ void prof_flush(Exec& ex);  // after a stream sync: accumulate finished records
 // once per kernel and process (the attribute is global to the function, so it
 // must not be changed per launch while other host threads launch it).
 int smem_optin_max();
+// multiprocessors of the current device (read once per process)
+int sm_count();
 cudaError_t smem_attr_once_impl(const void* fn);
 template <typename K>
 inline void smem_attr_once(K kernel) {
@@ -166,33 +180,51 @@ int fetch_int(Exec& ex, const int* d);
 int fetch_svd_info(Exec& ex, const int* d, int p);
 void fetch_doubles(Exec& ex, const double* d, int n, double* out);
 
+// TT_DEBUG_SYNC=1: every launch is waited for, and debug_finite() copies an
+// array to the host and throws TT_ERR_NONFINITE (printing `what`) if it holds
+// a NaN or Inf.  Both are no-ops otherwise.
+bool debug_sync();
+void debug_finite(Exec& ex, const double* d, long n, const char* what, int a = 0, int b = 0, int c = 0);
+void debug_finite(Exec& ex, const float* d, long n, const char* what, int a = 0, int b = 0, int c = 0);
+
 // ---------------------------------------------------------------- kernels (la.cu)
+// The dense kernels are templates on the working precision Real (double for
+// the FP64 path, float for the FP32 precision form); la.cu instantiates both.
+//
 // C[i,j] = alpha * sum_k A(i,k) B(k,j) + beta * C[i,j]; A(i,k) = A[i*ars + k*acs] etc.
-void gemm(Exec& ex, int M, int N, int K, double alpha, const double* A, long ars, long acs,
-          const double* B, long brs, long bcs, double beta, double* C, long ldc);
-// Y[i,j] = (sum_k A1[i,k]B1[j,k]) * (sum_l A2[i,l]B2[j,l]); cores column-major.
-void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, const double* B1,
-                        const double* A2, int r2, const double* B2, double* Y, long ldy);
-// sum of squares of an m x n column-major matrix -> device double
-void sumsq(Exec& ex, const double* X, int m, int n, long ld, double* out);
+template <typename Real>
+void gemm(Exec& ex, int M, int N, int K, Real alpha, const Real* A, long ars, long acs, const Real* B, long brs,
+          long bcs, Real beta, Real* C, long ldc);
+// Y[i,j] = (sum_k A1[i,k]B1[j,k]) * (sum_l A2[i,l]B2[j,l]); FP64 cores
+// (column-major), each product accumulated in Real.
+template <typename Real>
+void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, const double* B1, const double* A2,
+                        int r2, const double* B2, Real* Y, long ldy);
+// sum of squares of an m x n column-major matrix, accumulated in FP64 -> device double
+template <typename Real>
+void sumsq(Exec& ex, const Real* X, int m, int n, long ld, double* out);
 
 // Householder TSQR of a tall m x p matrix (p <= 112): row blocks of mb0
 // rows factored independently, then a g-ary tree of merges of stacked
 // triangular factors (g as many as fit in shared memory); Q is kept implicit.
-struct QRTree {
+template <typename Real>
+struct QRTreeT {
   int m = 0, p = 0, mb0 = 0, nb0 = 0;
-  double* V0 = nullptr;        // leaf reflectors: nb0 blocks of mb0 x p (unit diagonal implicit)
-  double* tau0 = nullptr;      // nb0 x p
-  int g = 2;                   // fan-in of a merge node
-  std::vector<int> nin;        // inputs of each merge level (bottom-up)
-  std::vector<double*> Vm;     // per merge level: nodes x g x (p x p) bottom-block reflectors
-  std::vector<double*> vtop;   // per merge level: nodes x p top entries (alpha - beta)
-  std::vector<double*> taum;   // per merge level: nodes x p
-  double* R = nullptr;         // final p x p upper triangle (ld p)
+  Real* V0 = nullptr;        // leaf reflectors: nb0 blocks of mb0 x p (unit diagonal implicit)
+  Real* tau0 = nullptr;      // nb0 x p
+  int g = 2;                 // fan-in of a merge node
+  std::vector<int> nin;      // inputs of each merge level (bottom-up)
+  std::vector<Real*> Vm;     // per merge level: nodes x g x (p x p) bottom-block reflectors
+  std::vector<Real*> vtop;   // per merge level: nodes x p top entries (alpha - beta)
+  std::vector<Real*> taum;   // per merge level: nodes x p
+  Real* R = nullptr;         // final p x p upper triangle (ld p)
 };
-void tsqr(Exec& ex, const double* X, int m, int p, long ldx, QRTree& t);
+using QRTree = QRTreeT<double>;
+template <typename Real>
+void tsqr(Exec& ex, const Real* X, int m, int p, long ldx, QRTreeT<Real>& t);
 // Out (m x k, ld ldo) = Q [C; 0] with C p x k (ld ldc).
-void tsqr_apply(Exec& ex, const QRTree& t, const double* C, int k, long ldc, double* Out, long ldo);
+template <typename Real>
+void tsqr_apply(Exec& ex, const QRTreeT<Real>& t, const Real* C, int k, long ldc, Real* Out, long ldo);
 
 // One-sided Jacobi SVD of a square p x p matrix M (ld p, p <= 112).  Writes
 // the singular values sorted descending to sig (device, p), U*S (p x p, ld p)
@@ -204,6 +236,15 @@ void jacobi_svd(Exec& ex, const double* M, int p, double tol, int cap, double* U
 // Maximum-volume rows of U (n x r, ld n): LU-pivoted start then swaps until
 // max|B| <= 1 + delta (ties to the smallest row-major index).  I (device, r).
 void maxvol(Exec& ex, const double* U, int n, int r, double delta, int max_iter, int* I);
+
+// Tensor-core contraction (tc_gemm.cu): C (M x N, FP32, ld ldc) = alpha A B +
+// beta C with A(i,k) = A[i*ars + k*acs], B(k,j) = B[k*brs + j*bcs], on
+// tcgen05 in precision TT_TF32 or TT_BF16; with split, the operands are
+// decomposed into tensor-core parts whose products reach FP32 accuracy.
+int tc_parts(int precision, bool split);
+template <typename Src>
+void tc_gemm(Exec& ex, int precision, bool split, int M, int N, int K, float alpha, const Src* A, long ars,
+             long acs, const Src* B, long brs, long bcs, float beta, float* C, long ldc);
 
 // Elementwise helpers (ops.cu)
 void scaled_copy(Exec& ex, double* dst, const double* src, long n, double alpha);

@@ -37,13 +37,17 @@ struct RoundInfo {
 
 void stencil(Exec& ex, const StencilSet& st, const double* in, long ldin, int n, int r);
 void khatri_rao(Exec& ex, const double* X, int r1, const double* Y, int r2, int n, double* Z);
-void transpose(Exec& ex, const double* X, int m, int n, long ldx, double* Y, long ldy);
+template <typename Real>
+void transpose(Exec& ex, const Real* X, int m, int n, long ldx, Real* Y, long ldy);
 void set_identity(Exec& ex, double* I, int p);
 void tt_concat(Exec& ex, const std::vector<Term>& terms, TT& out);
 int total_rank(const std::vector<Term>& terms);
 void tt_sum_norm(Exec& ex, const TT& X, double* out_dev);
 
 RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int cap, TT& Y);
+// Truncation tolerance actually applied under ex.precision (the FP32 form
+// does not truncate below its own round-off).
+double effective_tol(const Exec& ex, double tol);
 RoundInfo round_cores(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol, int cap,
                       TT& Y);
 RoundInfo round_tt(Exec& ex, const TT& X, double tol, int cap, TT& Y);
@@ -62,6 +66,23 @@ struct CrossFn {
 };
 int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, int cap, int kick,
           int max_sweeps, unsigned seed, TT& y);
+
+// Learned-pivot network (mlp.cu): features X (n2 x 12, ld n2) of the column
+// mode of x0; scores s of m rows; gradients of the mean logistic loss into g
+// (same shapes as the parameters) and the loss into *loss (device, may be
+// null); one Adam step of the FP32 masters; top-k indices ascending.
+constexpr int kMlpFeatures = 12;
+constexpr int kMlpHidden = 256;
+void mlp_features(Exec& ex, const TT& x0, float* X);
+void mlp_forward(Exec& ex, const MlpNet& net, const float* X, int m, float* s);
+void mlp_grad(Exec& ex, const MlpNet& net, const float* X, const float* y, int m, const MlpNet& g, double* loss);
+void mlp_adam(Exec& ex, const MlpNet& p, const MlpNet& g, const MlpNet& m1, const MlpNet& m2, int t, float lr);
+void mlp_topk(Exec& ex, const float* s, int m, int k, int* idx);
+void mlp_propose(Exec& ex, const MlpNet& net, const TT& x0, int k, int* idx);
+
+// Training-data capture (fv.cu): features of x0's column mode with a 0/1
+// label per index (1: in the converged column pivot set J).
+void record_pivots(Exec& ex, const TT& x0, const std::vector<int>& J);
 
 // Linear reconstruction on cores (fv.cu)
 void recon_linear(Exec& ex, const TT& x, int direction, int scheme, TT& qm, TT& qp);

@@ -14,5 +14,6 @@ from .ic import (  # noqa: F401
     initial_tt,
     tt_to_full,
     random_tt,
+    ensemble,
     igw_cellavg,
 )

@@ -142,6 +142,26 @@ def initial_tt(w):
     raise ValueError(w["ic"])
 
 
+def ensemble(count=256, seed=1000, sizes=(128, 256, 512, 1024), cap_range=(8, 64)):
+    """Workload dicts of the batched ensemble: instance k draws its grid size
+    (uniform over `sizes`), rank cap (uniform integer in cap_range) and 1-3
+    Gaussian bumps of amplitude U[0.01, 0.1] and width U[0.03, 0.1] from
+    default_rng(seed + k); the reconstructions are a seeded permutation of
+    equal thirds of up3 / up5 / weno5.  Nonlinear SWE, tol 1e-8, CFL 0.4."""
+    rng = np.random.default_rng(seed)
+    schemes = (["up3", "up5", "weno5"] * ((count + 2) // 3))[:count]
+    schemes = [schemes[i] for i in rng.permutation(count)]
+    out = []
+    for k in range(count):
+        rk = np.random.default_rng(seed + k)
+        n = int(rk.choice(np.asarray(sizes)))
+        cap = int(rk.integers(cap_range[0], cap_range[1] + 1))
+        nb = int(rk.integers(1, 4))
+        out.append(dict(eqn="nonlinear", scheme=schemes[k], n=n, steps=100, tol=1e-8, cap=cap, ic="bumps",
+                        amp=0.1, amp_range=(0.01, 0.1), nbumps=nb, seed=seed + k, cfl=0.4, f=0.0))
+    return out
+
+
 def random_tt(n1, n2, r, seed, decay=None):
     """Seeded random TT cores (A, B) of rank r; with `decay`, column k of A is
     scaled by decay**k so the singular values fall off geometrically."""

@@ -48,6 +48,17 @@ def test_workspace_queries_without_gpu(lib):
     assert lib.tt_fv_workspace_size(ctypes.byref(p)) > 0
     bad = capi.tt_fv_params(1, 2, 256, 256, 1.0, 1.0, 9.81, 1.0, 0.0, -1.0, 1e-8, 32, 0, 0, 4, 10, 50, 0)
     assert lib.tt_fv_workspace_size(ctypes.byref(bad)) == 0
+    # the precision forms size their FP32 working copies on top of the FP64 cores
+    for prec in (capi.TT_FP32, capi.TT_TF32, capi.TT_BF16):
+        pp = capi.tt_fv_params(1, 1, 1024, 1024, 1.0, 1.0, 9.81, 1.0, 10.0, 1e-4, 1e-8, 48, prec, 0, 4, 10, 50, 0)
+        assert lib.tt_fv_workspace_size(ctypes.byref(pp)) > 0
+    pp = capi.tt_fv_params(1, 1, 1024, 1024, 1.0, 1.0, 9.81, 1.0, 10.0, 1e-4, 1e-8, 48, 7, 0, 4, 10, 50, 0)
+    assert lib.tt_fv_workspace_size(ctypes.byref(pp)) == 0
+    for prec in (capi.TT_FP64, capi.TT_FP32, capi.TT_TF32, capi.TT_BF16):
+        for split in (0, 1):
+            assert lib.tt_contract_workspace_size(prec, split, 1024, 112, 3072) > 0
+    assert lib.tt_contract_workspace_size(9, 1, 1024, 112, 3072) == 0
+    assert lib.tt_contract_workspace_size(capi.TT_TF32, 1, 0, 112, 3072) == 0
 
 
 def test_argument_errors_return_codes(lib):
