@@ -11,7 +11,7 @@ indicators; the top-scoring indices seed the sweeps, which keep judging the
 interpolation error, so plain maxvol remains the fallback.  Everything here
 is this project's own construction, written out plainly:
 
-features(A, B)  -> X (n2 x F), F = 12 columns per index j:
+features(A, B, prev)  -> X (n2 x F), F = 14 columns per index j:
   0  leverage l_j = (n2 / r) ||Q[j, :]||^2 with Q an orthonormal basis of B
   1-4 leverages of j-2, j-1, j+1, j+2 (periodic in j)
   5  column mean c_j = mean_i (A B^T)[i, j], standardised over j
@@ -20,6 +20,9 @@ features(A, B)  -> X (n2 x F), F = 12 columns per index j:
   8  log(1 + |second difference| / (mean |second difference| + 1e-300))
   9  column energy ||(A B^T)[:, j]||^2 / mean over j
   10, 11  sin, cos of 2 pi j / n2
+  12  1 if j is in `prev`, the converged column pivots of the same cross
+      site at the previous stage, else 0
+  13  min(periodic distance from j to `prev`, 8) / 8 (1 when prev is empty)
 (std(c) and the means are over j; a spread below 1e-12 mean|c| -- a flat
 profile up to round-off -- is replaced by 1.)
 
@@ -38,12 +41,13 @@ bf16=False.
 """
 import numpy as np
 
-F_IN = 12
+F_IN = 14
 HIDDEN = 256
 
 
-def features(A, B):
-    """Index features of the column mode of X = A B^T (A n1 x r, B n2 x r)."""
+def features(A, B, prev=()):
+    """Index features of the column mode of X = A B^T (A n1 x r, B n2 x r);
+    prev: the previous converged pivot indices of the same cross site."""
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
     n1, r = A.shape
@@ -70,6 +74,15 @@ def features(A, B):
     ang = 2.0 * np.pi * np.arange(n2) / n2
     X[:, 10] = np.sin(ang)
     X[:, 11] = np.cos(ang)
+    prev = np.asarray(list(prev), dtype=np.int64)
+    if prev.size:
+        X[prev, 12] = 1.0
+        j = np.arange(n2)[:, None]
+        d = np.abs(j - prev[None, :])
+        d = np.minimum(d, n2 - d).min(axis=1)
+        X[:, 13] = np.minimum(d, 8) / 8.0
+    else:
+        X[:, 13] = 1.0
     return X
 
 

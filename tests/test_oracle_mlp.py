@@ -56,9 +56,14 @@ def test_bf16_products_round_both_operands():
     Z2 = M.bf16(np.maximum(Z1, 0)) @ M.bf16(P["W2"]) + P["b2"]
     s = M.bf16(np.maximum(Z2, 0)) @ M.bf16(P["w3"]) + P["b3"][0]
     assert np.allclose(s_r, s, rtol=1e-13, atol=1e-13)
-    # rounding moves the scores by no more than BF16 resolution of the operands
+    # six operand roundings of relative size <= 2^-8 on the way to a score,
+    # through 1-Lipschitz ReLUs: |s_bf16 - s| <= ~6 2^-8 times the same
+    # network run on absolute values (first order; asserted with slack 8)
     s_e, _ = M.forward(P, X, bf16_ops=False)
-    assert np.max(np.abs(s_r - s_e)) <= 2 * 2.0 ** -8 * np.max(np.abs(s_e)) + 1e-3
+    H1a = np.abs(X) @ np.abs(P["W1"]) + np.abs(P["b1"])
+    H2a = H1a @ np.abs(P["W2"]) + np.abs(P["b2"])
+    sa = H2a @ np.abs(P["w3"]) + abs(P["b3"][0])
+    assert np.all(np.abs(s_r - s_e) <= 8 * 2.0 ** -8 * sa)
 
 
 def test_forward_closed_form():
@@ -108,6 +113,20 @@ def test_features_invariants():
     # a rank-1 matrix constant along j: uniform leverage, flat profile
     X1 = M.features(rng.standard_normal((n1, 1)), np.ones((n2, 1)))
     assert np.allclose(X1[:, 0], 1.0) and np.allclose(X1[:, 5:9], 0.0) and np.allclose(X1[:, 9], 1.0)
+    # no previous pivots: indicator 0, distance feature saturated at 1
+    assert np.all(X[:, 12] == 0.0) and np.all(X[:, 13] == 1.0)
+
+
+def test_previous_pivot_features_closed_form():
+    rng = np.random.default_rng(7)
+    A, B = rng.standard_normal((10, 3)), rng.standard_normal((16, 3))
+    X = M.features(A, B, prev=[3, 10])
+    assert list(np.nonzero(X[:, 12])[0]) == [3, 10]
+    # distances to {3, 10} on a 16-cycle, capped at 8, divided by 8
+    want = [3, 2, 1, 0, 1, 2, 3, 3, 2, 1, 0, 1, 2, 3, 4, 4]
+    assert np.array_equal(X[:, 13], np.array(want) / 8.0)
+    # the other features do not depend on prev
+    assert np.array_equal(X[:, :12], M.features(A, B)[:, :12])
 
 
 def test_top_indices_ties_to_smaller_index():
