@@ -191,18 +191,22 @@ tt_status tt_round(const tt2* x, double tol, int32_t rank_cap, tt2* y, double* e
 
 /* Learned-pivot form.  The paper's crosses (Sec. 3.3) refine pivots by maxvol
  * sweeps from some start; this form starts them from the column indices that
- * a 3-layer perceptron (12 -> 256 -> 256 -> 1, ReLU) scores highest from
- * features of the cross's initial TT.  The sweeps still judge the sampled
+ * a 3-layer perceptron (14 -> 256 -> 256 -> 1, ReLU) scores highest from
+ * features of the cross's initial TT and of the call site's previous pivots,
+ * and accepts them after one sweep when that sweep's skeleton already
+ * predicts fresh sample rows to the tolerance.  The sweeps still judge the sampled
  * interpolation error against the tolerance, so plain maxvol refinement is
  * the fallback whenever the proposal is not good enough.
- *   tt_mlp: caller-owned device FP32 parameters: W1 12x256 and W2 256x256
+ *   tt_mlp: caller-owned device FP32 parameters: W1 14x256 and W2 256x256
  *   row-major (W[in*256 + out]), b1, b2, w3 (256 each), b3 (1).  Every
  *   product of the forward and backward passes runs on tcgen05 tensor cores
  *   with both operands rounded to BF16 and FP32 accumulation.
- *   tt_mlp_features: X (n2 x 12 column-major, ld n2, device float) = the index
+ *   tt_mlp_features: X (n2 x 14 column-major, ld n2, device float) = the index
  *   features of x0's column mode (leverage of an orthonormal basis of x0->b
  *   and of its 4 neighbours, standardised column mean and its first/second
- *   differences, log curvature, column energy, sin/cos of the index angle).
+ *   differences, log curvature, column energy, sin/cos of the index angle,
+ *   and, from the nprev device indices prev of the same cross site's previous
+ *   converged pivots, an indicator and the distance to them capped at 8).
  *   tt_mlp_forward: scores s (m) of the rows of X (m x 12, ld m).
  *   tt_mlp_grad: gradients of the mean logistic loss over labels y (m, 0/1)
  *   into *grad (same shapes as net) and the loss into *loss (device double,
@@ -217,7 +221,7 @@ tt_status tt_round(const tt2* x, double tol, int32_t rank_cap, tt2* y, double* e
  * starts capturing, for every cross, the features of its initial TT with
  * label 1 on the converged column pivots (training data; adds a sync per
  * cross), tt_fv_pivot_rows reports the captured rows and tt_fv_pivot_take
- * copies them to host arrays X (rows x 12 row-major) and y (rows), then
+ * copies them to host arrays X (rows x 14 row-major) and y (rows), then
  * clears the capture. */
 typedef struct {
   float* W1;
@@ -228,7 +232,8 @@ typedef struct {
   float* b3;
 } tt_mlp;
 size_t tt_mlp_workspace_size(int32_t rows, int32_t rank);
-tt_status tt_mlp_features(const tt2* x0, float* X, void* ws, size_t ws_bytes, void* stream);
+tt_status tt_mlp_features(const tt2* x0, const int32_t* prev, int32_t nprev, float* X, void* ws, size_t ws_bytes,
+                          void* stream);
 tt_status tt_mlp_forward(const tt_mlp* net, const float* X, int32_t m, float* s, void* ws, size_t ws_bytes,
                          void* stream);
 tt_status tt_mlp_grad(const tt_mlp* net, const float* X, const float* y, int32_t m, const tt_mlp* grad,

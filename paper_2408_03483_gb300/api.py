@@ -230,10 +230,10 @@ class Solver:
         C.check("tt_fv_record_pivots", self.lib.tt_fv_record_pivots(self.h, 1 if enable else 0))
 
     def take_pivots(self):
-        """Captured (features rows x 12, labels rows) as numpy float32 arrays."""
+        """Captured (features rows x 14, labels rows) as numpy float32 arrays."""
         import numpy as np
         rows = int(self.lib.tt_fv_pivot_rows(self.h))
-        X = np.empty((rows, 12), dtype=np.float32)
+        X = np.empty((rows, 14), dtype=np.float32)
         y = np.empty(rows, dtype=np.float32)
         C.check("tt_fv_pivot_take", self.lib.tt_fv_pivot_take(self.h, X.ctypes.data_as(ctypes.c_void_p),
                                                               y.ctypes.data_as(ctypes.c_void_p), rows))
@@ -331,11 +331,11 @@ class Batch:
 
 class PivotNet:
     """Device parameters of the learned-pivot network (tt_mlp) with Adam
-    moments; weights as float32 CUDA tensors (W1 12x256, W2 256x256
+    moments; weights as float32 CUDA tensors (W1 14x256, W2 256x256
     row-major, b1, b2, w3 of 256, b3 of 1)."""
 
     NAMES = ("W1", "b1", "W2", "b2", "w3", "b3")
-    SHAPES = {"W1": (12, 256), "b1": (256,), "W2": (256, 256), "b2": (256,), "w3": (256,), "b3": (1,)}
+    SHAPES = {"W1": (14, 256), "b1": (256,), "W2": (256, 256), "b2": (256,), "w3": (256,), "b3": (1,)}
 
     def __init__(self, params=None, device="cuda"):
         _require_cuda()
@@ -363,8 +363,8 @@ class PivotNet:
         return self._struct(self.p)
 
     def forward(self, X, stream=None):
-        """Scores of the rows of X (m x 12 float32 CUDA tensor)."""
-        Xc = X.t().contiguous()  # column-major m x 12
+        """Scores of the rows of X (m x 14 float32 CUDA tensor)."""
+        Xc = X.t().contiguous()  # column-major m x 14
         m = X.shape[0]
         s = torch.empty(m, dtype=torch.float32, device=X.device)
         ws = _ws(self.lib.tt_mlp_workspace_size(m, 1))
@@ -401,15 +401,18 @@ class PivotNet:
         return loss
 
 
-def tt_mlp_features(x0, stream=None):
-    """Index features (n2 x 12 float32 CUDA tensor, row-major view) of x0's column mode."""
+def tt_mlp_features(x0, prev=(), stream=None):
+    """Index features (n2 x 14 float32 CUDA tensor, row-major view) of x0's
+    column mode; prev: the site's previous converged pivot indices."""
     _require_cuda()
     lib = C.load()
-    Xc = torch.empty((12, x0.n2), dtype=torch.float32, device="cuda")  # column-major n2 x 12
+    Xc = torch.empty((14, x0.n2), dtype=torch.float32, device="cuda")  # column-major n2 x 14
+    pv = torch.tensor(list(prev) or [0], dtype=torch.int32, device="cuda")
     ws = _ws(lib.tt_mlp_workspace_size(x0.n2, x0.rank))
     xs = x0.struct()
-    C.check("tt_mlp_features", lib.tt_mlp_features(ctypes.byref(xs), ctypes.c_void_p(Xc.data_ptr()),
-                                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    C.check("tt_mlp_features", lib.tt_mlp_features(ctypes.byref(xs), ctypes.c_void_p(pv.data_ptr()), len(prev),
+                                                   ctypes.c_void_p(Xc.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                                   ws.numel(), _stream_ptr(stream)))
     return Xc.t()
 
 

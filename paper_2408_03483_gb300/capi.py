@@ -95,7 +95,7 @@ SIGNATURES = {
     "tt_round_workspace_size": (_sz, [_i32, _i32, _i32, _i32]),
     "tt_round": (ctypes.c_int, [_P(tt2), _d, _i32, _P(tt2), _P(_d), _vp, _sz, _vp]),
     "tt_mlp_workspace_size": (_sz, [_i32, _i32]),
-    "tt_mlp_features": (ctypes.c_int, [_P(tt2), _vp, _vp, _sz, _vp]),
+    "tt_mlp_features": (ctypes.c_int, [_P(tt2), _vp, _i32, _vp, _vp, _sz, _vp]),
     "tt_mlp_forward": (ctypes.c_int, [_P(tt_mlp), _vp, _i32, _vp, _vp, _sz, _vp]),
     "tt_mlp_grad": (ctypes.c_int, [_P(tt_mlp), _vp, _vp, _i32, _P(tt_mlp), _vp, _vp, _sz, _vp]),
     "tt_mlp_adam": (ctypes.c_int, [_P(tt_mlp), _P(tt_mlp), _P(tt_mlp), _P(tt_mlp), _i32, ctypes.c_float, _vp]),

@@ -371,10 +371,11 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
   std::vector<int> J;
   const int r0 = std::max(1, std::min({x0.r, cap, n1, n2}));
   const bool learned = ex.pivot_net != nullptr && n2 > r0 && r0 <= 128;
+  const std::vector<int> prev_site = f.site ? *f.site : std::vector<int>();
   bool first_check_converged = false;
   if (learned) {
     ex.learned_calls++;
-    mlp_propose(ex, *ex.pivot_net, x0, r0, dJ);
+    mlp_propose(ex, *ex.pivot_net, x0, prev_site, r0, dJ);
     J = fetch_idx(ex, dJ, r0);
   } else {
     Scope s2(*ex.ar);
@@ -458,6 +459,38 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
     kprev = kc;
     Iprev = I;
     have_prev = true;
+    // learned start: accept after this first sweep when its skeleton
+    // Uc Uc[I]^{-1} F(I, :) already predicts the fresh kick rows to tol
+    if (learned && s == 0 && ri > kc && !ex.dry) {
+      Scope s5(*ex.ar);
+      const int nk = ri - kc;
+      double* Pm = ex.ar->get<double>((size_t)kc * kc);
+      double* PT = ex.ar->get<double>((size_t)kc * kc);
+      double* Gk = ex.ar->get<double>((size_t)nk * kc);
+      double* GT = ex.ar->get<double>((size_t)kc * nk);
+      double* ZT = ex.ar->get<double>((size_t)kc * nk);
+      double* Dk = ex.ar->get<double>((size_t)n2 * nk);
+      TT_KERNEL(ex, K_OTHER, 0, 16.0 * kc * kc,
+                k_gather_rows<<<ceil_div((long)kc * kc, 256), 256, 0, ex.s>>>(Uc, n1, dI, kc, kc, Pm));
+      TT_KERNEL(ex, K_OTHER, 0, 16.0 * nk * kc,
+                k_gather_rows<<<ceil_div((long)nk * kc, 256), 256, 0, ex.s>>>(Uc, n1, dI + kc, nk, kc, Gk));
+      transpose(ex, Pm, kc, kc, kc, PT, kc);
+      transpose(ex, Gk, nk, kc, nk, GT, kc);
+      // ZT = Uc[I]^{-T} Uc[kick]^T, so Z = Uc[kick] Uc[I]^{-1}
+      small_solve(ex, PT, kc, GT, nk, ZT);
+      // D = F(kick, :)^T - F(I, :)^T Z^T
+      scaled_copy(ex, Dk, RT + (size_t)kc * n2, (long)n2 * nk, 1.0);
+      gemm(ex, n2, nk, kc, -1.0, RT, 1, n2, ZT, 1, kc, 1.0, Dk, n2);
+      sumsq(ex, Dk, n2, nk, n2, nrm);
+      sumsq(ex, RT + (size_t)kc * n2, n2, nk, n2, nrm + 1);
+      double v[2];
+      fetch_doubles(ex, nrm, 2, v);
+      const double err = v[1] > 0.0 ? std::sqrt(v[0] / v[1]) : 0.0;
+      if (err <= tol) {
+        first_check_converged = true;
+        break;
+      }
+    }
     const int kr = orth_left(ex, RT, n2, ri, tol, cap, Vr);
     maxvol(ex, Vr, n2, kr, 1e-2, 200, dJ);
     std::vector<int> Jn = fetch_idx(ex, dJ, kr);
@@ -468,7 +501,8 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
   // the learned start is accepted when the first interpolation check on
   // fresh fibres already passes; otherwise the maxvol sweeps above took over
   if (learned && first_check_converged) ex.learned_accepted++;
-  if (ex.pivot_rec) record_pivots(ex, x0, J);
+  if (ex.pivot_rec) record_pivots(ex, x0, prev_site, J);
+  if (f.site) *f.site = J;
   // skeleton: A = Uc_prev (Uc_prev[I])^{-1}, B = F(I, :)^T = RT_prev[:, :k]
   {
     Scope s4(*ex.ar);

@@ -157,13 +157,16 @@ struct Solver {
   double section_ms[6] = {};
   MlpNet net;                      // learned-pivot network (caller-owned weights)
   PivotRecorder* rec = nullptr;    // training-data capture, when enabled
+  // converged column pivots of each cross site at its previous call:
+  // WENO (direction, field, side, step) = 24 sites, then LLF lambda per direction
+  std::vector<int> sites[26];
   ~Solver();
 };
 
 // Captured (features, label) rows of the crosses of one solver
 struct PivotRecorder {
   std::mutex mu;
-  std::vector<float> X;  // rows x 12, row-major
+  std::vector<float> X;  // rows x kMlpFeatures, row-major
   std::vector<float> y;
 };
 
@@ -176,12 +179,12 @@ Solver::~Solver() {
   }
 }
 
-void record_pivots(Exec& ex, const TT& x0, const std::vector<int>& J) {
+void record_pivots(Exec& ex, const TT& x0, const std::vector<int>& prev, const std::vector<int>& J) {
   if (ex.dry || !ex.pivot_rec) return;
   const int n2 = x0.n2;
   Scope sc(*ex.ar);
   float* X = ex.ar->get<float>((size_t)n2 * kMlpFeatures);
-  mlp_features(ex, x0, X);
+  mlp_features_host_prev(ex, x0, prev, X);
   std::vector<float> h((size_t)n2 * kMlpFeatures);
   TT_CUDA(cudaMemcpyAsync(h.data(), X, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, ex.s));
   TT_CUDA(cudaStreamSynchronize(ex.s));
@@ -229,10 +232,12 @@ static void weno_side(Solver& S, Exec& ex, const TT& q, int d, int fieldc, int k
   const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
   const unsigned seed_base = seed + 64u * d + 8u * fieldc;
   Scope sc(*ex.ar);
+  const int site = ((d * 3 + fieldc) * 2 + k) * 2;
   CrossFn f1n;
   f1n.fn = TT_FN_WENO_S1;
   f1n.in = &q;
   f1n.nin = 1;
+  f1n.site = &S.sites[site];
   f1n.prm[0] = e1;
   f1n.prm[1] = k == 0 ? -1.0 : 1.0;
   f1n.prm[2] = d;
@@ -256,6 +261,7 @@ static void weno_side(Solver& S, Exec& ex, const TT& q, int d, int fieldc, int k
   f2n.fn = TT_FN_WENO_S2;
   f2n.in = &vt;
   f2n.nin = 1;
+  f2n.site = &S.sites[site + 1];
   f2n.prm[0] = e2;
   f2n.prm[1] = d == 0 ? 1.0 : 0.0;
   f2n.prm[2] = 3;
@@ -341,6 +347,7 @@ static void face_lambda(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int
   fl.fn = TT_FN_LLF_LAMBDA;
   fl.in = ins;
   fl.nin = 4;
+  fl.site = &S.sites[24 + d];
   fl.prm[0] = p.g;
   const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
   cross(ex, fl, qm[0].n1, qm[0].n2, qp[0], p.tol, p.rank_cap, kick, sweeps, seed, lam);
@@ -999,17 +1006,18 @@ size_t tt_mlp_workspace_size(int32_t rows, int32_t rank) {
     TT x0 = fake_tt(*ex.ar, rows, rows, rank);
     float* X = ex.ar->get<float>((size_t)rows * kMlpFeatures);
     float* y = ex.ar->get<float>((size_t)rows);
-    mlp_features(ex, x0, X);
+    mlp_features(ex, x0, nullptr, 0, X);
     MlpNet n, g;
     mlp_grad(ex, n, X, y, rows, g, nullptr);
     mlp_topk(ex, y, rows, std::min(rows, 112), nullptr);
   });
 }
 
-tt_status tt_mlp_features(const tt2* x0, float* X, void* ws, size_t ws_bytes, void* stream) {
-  if (!valid_tt(x0) || x0->rank > 112 || !X) return TT_ERR_ARG;
+tt_status tt_mlp_features(const tt2* x0, const int32_t* prev, int32_t nprev, float* X, void* ws, size_t ws_bytes,
+                          void* stream) {
+  if (!valid_tt(x0) || x0->rank > 112 || !X || nprev < 0 || (nprev > 0 && !prev)) return TT_ERR_ARG;
   return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
-    mlp_features(ex, to_tt(*x0), X);
+    mlp_features(ex, to_tt(*x0), prev, nprev, X);
     return TT_OK;
   });
 }

@@ -9,6 +9,7 @@
 #include <cfloat>
 #include <cmath>
 #include <algorithm>
+#include <type_traits>
 
 #include "tt_common.cuh"
 
@@ -299,16 +300,50 @@ __device__ void cta_householder_qr(Real* A, int mb, int p, Real* tau_out) {
   }
 }
 
+// Element i of an array that is FP64 (f64 != 0) or of the working type
 template <typename Real>
-__global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const Real* __restrict__ X, int m, int p, long ldx,
-                                                          int mb, Real* V, Real* tau, Real* Rout) {
+__device__ __forceinline__ Real ld_any(const void* p, size_t i, int f64) {
+  return f64 ? Real(static_cast<const double*>(p)[i]) : static_cast<const Real*>(p)[i];
+}
+template <typename Real>
+__device__ __forceinline__ void st_any(void* p, size_t i, int f64, Real v) {
+  if (f64)
+    static_cast<double*>(p)[i] = double(v);
+  else
+    static_cast<Real*>(p)[i] = v;
+}
+
+// One matrix of a (one- or two-matrix) TSQR launch.  Launches carry two job
+// descriptors; the CTAs of job 0 come first and a job with no CTAs (nb = 0,
+// nodes = 0) is absent, so the two factorisations of a rounding share each
+// launch and run side by side on the GPU.
+template <typename Real>
+struct LeafJob {
+  const void* X;
+  int x64;
+  int m;
+  long ldx;
+  Real* V;
+  Real* tau;
+  Real* R;
+  int nb;
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(LeafJob<Real> j0, LeafJob<Real> j1, int p, int mb) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Real* sm = reinterpret_cast<Real*>(smraw);
-  const int b = blockIdx.x, r0 = b * mb;
+  const bool second = (int)blockIdx.x >= j0.nb;
+  const LeafJob<Real> jb = second ? j1 : j0;
+  const int b = second ? (int)blockIdx.x - j0.nb : (int)blockIdx.x, r0 = b * mb;
+  const int m = jb.m;
+  Real* V = jb.V;
+  Real* tau = jb.tau;
+  Real* Rout = jb.R;
   Real* A = sm;
   for (int t = threadIdx.x; t < mb * p; t += blockDim.x) {
     const int i = t % mb, j = t / mb;
-    A[t] = (r0 + i < m) ? X[(r0 + i) + (size_t)j * ldx] : Real(0);
+    A[t] = (r0 + i < m) ? ld_any<Real>(jb.X, (size_t)(r0 + i) + (size_t)j * jb.ldx, jb.x64) : Real(0);
   }
   __syncthreads();
   cta_householder_qr<Real>(A, mb, p, tau + (size_t)b * p);
@@ -328,11 +363,30 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(const Real* __restrict
 // is needed.  Columns are spread over lanes (lane = column within a group of
 // 32), the bottom blocks over warps; a node with one input passes it through.
 template <typename Real>
-__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(const Real* __restrict__ Rin, int nin, int p, int g,
-                                                         Real* Rout, Real* Vm, Real* vtop, Real* taum) {
+struct MergeJob {
+  const Real* Rin;
+  int nin;
+  int nodes;
+  Real* Rout;
+  Real* Vm;
+  Real* vtop;
+  Real* taum;
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, MergeJob<Real> j1, int p, int g) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Real* sm = reinterpret_cast<Real*>(smraw);
-  const int node = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool second = (int)blockIdx.x >= j0.nodes;
+  const MergeJob<Real> jb = second ? j1 : j0;
+  const Real* __restrict__ Rin = jb.Rin;
+  const int nin = jb.nin;
+  Real* Rout = jb.Rout;
+  Real* Vm = jb.Vm;
+  Real* vtop = jb.vtop;
+  Real* taum = jb.taum;
+  const int node = second ? (int)blockIdx.x - j0.nodes : (int)blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int first = node * g, ng = min(g, nin - first);
   Real* Ro = Rout + (size_t)node * p * p;
   Real* Vo = Vm + (size_t)node * g * p * p;  // bottom blocks 1..ng-1 at Vo + b*p*p
@@ -450,65 +504,130 @@ static int qr_leaf_rows(int p, size_t elem) {
   return std::max(std::min(mb, lim), p);
 }
 
+// Factor nj (1 or 2) tall matrices with the same column count p: one leaf
+// launch and one launch per merge level for both.
 template <typename Real>
-void tsqr(Exec& ex, const Real* X, int m, int p, long ldx, QRTreeT<Real>& t) {
-  TT_REQUIRE(p >= 1 && p <= 112 && m >= 1, TT_ERR_ARG);
-  t = QRTreeT<Real>{};
-  t.m = m;
-  t.p = p;
-  t.mb0 = qr_leaf_rows(p, sizeof(Real));
-  t.nb0 = ceil_div(m, t.mb0);
-  t.V0 = ex.ar->get<Real>((size_t)t.nb0 * t.mb0 * p);
-  t.tau0 = ex.ar->get<Real>((size_t)t.nb0 * p);
-  Real* R = ex.ar->get<Real>((size_t)t.nb0 * p * p);
+static void tsqr_run(Exec& ex, int nj, const void* const* X, const int* x64, const int* m, const long* ldx, int p,
+                     QRTreeT<Real>* const* t) {
+  TT_REQUIRE(p >= 1 && p <= 112, TT_ERR_ARG);
+  const int mb = qr_leaf_rows(p, sizeof(Real)), g = qr_merge_fanin(p, sizeof(Real));
+  Real* R[2] = {nullptr, nullptr};
+  int n[2] = {1, 1};
+  LeafJob<Real> lj[2] = {};
+  int nbt = 0;
+  double fl = 0.0, by = 0.0;
+  for (int q = 0; q < nj; ++q) {
+    TT_REQUIRE(m[q] >= 1, TT_ERR_ARG);
+    QRTreeT<Real>& tq = *t[q];
+    tq = QRTreeT<Real>{};
+    tq.m = m[q];
+    tq.p = p;
+    tq.mb0 = mb;
+    tq.nb0 = ceil_div(m[q], mb);
+    tq.g = g;
+    tq.V0 = ex.ar->get<Real>((size_t)tq.nb0 * mb * p);
+    tq.tau0 = ex.ar->get<Real>((size_t)tq.nb0 * p);
+    R[q] = ex.ar->get<Real>((size_t)tq.nb0 * p * p);
+    lj[q] = LeafJob<Real>{X[q], x64[q], m[q], ldx[q], tq.V0, tq.tau0, R[q], tq.nb0};
+    nbt += tq.nb0;
+    n[q] = tq.nb0;
+    fl += std::max(2.0 * m[q] * (double)p * p - tq.nb0 * (2.0 / 3.0) * p * (double)p * p, 0.0);
+    by += (double)sizeof(Real) * ((double)m[q] * p * 2 + (double)tq.nb0 * p * p);
+  }
   if (!ex.dry) {
     smem_attr_once(k_qr_blocks<Real>);
-    const size_t smem = (size_t)t.mb0 * p * sizeof(Real);
-    const double fl = 2.0 * m * (double)p * p - t.nb0 * (2.0 / 3.0) * p * (double)p * p;
-    TT_KERNEL(ex, K_QR, std::max(fl, 0.0), (double)sizeof(Real) * ((double)m * p * 2 + (double)t.nb0 * p * p),
-              k_qr_blocks<Real><<<t.nb0, QR_THREADS, smem, ex.s>>>(X, m, p, ldx, t.mb0, t.V0, t.tau0, R));
+    const size_t smem = (size_t)mb * p * sizeof(Real);
+    TT_KERNEL(ex, K_QR, fl, by, k_qr_blocks<Real><<<nbt, QR_THREADS, smem, ex.s>>>(lj[0], lj[1], p, mb));
   }
-  int n = t.nb0;
-  const int g = qr_merge_fanin(p, sizeof(Real));
-  while (n > 1) {
-    const int nodes = (n + g - 1) / g;
-    Real* Vm = ex.ar->get<Real>((size_t)nodes * g * p * p);
-    Real* vt = ex.ar->get<Real>((size_t)nodes * p);
-    Real* tm = ex.ar->get<Real>((size_t)nodes * p);
-    Real* Rn = ex.ar->get<Real>((size_t)nodes * p * p);
-    t.nin.push_back(n);
-    t.Vm.push_back(Vm);
-    t.vtop.push_back(vt);
-    t.taum.push_back(tm);
+  for (;;) {
+    MergeJob<Real> mj[2] = {};
+    int nodes_total = 0, maxin = 0;
+    double mfl = 0.0, mby = 0.0;
+    for (int q = 0; q < nj; ++q) {
+      if (n[q] <= 1) continue;
+      QRTreeT<Real>& tq = *t[q];
+      const int nodes = (n[q] + g - 1) / g;
+      Real* Vm = ex.ar->get<Real>((size_t)nodes * g * p * p);
+      Real* vt = ex.ar->get<Real>((size_t)nodes * p);
+      Real* tm = ex.ar->get<Real>((size_t)nodes * p);
+      Real* Rn = ex.ar->get<Real>((size_t)nodes * p * p);
+      tq.nin.push_back(n[q]);
+      tq.Vm.push_back(Vm);
+      tq.vtop.push_back(vt);
+      tq.taum.push_back(tm);
+      mj[q] = MergeJob<Real>{R[q], n[q], nodes, Rn, Vm, vt, tm};
+      nodes_total += nodes;
+      maxin = std::max(maxin, std::min(g, n[q]));
+      mfl += (n[q] - nodes) * (2.0 / 3.0) * p * (double)p * p;
+      mby += (double)sizeof(Real) * 3.0 * n[q] * p * (double)p;
+      R[q] = Rn;
+      n[q] = nodes;
+    }
+    if (nodes_total == 0) break;
     if (!ex.dry) {
       smem_attr_once(k_qr_merge<Real>);
-      const size_t smem = ((size_t)std::min(g, n) * p * p + (size_t)16 * p) * sizeof(Real);
-      TT_KERNEL(ex, K_QR, (n - nodes) * (2.0 / 3.0) * p * (double)p * p, (double)sizeof(Real) * 3.0 * n * p * (double)p,
-                k_qr_merge<Real><<<nodes, QR_THREADS, smem, ex.s>>>(R, n, p, g, Rn, Vm, vt, tm));
+      const size_t smem = ((size_t)maxin * p * p + (size_t)16 * p) * sizeof(Real);
+      TT_KERNEL(ex, K_QR, mfl, mby, k_qr_merge<Real><<<nodes_total, QR_THREADS, smem, ex.s>>>(mj[0], mj[1], p, g));
     }
-    R = Rn;
-    n = nodes;
   }
-  t.g = g;
-  t.R = R;
+  for (int q = 0; q < nj; ++q) t[q]->R = R[q];
+}
+
+template <typename Real, typename Src>
+void tsqr(Exec& ex, const Src* X, int m, int p, long ldx, QRTreeT<Real>& t) {
+  const void* xs[1] = {X};
+  const int f64[1] = {std::is_same<Src, double>::value ? 1 : 0};
+  const int ms[1] = {m};
+  const long ls[1] = {ldx};
+  QRTreeT<Real>* ts[1] = {&t};
+  tsqr_run<Real>(ex, 1, xs, f64, ms, ls, p, ts);
+}
+
+template <typename Real, typename Src>
+void tsqr2(Exec& ex, const Src* X1, int m1, long ldx1, const Src* X2, int m2, long ldx2, int p, QRTreeT<Real>& t1,
+           QRTreeT<Real>& t2) {
+  const void* xs[2] = {X1, X2};
+  const int f = std::is_same<Src, double>::value ? 1 : 0;
+  const int f64[2] = {f, f};
+  const int ms[2] = {m1, m2};
+  const long ls[2] = {ldx1, ldx2};
+  QRTreeT<Real>* ts[2] = {&t1, &t2};
+  tsqr_run<Real>(ex, 2, xs, f64, ms, ls, p, ts);
 }
 
 // Apply the level-0 reflectors of each block (in reverse order) to
 // [Zin_block; 0], Zin_block = Zin + b*zstride (p x k, ld zld).
 template <typename Real>
-__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const Real* __restrict__ V,
-                                                                const Real* __restrict__ tau, int mb, int p,
-                                                                int rows, int k, const Real* __restrict__ Zin,
-                                                                long zstride, long zld, Real* __restrict__ Zout,
-                                                                long ldzo) {
+struct ALeafJob {
+  const Real* V;
+  const Real* tau;
+  int rows;
+  int nb;
+  const void* zin;
+  int z64;
+  long zstride, zld;
+  void* out;
+  int o64;
+  long ldo;
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(ALeafJob<Real> j0, ALeafJob<Real> j1, int mb, int p,
+                                                                int k) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Real* sm = reinterpret_cast<Real*>(smraw);
-  const int b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool second = (int)blockIdx.x >= j0.nb;
+  const ALeafJob<Real> jb = second ? j1 : j0;
+  const Real* __restrict__ V = jb.V;
+  const Real* __restrict__ tau = jb.tau;
+  const int rows = jb.rows;
+  const int b = second ? (int)blockIdx.x - j0.nb : (int)blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   Real* Z = sm;  // mb x k
-  const Real* zb = Zin + (size_t)b * zstride;
+  const size_t zoff = (size_t)b * jb.zstride;
   for (int t = threadIdx.x; t < mb * k; t += blockDim.x) {
     const int i = t % mb, j = t / mb;
-    Z[t] = (i < p) ? zb[i + (size_t)j * zld] : Real(0);
+    Z[t] = (i < p) ? ld_any<Real>(jb.zin, zoff + i + (size_t)j * jb.zld, jb.z64) : Real(0);
   }
   __syncthreads();
   const Real* Vb = V + (size_t)b * mb * p;
@@ -532,31 +651,51 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(const Real* __re
   const int r0 = b * mb;
   for (int t = threadIdx.x; t < mb * k; t += blockDim.x) {
     const int i = t % mb, j = t / mb;
-    if (r0 + i < rows) Zout[(size_t)(r0 + i) + (size_t)j * ldzo] = Z[t];
+    if (r0 + i < rows) st_any<Real>(jb.out, (size_t)(r0 + i) + (size_t)j * jb.ldo, jb.o64, Z[t]);
   }
 }
 
 // Reverse of a merge node: [top; B_1; ...] = Q_node [Z; 0; ...]; the top goes
 // to input node*g, block b to input node*g + b (each p x k, ld p).
 template <typename Real>
-__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(const Real* __restrict__ Vm,
-                                                               const Real* __restrict__ vtop,
-                                                               const Real* __restrict__ taum, int nin, int p,
-                                                               int g, int k, const Real* __restrict__ Zin,
-                                                               long zstride, long zld, Real* __restrict__ Zout) {
+struct AMergeJob {
+  const Real* Vm;
+  const Real* vtop;
+  const Real* taum;
+  int nin;
+  int nodes;
+  const void* zin;
+  int z64;
+  long zstride, zld;
+  Real* zout;
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(AMergeJob<Real> j0, AMergeJob<Real> j1, int p, int g,
+                                                               int k) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Real* sm = reinterpret_cast<Real*>(smraw);
-  const int node = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool second = (int)blockIdx.x >= j0.nodes;
+  const AMergeJob<Real> jb = second ? j1 : j0;
+  const Real* __restrict__ Vm = jb.Vm;
+  const Real* __restrict__ vtop = jb.vtop;
+  const Real* __restrict__ taum = jb.taum;
+  const int nin = jb.nin;
+  const int node = second ? (int)blockIdx.x - j0.nodes : (int)blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int first = node * g, ng = min(g, nin - first);
-  const Real* zb = Zin + (size_t)node * zstride;
-  Real* out = Zout + (size_t)first * p * k;
+  const size_t zoff = (size_t)node * jb.zstride;
+  const long zld = jb.zld;
+  Real* out = jb.zout + (size_t)first * p * k;
   if (ng == 1) {
-    for (int t = threadIdx.x; t < p * k; t += blockDim.x) out[t] = zb[(t % p) + (size_t)(t / p) * zld];
+    for (int t = threadIdx.x; t < p * k; t += blockDim.x)
+      out[t] = ld_any<Real>(jb.zin, zoff + (t % p) + (size_t)(t / p) * zld, jb.z64);
     return;
   }
   Real* Z = sm;                          // ng blocks of p x k
   Real* part = sm + (size_t)ng * p * k;  // [slice][column]
-  for (int t = threadIdx.x; t < p * k; t += blockDim.x) Z[t] = zb[(t % p) + (size_t)(t / p) * zld];
+  for (int t = threadIdx.x; t < p * k; t += blockDim.x)
+    Z[t] = ld_any<Real>(jb.zin, zoff + (t % p) + (size_t)(t / p) * zld, jb.z64);
   for (int t = threadIdx.x; t < (ng - 1) * p * k; t += blockDim.x) Z[(size_t)p * k + t] = Real(0);
   const Real* V = Vm + (size_t)node * g * p * p;
   const Real* vt = vtop + (size_t)node * p;
@@ -601,39 +740,94 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(const Real* __res
   for (int t = threadIdx.x; t < ng * p * k; t += blockDim.x) out[t] = Z[t];
 }
 
+// Out_q (m_q x k) = Q_q [C_q; 0] for nj (1 or 2) trees with the same p:
+// one launch per merge level (counted from the leaves) and one leaf launch.
 template <typename Real>
-void tsqr_apply(Exec& ex, const QRTreeT<Real>& t, const Real* C, int k, long ldc, Real* Out, long ldo) {
-  TT_REQUIRE(k >= 1 && k <= t.p, TT_ERR_ARG);
+static void tsqr_apply_run(Exec& ex, int nj, const QRTreeT<Real>* const* t, const void* const* C, const int* c64,
+                           const long* ldc, void* const* Out, const int* o64, const long* ldo, int k) {
+  const int p = t[0]->p;
+  TT_REQUIRE(k >= 1 && k <= p && (nj == 1 || t[1]->p == p), TT_ERR_ARG);
   Scope sc(*ex.ar);
-  const int p = t.p;
-  const Real* zin = C;
-  long zstride = 0, zld = ldc;
-  for (int l = (int)t.nin.size() - 1; l >= 0; --l) {
-    const int nin = t.nin[l], nodes = (nin + t.g - 1) / t.g;
-    Real* zout = ex.ar->get<Real>((size_t)nin * p * k);
-    if (!ex.dry) {
-      smem_attr_once(k_qr_apply_merge<Real>);
-      const size_t smem = ((size_t)std::min(t.g, nin) * p * k + (size_t)16 * k) * sizeof(Real);
-      TT_KERNEL(ex, K_QR_APPLY, (nin - nodes) * 2.0 * p * (double)p * k,
-                (double)sizeof(Real) * ((double)nin * p * p + 2.0 * nin * p * k),
-                k_qr_apply_merge<Real><<<nodes, QR_THREADS, smem, ex.s>>>(t.Vm[l], t.vtop[l], t.taum[l], nin, p, t.g, k,
-                                                                    zin, zstride, zld, zout));
+  const void* zin[2] = {C[0], nj > 1 ? C[1] : nullptr};
+  int z64[2] = {c64[0], nj > 1 ? c64[1] : 0};
+  long zs[2] = {0, 0}, zl[2] = {ldc[0], nj > 1 ? ldc[1] : 0};
+  int L[2] = {0, 0}, maxL = 0;
+  for (int q = 0; q < nj; ++q) {
+    L[q] = (int)t[q]->nin.size();
+    maxL = std::max(maxL, L[q]);
+  }
+  const int g = t[0]->g;
+  for (int d = maxL - 1; d >= 0; --d) {
+    AMergeJob<Real> aj[2] = {};
+    int nodes_total = 0, maxin = 0;
+    double fl = 0.0, by = 0.0;
+    for (int q = 0; q < nj; ++q) {
+      if (d >= L[q]) continue;
+      const int nin = t[q]->nin[d], nodes = (nin + g - 1) / g;
+      Real* zout = ex.ar->get<Real>((size_t)nin * p * k);
+      aj[q] = AMergeJob<Real>{t[q]->Vm[d], t[q]->vtop[d], t[q]->taum[d], nin, nodes, zin[q], z64[q], zs[q], zl[q],
+                              zout};
+      nodes_total += nodes;
+      maxin = std::max(maxin, std::min(g, nin));
+      fl += (nin - nodes) * 2.0 * p * (double)p * k;
+      by += (double)sizeof(Real) * ((double)nin * p * p + 2.0 * nin * p * k);
+      zin[q] = zout;
+      z64[q] = 0;
+      zs[q] = (long)p * k;
+      zl[q] = p;
     }
-    zin = zout;
-    zstride = (long)p * k;
-    zld = p;
+    if (!ex.dry && nodes_total > 0) {
+      smem_attr_once(k_qr_apply_merge<Real>);
+      const size_t smem = ((size_t)maxin * p * k + (size_t)16 * k) * sizeof(Real);
+      TT_KERNEL(ex, K_QR_APPLY, fl, by,
+                k_qr_apply_merge<Real><<<nodes_total, QR_THREADS, smem, ex.s>>>(aj[0], aj[1], p, g, k));
+    }
+  }
+  ALeafJob<Real> lj[2] = {};
+  int nbt = 0;
+  double fl = 0.0, by = 0.0;
+  for (int q = 0; q < nj; ++q) {
+    const QRTreeT<Real>& tq = *t[q];
+    lj[q] = ALeafJob<Real>{tq.V0, tq.tau0, tq.m, tq.nb0, zin[q], z64[q], zs[q], zl[q], Out[q], o64[q], ldo[q]};
+    nbt += tq.nb0;
+    fl += 4.0 * tq.m * (double)p * k;
+    by += (double)sizeof(Real) * ((double)tq.m * (p + k) + (double)tq.nb0 * p * k);
   }
   if (!ex.dry) {
+    const int mb = t[0]->mb0;
     smem_attr_once(k_qr_apply_blocks<Real>);
-    const size_t smem = (size_t)t.mb0 * k * sizeof(Real);
+    const size_t smem = (size_t)mb * k * sizeof(Real);
     TT_REQUIRE(smem <= QR_SMEM_MAX + 16 * 1024, TT_ERR_ARG);
-    TT_KERNEL(ex, K_QR_APPLY, 4.0 * t.m * (double)p * k,
-              (double)sizeof(Real) * ((double)t.m * (p + k) + (double)t.nb0 * p * k),
-              k_qr_apply_blocks<Real><<<t.nb0, QR_THREADS, smem, ex.s>>>(t.V0, t.tau0, t.mb0, p, t.m, k, zin, zstride, zld,
-                                                                  Out, ldo));
+    TT_KERNEL(ex, K_QR_APPLY, fl, by,
+              k_qr_apply_blocks<Real><<<nbt, QR_THREADS, smem, ex.s>>>(lj[0], lj[1], mb, p, k));
   }
 }
 
+template <typename Real, typename ZT, typename OT>
+void tsqr_apply(Exec& ex, const QRTreeT<Real>& t, const ZT* C, int k, long ldc, OT* Out, long ldo) {
+  const QRTreeT<Real>* ts[1] = {&t};
+  const void* cs[1] = {C};
+  const int c64[1] = {std::is_same<ZT, double>::value ? 1 : 0};
+  const long lc[1] = {ldc};
+  void* os[1] = {Out};
+  const int o64[1] = {std::is_same<OT, double>::value ? 1 : 0};
+  const long lo[1] = {ldo};
+  tsqr_apply_run<Real>(ex, 1, ts, cs, c64, lc, os, o64, lo, k);
+}
+
+template <typename Real, typename ZT, typename OT>
+void tsqr_apply2(Exec& ex, const QRTreeT<Real>& t1, const ZT* C1, long ldc1, OT* Out1, long ldo1,
+                 const QRTreeT<Real>& t2, const ZT* C2, long ldc2, OT* Out2, long ldo2, int k) {
+  const QRTreeT<Real>* ts[2] = {&t1, &t2};
+  const void* cs[2] = {C1, C2};
+  const int cf = std::is_same<ZT, double>::value ? 1 : 0, of = std::is_same<OT, double>::value ? 1 : 0;
+  const int c64[2] = {cf, cf};
+  const long lc[2] = {ldc1, ldc2};
+  void* os[2] = {Out1, Out2};
+  const int o64[2] = {of, of};
+  const long lo[2] = {ldo1, ldo2};
+  tsqr_apply_run<Real>(ex, 2, ts, cs, c64, lc, os, o64, lo, k);
+}
 
 // ---- explicit instantiations: FP64 path and the FP32 precision form
 template void gemm<double>(Exec&, int, int, int, double, const double*, long, long, const double*, long, long, double,
@@ -646,10 +840,22 @@ template void form_hadamard_full<float>(Exec&, int, int, const double*, int, con
                                         const double*, float*, long);
 template void sumsq<double>(Exec&, const double*, int, int, long, double*);
 template void sumsq<float>(Exec&, const float*, int, int, long, double*);
-template void tsqr<double>(Exec&, const double*, int, int, long, QRTreeT<double>&);
-template void tsqr<float>(Exec&, const float*, int, int, long, QRTreeT<float>&);
-template void tsqr_apply<double>(Exec&, const QRTreeT<double>&, const double*, int, long, double*, long);
-template void tsqr_apply<float>(Exec&, const QRTreeT<float>&, const float*, int, long, float*, long);
+template void tsqr<double, double>(Exec&, const double*, int, int, long, QRTreeT<double>&);
+template void tsqr<float, float>(Exec&, const float*, int, int, long, QRTreeT<float>&);
+template void tsqr<float, double>(Exec&, const double*, int, int, long, QRTreeT<float>&);
+template void tsqr2<double, double>(Exec&, const double*, int, long, const double*, int, long, int,
+                                    QRTreeT<double>&, QRTreeT<double>&);
+template void tsqr2<float, double>(Exec&, const double*, int, long, const double*, int, long, int, QRTreeT<float>&,
+                                   QRTreeT<float>&);
+template void tsqr_apply2<double, double, double>(Exec&, const QRTreeT<double>&, const double*, long, double*, long,
+                                                  const QRTreeT<double>&, const double*, long, double*, long, int);
+template void tsqr_apply2<float, double, double>(Exec&, const QRTreeT<float>&, const double*, long, double*, long,
+                                                 const QRTreeT<float>&, const double*, long, double*, long, int);
+template void tsqr_apply<double, double, double>(Exec&, const QRTreeT<double>&, const double*, int, long, double*,
+                                                 long);
+template void tsqr_apply<float, float, float>(Exec&, const QRTreeT<float>&, const float*, int, long, float*, long);
+template void tsqr_apply<float, double, double>(Exec&, const QRTreeT<float>&, const double*, int, long, double*,
+                                                long);
 
 // ============================================================== small SVD
 // SVD of a p x p matrix M (p <= 112) in one CTA, all in shared memory:
@@ -993,8 +1199,11 @@ void jacobi_svd(Exec& ex, const double* M, int p, double tol, int cap, double* U
   if (ex.dry) return;
   const size_t smem = 2 * (size_t)p * p * 8;
   smem_attr_once(k_svd_small);
-  // deflation level: far below the truncation tolerance and the 1e-10 parity bar
-  const double defl = std::max(std::min(1e-13, 1e-2 * tol), 1e-15);
+  // deflation level: far below the truncation tolerance and the 1e-10 parity
+  // bar on the FP64 path; the precision forms' cores carry FP32 round-off
+  // (~1e-7 relative), so there it deflates at 1e-2 of their tolerance
+  const double defl = ex.precision == TT_FP64 ? std::max(std::min(1e-13, 1e-2 * tol), 1e-15)
+                                              : std::max(1e-2 * tol, 1e-13);
   // algorithmic work: pivoted QR (4/3 p^3) plus a nominal 3 Jacobi sweeps
   TT_KERNEL(ex, K_JACOBI, 4.0 / 3.0 * p * (double)p * p + 3.0 * (p * (p - 1) / 2.0) * 18.0 * p,
             8.0 * 4.0 * p * (double)p,

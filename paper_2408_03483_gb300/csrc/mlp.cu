@@ -11,12 +11,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "tt_ops.cuh"
 
 namespace ttfv {
 
-constexpr int MLP_F = 12;
+constexpr int MLP_F = 14;
 constexpr int MLP_H = 256;
 
 namespace {
@@ -181,7 +182,7 @@ __global__ void k_feat_stats(const double* __restrict__ raw, int n2, double* __r
   }
 }
 __global__ void k_feat_fill(const double* __restrict__ raw, const double* __restrict__ st, int n2,
-                            float* __restrict__ X) {
+                            const int* __restrict__ prev, int nprev, float* __restrict__ X) {
   const double* lev = raw;
   const double* c = raw + n2;
   const double* e = raw + 2 * n2;
@@ -205,6 +206,16 @@ __global__ void k_feat_fill(const double* __restrict__ raw, const double* __rest
     f[9] = e[j] / me;
     f[10] = sin(ang);
     f[11] = cos(ang);
+    // previous converged pivots of the same cross site: indicator and
+    // periodic distance, capped at 8 (1 when there are none)
+    int dmin = 8;
+    for (int q = 0; q < nprev; ++q) {
+      int dd = abs(j - prev[q]);
+      dd = min(dd, n2 - dd);
+      dmin = min(dmin, dd);
+    }
+    f[12] = (nprev > 0 && dmin == 0) ? 1.0 : 0.0;
+    f[13] = dmin / 8.0;
 #pragma unroll
     for (int q = 0; q < MLP_F; ++q) X[j + (size_t)q * n2] = (float)f[q];
   }
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(1024) k_topk(const float* __restrict__ s, int 
 }  // namespace
 
 // ------------------------------------------------------------------ host side
-void mlp_features(Exec& ex, const TT& x0, float* X) {
+void mlp_features(Exec& ex, const TT& x0, const int* prev, int nprev, float* X) {
   const int n1 = x0.n1, n2 = x0.n2, r = x0.r;
   TT_REQUIRE(r >= 1 && r <= 112 && n2 >= 1, TT_ERR_ARG);
   Scope sc(*ex.ar);
@@ -309,8 +320,8 @@ void mlp_features(Exec& ex, const TT& x0, float* X) {
   TT_KERNEL(ex, K_OTHER, 6.0 * n2 * r, 8.0 * (3.0 * n2 * r + 3.0 * n2),
             k_feat_raw<<<grid_for(n2), 256, 0, ex.s>>>(Q, x0.b, BG, amean, n2, r, raw));
   TT_KERNEL(ex, K_OTHER, 8.0 * n2, 16.0 * n2, k_feat_stats<<<1, 1024, 0, ex.s>>>(raw, n2, st));
-  TT_KERNEL(ex, K_OTHER, 20.0 * n2, 24.0 * n2 + 48.0 * n2,
-            k_feat_fill<<<grid_for(n2), 256, 0, ex.s>>>(raw, st, n2, X));
+  TT_KERNEL(ex, K_OTHER, 20.0 * n2 + 3.0 * n2 * nprev, 24.0 * n2 + 56.0 * n2,
+            k_feat_fill<<<grid_for(n2), 256, 0, ex.s>>>(raw, st, n2, prev, nprev, X));
 }
 
 // Cached activations of a forward pass over m rows
@@ -399,12 +410,26 @@ void mlp_topk(Exec& ex, const float* s, int m, int k, int* idx) {
   TT_KERNEL(ex, K_OTHER, (double)m * k, 8.0 * m, k_topk<<<1, 1024, 0, ex.s>>>(s, m, k, work, idx));
 }
 
+// Previous pivots (host) copied to a device array of the arena
+static const int* upload_prev(Exec& ex, const std::vector<int>& prev) {
+  int* d = ex.ar->get<int>(std::max<size_t>(prev.size(), 1));
+  if (!ex.dry && !prev.empty())
+    TT_CUDA(cudaMemcpyAsync(d, prev.data(), sizeof(int) * prev.size(), cudaMemcpyHostToDevice, ex.s));
+  return d;
+}
+
+void mlp_features_host_prev(Exec& ex, const TT& x0, const std::vector<int>& prev, float* X) {
+  Scope sc(*ex.ar);
+  const int* dprev = upload_prev(ex, prev);
+  mlp_features(ex, x0, dprev, (int)prev.size(), X);
+}
+
 // Column pivots proposed by the network for a cross whose initial TT is x0
-void mlp_propose(Exec& ex, const MlpNet& net, const TT& x0, int k, int* idx) {
+void mlp_propose(Exec& ex, const MlpNet& net, const TT& x0, const std::vector<int>& prev, int k, int* idx) {
   Scope sc(*ex.ar);
   float* X = ex.ar->get<float>((size_t)x0.n2 * MLP_F);
   float* s = ex.ar->get<float>((size_t)x0.n2);
-  mlp_features(ex, x0, X);
+  mlp_features_host_prev(ex, x0, prev, X);
   mlp_forward(ex, net, X, x0.n2, s);
   mlp_topk(ex, s, x0.n2, k, idx);
 }

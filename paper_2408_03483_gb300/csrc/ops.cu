@@ -309,15 +309,7 @@ static const double* as_double(Exec& ex, const Real* X, long n) {
 // Q [C; 0] into the FP64 core Out (m x k, ld m)
 template <typename Real>
 static void apply_to_core(Exec& ex, const QRTreeT<Real>& t, const double* C, int k, long ldc, double* Out) {
-  if constexpr (std::is_same<Real, double>::value) {
-    tsqr_apply(ex, t, C, k, ldc, Out, (long)t.m);
-  } else {
-    Scope sc(*ex.ar);
-    const Real* Cr = as_real<Real>(ex, C, ldc * k);
-    Real* O = ex.ar->get<Real>((size_t)t.m * k);
-    tsqr_apply(ex, t, Cr, k, ldc, O, (long)t.m);
-    convert(ex, Out, O, (long)t.m * k);
-  }
+  tsqr_apply(ex, t, C, k, ldc, Out, (long)t.m);  // FP32 trees read C and write Out in FP64
 }
 
 // Working-precision product C = alpha A B + beta C of the rounding routes:
@@ -383,11 +375,10 @@ template <typename Real>
 static RoundInfo round_factored(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol,
                                 int cap, TT& Y) {
   Scope sc(*ex.ar);
-  const Real* Ar = as_real<Real>(ex, A, (long)n1 * R);
-  const Real* Br = as_real<Real>(ex, B, (long)n2 * R);
+  // both cores factored side by side in shared launches (FP32 leaves
+  // convert the FP64 cores on load)
   QRTreeT<Real> ta, tb;
-  tsqr(ex, Ar, n1, R, n1, ta);
-  tsqr(ex, Br, n2, R, n2, tb);
+  tsqr2(ex, A, n1, (long)n1, B, n2, (long)n2, R, ta, tb);
   Real* Mr = ex.ar->get<Real>((size_t)R * R);
   // M = R_A R_B^T
   gemm<Real>(ex, R, R, R, Real(1), ta.R, 1, R, tb.R, R, 1, Real(0), Mr, R);
@@ -403,8 +394,8 @@ static RoundInfo round_factored(Exec& ex, const double* A, const double* B, int 
   if (ex.dry) k = std::min(cap, R);
   double tl[2];
   fetch_doubles(ex, tail, 2, tl);
-  apply_to_core(ex, ta, US, k, R, Y.a);
-  apply_to_core(ex, tb, V, k, R, Y.b);
+  tsqr_apply2(ex, ta, (const double*)US, (long)R, Y.a, (long)Y.n1, tb, (const double*)V, (long)R, Y.b,
+              (long)Y.n2, k);
   Y.r = k;
   finish_counts(ex, k, cap, R);
   return RoundInfo{k, tl[0], tl[1], 0.0};

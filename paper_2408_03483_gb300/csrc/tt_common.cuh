@@ -220,11 +220,21 @@ struct QRTreeT {
   Real* R = nullptr;         // final p x p upper triangle (ld p)
 };
 using QRTree = QRTreeT<double>;
-template <typename Real>
-void tsqr(Exec& ex, const Real* X, int m, int p, long ldx, QRTreeT<Real>& t);
-// Out (m x k, ld ldo) = Q [C; 0] with C p x k (ld ldc).
-template <typename Real>
-void tsqr_apply(Exec& ex, const QRTreeT<Real>& t, const Real* C, int k, long ldc, Real* Out, long ldo);
+// (X may be FP64 for an FP32 factorisation: the leaves convert on load.)
+template <typename Real, typename Src>
+void tsqr(Exec& ex, const Src* X, int m, int p, long ldx, QRTreeT<Real>& t);
+// Out (m x k, ld ldo) = Q [C; 0] with C p x k (ld ldc); C and Out may be FP64
+// around an FP32 factorisation (converted on load / store).
+template <typename Real, typename ZT, typename OT>
+void tsqr_apply(Exec& ex, const QRTreeT<Real>& t, const ZT* C, int k, long ldc, OT* Out, long ldo);
+// The two factorisations (and the two applications) of a rounding in shared
+// launches: same column count p, independent matrices.
+template <typename Real, typename Src>
+void tsqr2(Exec& ex, const Src* X1, int m1, long ldx1, const Src* X2, int m2, long ldx2, int p, QRTreeT<Real>& t1,
+           QRTreeT<Real>& t2);
+template <typename Real, typename ZT, typename OT>
+void tsqr_apply2(Exec& ex, const QRTreeT<Real>& t1, const ZT* C1, long ldc1, OT* Out1, long ldo1,
+                 const QRTreeT<Real>& t2, const ZT* C2, long ldc2, OT* Out2, long ldo2, int k);
 
 // One-sided Jacobi SVD of a square p x p matrix M (ld p, p <= 112).  Writes
 // the singular values sorted descending to sig (device, p), U*S (p x p, ld p)

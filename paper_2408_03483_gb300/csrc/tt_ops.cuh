@@ -63,6 +63,9 @@ struct CrossFn {
   const TT* in = nullptr;
   int nin = 0;
   double prm[4] = {0, 0, 0, 0};
+  // the call site's converged column pivots of the previous stage (read by
+  // the learned start, rewritten on exit); null: no memory
+  std::vector<int>* site = nullptr;
 };
 int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, int cap, int kick,
           int max_sweeps, unsigned seed, TT& y);
@@ -71,18 +74,20 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
 // mode of x0; scores s of m rows; gradients of the mean logistic loss into g
 // (same shapes as the parameters) and the loss into *loss (device, may be
 // null); one Adam step of the FP32 masters; top-k indices ascending.
-constexpr int kMlpFeatures = 12;
+constexpr int kMlpFeatures = 14;
 constexpr int kMlpHidden = 256;
-void mlp_features(Exec& ex, const TT& x0, float* X);
+// prev: device array of the site's previous converged pivots (nprev entries)
+void mlp_features(Exec& ex, const TT& x0, const int* prev, int nprev, float* X);
+void mlp_features_host_prev(Exec& ex, const TT& x0, const std::vector<int>& prev, float* X);
 void mlp_forward(Exec& ex, const MlpNet& net, const float* X, int m, float* s);
 void mlp_grad(Exec& ex, const MlpNet& net, const float* X, const float* y, int m, const MlpNet& g, double* loss);
 void mlp_adam(Exec& ex, const MlpNet& p, const MlpNet& g, const MlpNet& m1, const MlpNet& m2, int t, float lr);
 void mlp_topk(Exec& ex, const float* s, int m, int k, int* idx);
-void mlp_propose(Exec& ex, const MlpNet& net, const TT& x0, int k, int* idx);
+void mlp_propose(Exec& ex, const MlpNet& net, const TT& x0, const std::vector<int>& prev, int k, int* idx);
 
 // Training-data capture (fv.cu): features of x0's column mode with a 0/1
 // label per index (1: in the converged column pivot set J).
-void record_pivots(Exec& ex, const TT& x0, const std::vector<int>& J);
+void record_pivots(Exec& ex, const TT& x0, const std::vector<int>& prev, const std::vector<int>& J);
 
 // Linear reconstruction on cores (fv.cu)
 void recon_linear(Exec& ex, const TT& x, int direction, int scheme, TT& qm, TT& qp);

@@ -53,7 +53,7 @@ def _init_params(seed):
         lim = np.sqrt(6.0 / fan_in)
         return rng.uniform(-lim, lim, size=shape).astype(np.float32)
 
-    return dict(W1=u(12, (12, 256)), b1=np.zeros(256, np.float32), W2=u(256, (256, 256)),
+    return dict(W1=u(14, (14, 256)), b1=np.zeros(256, np.float32), W2=u(256, (256, 256)),
                 b2=np.zeros(256, np.float32), w3=u(256, (256,)), b3=np.zeros(1, np.float32))
 
 

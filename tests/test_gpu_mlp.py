@@ -95,12 +95,12 @@ def test_adam_matches_oracle(api):
 
 def test_features_match_oracle(api):
     rng = np.random.default_rng(11)
-    for n1, n2, r in ((40, 300, 6), (64, 97, 1), (200, 768, 12)):
+    for n1, n2, r, prev in ((40, 300, 6, [0, 17, 299]), (64, 97, 1, []), (200, 768, 12, [5, 6, 400, 767])):
         A = rng.standard_normal((n1, r))
         B = rng.standard_normal((n2, r)) * (0.7 ** np.arange(r))
         x0 = api.DevTT.from_cores(A, B)
-        got = api.tt_mlp_features(x0).cpu().numpy()
-        ref = M.features(A, B)
+        got = api.tt_mlp_features(x0, prev).cpu().numpy()
+        ref = M.features(A, B, prev)
         assert np.allclose(got, ref, rtol=1e-5, atol=1e-5), np.max(np.abs(got - ref))
 
 
