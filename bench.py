@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"],
                     help="working precision of the rounding contractions (fp64: the plain path)")
+    ap.add_argument("--pivots", default="maxvol", choices=["maxvol", "learned"],
+                    help="cross start: maxvol of the initial TT, or the shipped learned network")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     return ap.parse_args()
@@ -200,11 +202,15 @@ def run_ours(args):
     n, cap = w["n"], w["cap"]
     Q, p = make_state(w, cap)
     stream = torch.cuda.current_stream()
+    net = api.PivotNet.shipped() if args.pivots == "learned" else None
 
     def new_solver(state):
         q0 = [api.DevTT.from_cores(A, B, cap=cap) for A, B in state]
-        return api.Solver(q0, w["eqn"], w["scheme"], n, p["dt"], w["tol"], cap, g=p["g"], H=p["H"], f=p["f"],
-                          kick=4, max_sweeps=10, max_iter=50, seed=0, precision=args.precision)
+        s = api.Solver(q0, w["eqn"], w["scheme"], n, p["dt"], w["tol"], cap, g=p["g"], H=p["H"], f=p["f"],
+                       kick=4, max_sweeps=10, max_iter=50, seed=0, precision=args.precision, pivots=args.pivots)
+        if args.pivots == "learned":
+            s.set_pivot_net(net)
+        return s
 
     # ---- parity sample: first step from the initial state vs the oracle
     s0 = new_solver(Q)
@@ -251,8 +257,13 @@ def run_ours(args):
         s.step(1)
     prof = s.kernel_profile(reset=True)
     s.profile(False)
-    ranks_after = s.stats()["rank"]
-    dev_status = s.stats()["device_status"]
+    st_all = s.stats()
+    ranks_after = st_all["rank"]
+    dev_status = st_all["device_status"]
+    cross_info = {"calls": st_all["cross_calls"], "sweeps": st_all["cross_sweeps"],
+                  "sweeps_per_call": st_all["cross_sweeps"] / max(st_all["cross_calls"], 1),
+                  "learned_calls": st_all["learned_calls"], "learned_accepted": st_all["learned_accepted"],
+                  "window": "all steps of the timed solver (warm-up, timed, profile)"}
     total_ms = sum(step_ms)
     if world > 1:
         import torch.distributed as dist
@@ -321,11 +332,11 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "scheme": w["scheme"], "eqn": w["eqn"],
-                       "precision": args.precision,
+                       "precision": args.precision, "pivots": args.pivots,
                        "rank_cap": cap, "tol": w["tol"], "steps_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
                        "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
             "clocks": clk, "gpu_launches": launches, "roofline": roofline, "kernel_classes": classes,
-            "ranks_after": ranks_after, "device_status": dev_status, "wall_s_timed": wall,
+            "ranks_after": ranks_after, "device_status": dev_status, "cross": cross_info, "wall_s_timed": wall,
             "e2e": {"value": n * n * args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                     "d2h_bytes_per_step": d2h // args.steps}}
     # ---- CPU oracle baseline and the parity of the first step

@@ -348,6 +348,16 @@ class PivotNet:
         self.m2 = {k: torch.zeros_like(v) for k, v in self.p.items()}
         self.t = 0
 
+    @classmethod
+    def shipped(cls, device="cuda"):
+        """The network trained by train_pivots.py on plain-cross pivots of
+        seeded 128^2 and 256^2 WENO5 runs (pivot_net.npz beside this file)."""
+        import os
+        import numpy as np
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "pivot_net.npz")
+        with np.load(path) as f:
+            return cls({k: f[k] for k in cls.NAMES}, device=device)
+
     def load(self, params):
         for k in self.NAMES:
             self.p[k].copy_(torch.as_tensor(params[k], dtype=torch.float32).reshape(self.SHAPES[k]))

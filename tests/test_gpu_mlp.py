@@ -167,3 +167,31 @@ def test_recording_captures_labelled_rows(api):
     assert np.all(np.isfinite(X)) and set(np.unique(y)) <= {0.0, 1.0} and y.sum() > 0
     assert y.shape[0] >= st["cross_calls"] * w["n"]
     s.close()
+
+
+def test_shipped_network_gain_over_plain_maxvol(api):
+    # the trained network (train_pivots.py, seeds 20000+) on held-out 256^2
+    # WENO5 instances: fewer cross sweeps than the plain maxvol start, and the
+    # same accuracy class against the exact full-tensor stage
+    import importlib
+    tp = importlib.import_module("paper_2408_03483_gb300.train_pivots")
+    net = api.PivotNet.shipped()
+    sweeps = {"maxvol": 0, "learned": 0}
+    for seed in (30000, 30003):
+        w, Q, p = tp.instance(256, seed)
+        for mode in ("maxvol", "learned"):
+            s = tp.solver(api, w, Q, p, pivots=mode)
+            if mode == "learned":
+                s.set_pivot_net(net)
+            s.step(1)  # stages 1 and 2 start from the site pivots of the stage before
+            st = s.stats()
+            sweeps[mode] += st["cross_sweeps"]
+            if mode == "learned":
+                assert st["learned_calls"] == st["cross_calls"] > 0
+                got = s.get()
+                ref = FA.ssprk3_step([T.full(q) for q in Q], "nonlinear", "weno5", p, p["dt"])
+                scale = np.linalg.norm(ref[0])
+                for c in range(3):  # the WENO5 bar per stage, three stages
+                    assert np.linalg.norm(got[c].full().numpy() - ref[c]) <= 3 * 10 * w["tol"] * scale
+            s.close()
+    assert sweeps["learned"] < sweeps["maxvol"], sweeps
