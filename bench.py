@@ -44,6 +44,8 @@ def parse():
                     help="working precision of the rounding contractions (fp64: the plain path)")
     ap.add_argument("--pivots", default="maxvol", choices=["maxvol", "learned"],
                     help="cross start: maxvol of the initial TT, or the shipped learned network")
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="ensemble workloads: also time the one-instance-at-a-time path on the same steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     return ap.parse_args()
@@ -378,7 +380,7 @@ def run_ensemble(args):
         insts.append((q0, dict(eqn=w["eqn"], scheme=w["scheme"], n=w["n"], dt=p["dt"], tol=w["tol"],
                                rank_cap=w["cap"], g=p["g"], H=p["H"], f=p["f"], seed=0)))
     cells = sum(w["n"] ** 2 for w in ws)
-    prec = args.precision if args.precision != "fp64" else "fp64"
+    prec = args.precision
     b = api.Batch(insts, precision=prec, workers=8)
     stream = torch.cuda.current_stream()
     # warm-up = the autotuner's trials: one step per (workers, inner tasks)
@@ -409,10 +411,28 @@ def run_ensemble(args):
         total_ms = float(t.item())
     dev = max(b.stats(i)["device_status"] for i in range(count))
     b.close()
+    # the plain path on the same steps: one instance at a time with its own
+    # stage tasks, advanced through the same warm-up steps first
+    plain_ms = None
+    if args.compare_plain:
+        insts2 = []
+        for w in ws:
+            Q, p = initial_tt(w)
+            q0 = [api.DevTT.from_cores(A, B, cap=w["cap"]) for A, B in Q]
+            insts2.append((q0, dict(eqn=w["eqn"], scheme=w["scheme"], n=w["n"], dt=p["dt"], tol=w["tol"],
+                                    rank_cap=w["cap"], g=p["g"], H=p["H"], f=p["f"], seed=0)))
+        b2 = api.Batch(insts2, precision=prec, workers=1, inner_tasks=True)
+        b2.step(2 * len(cands))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b2.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        b2.close()
     if rank != 0:
         return
     value = cells * args.steps * world / (total_ms / 1e3)
-    plain = rates.get((1, True))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": 2 * len(cands), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
@@ -424,7 +444,9 @@ def run_ensemble(args):
                        "parallelism": "replicas"},
             "tuned": {"workers": bw, "inner_tasks": bi,
                       "trial_rates": {f"w{w}_{'inner' if i else 'flat'}": r for (w, i), r in rates.items()}},
-            "vs_one_instance_at_a_time": (value / world / plain) if plain else None,
+            "plain_same_steps": ({"ms_per_step": plain_ms / args.steps, "speedup": plain_ms / total_ms,
+                                  "what": "workers=1 with stage tasks (the single-instance path), same steps"}
+                                 if plain_ms else None),
             "clocks": clk, "gpu_launches": launches, "device_status": dev}
     print(json.dumps(line), flush=True)
 

@@ -1,9 +1,11 @@
-// Learned-pivot network: a 3-layer perceptron (12 -> 256 -> 256 -> 1) that
+// Learned-pivot network: a 3-layer perceptron (14 -> 256 -> 256 -> 1) that
 // scores the column indices of a cross from features of the cross's initial
-// TT; its top-scoring indices seed the maxvol sweeps.  Forward and backward
-// products run on the tcgen05 tensor cores with BF16 operands and FP32
-// accumulation (tc_gemm, one part); biases, activations, the logistic loss
-// and the Adam update are FP32 elementwise kernels.
+// TT and of the call site's previous pivots; its top-scoring indices seed the
+// maxvol sweeps.  Training products (forward and backward) run on the
+// tcgen05 tensor cores with BF16 operands and FP32 accumulation (tc_gemm, one
+// part); scoring for a cross uses one fused CUDA-core kernel with the same
+// BF16-operand products; biases, activations, the logistic loss and the Adam
+// update are FP32 elementwise kernels.
 //
 // Layouts: activations and features are column-major m x width (ld m);
 // W1 (12 x 256) and W2 (256 x 256) are row-major (W[in * 256 + out]).
@@ -295,6 +297,66 @@ __global__ void __launch_bounds__(1024) k_topk(const float* __restrict__ s, int 
   }
 }
 
+// Fused scoring of a tile of 32 rows per CTA, one thread per hidden unit:
+// the same products as the tensor-core passes (operands rounded to BF16,
+// FP32 accumulation), with both hidden layers kept in shared memory -- the
+// cross's proposals score a few hundred to a few thousand rows, where one
+// launch beats a chain of GEMM launches.
+constexpr int INF_ROWS = 32;
+__global__ void __launch_bounds__(MLP_H) k_mlp_infer(const float* __restrict__ X, int m,
+                                                     const float* __restrict__ W1, const float* __restrict__ b1,
+                                                     const float* __restrict__ W2, const float* __restrict__ b2,
+                                                     const float* __restrict__ w3, const float* __restrict__ b3,
+                                                     float* __restrict__ s) {
+  __shared__ float xs[INF_ROWS][MLP_F];
+  __shared__ float hs[INF_ROWS][MLP_H + 1];
+  const int h = threadIdx.x, r0 = blockIdx.x * INF_ROWS;
+  const int nr = min(INF_ROWS, m - r0);
+  for (int t = threadIdx.x; t < INF_ROWS * MLP_F; t += blockDim.x) {
+    const int r = t % INF_ROWS, f = t / INF_ROWS;
+    xs[r][f] = r < nr ? bf16r(X[(r0 + r) + (size_t)f * m]) : 0.0f;
+  }
+  __syncthreads();
+  // layer 1: unit h over the tile's rows
+  float w1[MLP_F];
+#pragma unroll
+  for (int f = 0; f < MLP_F; ++f) w1[f] = bf16r(W1[f * MLP_H + h]);
+  const float bb1 = b1[h];
+  for (int r = 0; r < INF_ROWS; ++r) {
+    float z = 0.0f;
+#pragma unroll
+    for (int f = 0; f < MLP_F; ++f) z = fmaf(xs[r][f], w1[f], z);
+    z += bb1;
+    hs[r][h] = bf16r(z > 0.0f ? z : 0.0f);
+  }
+  __syncthreads();
+  // layer 2: unit h of the second layer, W2 column h streamed from L2
+  float acc[INF_ROWS];
+#pragma unroll
+  for (int r = 0; r < INF_ROWS; ++r) acc[r] = 0.0f;
+  for (int k = 0; k < MLP_H; ++k) {
+    const float w = bf16r(W2[(size_t)k * MLP_H + h]);
+#pragma unroll
+    for (int r = 0; r < INF_ROWS; ++r) acc[r] = fmaf(hs[r][k], w, acc[r]);
+  }
+  __syncthreads();
+  // layer 3: per-row dot with w3 through shared memory
+  const float ww3 = bf16r(w3[h]), bb2 = b2[h];
+#pragma unroll
+  for (int r = 0; r < INF_ROWS; ++r) {
+    const float z = acc[r] + bb2;
+    hs[r][h] = bf16r(z > 0.0f ? z : 0.0f) * ww3;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int r = wp; r < nr; r += MLP_H / 32) {
+    float v = 0.0f;
+    for (int k = lane; k < MLP_H; k += 32) v += hs[r][k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s[r0 + r] = v + b3[0];
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host side
@@ -350,9 +412,11 @@ static MlpActs mlp_forward_acts(Exec& ex, const MlpNet& net, const float* X, int
 }
 
 void mlp_forward(Exec& ex, const MlpNet& net, const float* X, int m, float* s) {
-  Scope sc(*ex.ar);
-  MlpActs a = mlp_forward_acts(ex, net, X, m);
-  if (!ex.dry) TT_CUDA(cudaMemcpyAsync(s, a.s, sizeof(float) * m, cudaMemcpyDeviceToDevice, ex.s));
+  if (ex.dry || m <= 0) return;
+  TT_KERNEL(ex, K_OTHER, 2.0 * m * (double)MLP_H * (MLP_F + MLP_H + 1),
+            4.0 * ((double)m * (MLP_F + 1) + ceil_div(m, INF_ROWS) * (double)MLP_H * (MLP_F + MLP_H + 3)),
+            k_mlp_infer<<<ceil_div(m, INF_ROWS), MLP_H, 0, ex.s>>>(X, m, net.W1, net.b1, net.W2, net.b2, net.w3,
+                                                                    net.b3, s));
 }
 
 void mlp_grad(Exec& ex, const MlpNet& net, const float* X, const float* y, int m, const MlpNet& g,
