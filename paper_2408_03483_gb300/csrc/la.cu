@@ -867,6 +867,8 @@ template void tsqr_apply<float, double, double>(Exec&, const QRTreeT<float>&, co
 //  3. singular values = column norms, sorted; outputs P (L V) and Q V.
 constexpr int SVD_THREADS = 1024;
 constexpr int SVD_MAX_SWEEPS = 30;
+constexpr int SVD_MIXED_MIN = 8;      // FP32 pre-rotation from this deflated rank up
+constexpr int SVD_MIXED_SWEEPS = 12;  // cap of FP32 sweeps
 
 __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restrict__ Min, int p, double tol, int cap,
                                                           double defl, double* US, double* Vout, double* sig,
@@ -880,10 +882,14 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   __shared__ int piv[128];
   __shared__ int order[128];
   __shared__ double s_tau, s_fro2, s_trail;
-  __shared__ int s_jmax, s_stop, s_rot, s_k;
+  __shared__ int s_jmax, s_stop, s_rot, s_k, s_tmax;
+  __shared__ float cnf[128];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* HV = scr;                  // Householder vectors, p x p
   double* htau = scr + (size_t)p * p;
+  double* Vg = htau + p;             // pre-rotation scratch: pd x pd
+  double* Gg = Vg + (size_t)p * p;   // pd x pd
+  double* Tg = Gg + (size_t)p * p;   // p x pd
 
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
     const int i = t % p, j = t / p;
@@ -1049,6 +1055,106 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) J[t] = ((t % pd) == (t / pd)) ? 1.0 : 0.0;
   __syncthreads();
   const int q = pd + (pd & 1);
+  // ---- 2a. FP32 pre-rotation.  One-sided Jacobi sweeps on an FP32 copy of L
+  // (FP32 instructions cost 1/64 of FP64 ones here) orthogonalise its columns
+  // to FP32 level; the accumulated rotations V0 are re-orthonormalised in FP64
+  // (two Newton-Schulz steps V <- V (3 I - V^T V) / 2) and L <- L V0.  The
+  // FP64 sweeps below then start from near-orthogonal columns, where they
+  // converge in one or two sweeps; their result is the FP64 SVD whatever V0.
+  if (pd >= SVD_MIXED_MIN) {
+    float* Af = reinterpret_cast<float*>(J);  // p x pd floats, then pd x pd
+    float* Jf = Af + (size_t)p * pd;          // fits: J holds p*p doubles
+    // a power-of-two scale keeps the FP32 copy in range (rotations do not
+    // depend on the scale)
+    const double fscale = ldexp(1.0, -ilogb(sqrt(fro2)));
+    for (int t = threadIdx.x; t < p * pd; t += blockDim.x) Af[t] = (float)(A[t] * fscale);
+    for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) Jf[t] = ((t % pd) == (t / pd)) ? 1.0f : 0.0f;
+    __syncthreads();
+    const float epsf = 4.0f * FLT_EPSILON;
+    for (int sw = 0; sw < SVD_MIXED_SWEEPS; ++sw) {
+      for (int j = w; j < pd; j += nw) {
+        float sq = 0.0f;
+        for (int r = lane; r < p; r += 32) sq = fmaf(Af[r + (size_t)j * p], Af[r + (size_t)j * p], sq);
+        sq = warp_sum(sq);
+        if (lane == 0) cnf[j] = sq;
+      }
+      if (threadIdx.x == 0) s_rot = 0;
+      __syncthreads();
+      for (int step = 0; step < q - 1; ++step) {
+        for (int pr = w; pr < q / 2; pr += nw) {
+          const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
+          const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
+          if (i >= pd || j >= pd) continue;
+          float* ci = Af + (size_t)i * p;
+          float* cj = Af + (size_t)j * p;
+          float ga = 0.0f;
+          for (int r = lane; r < p; r += 32) ga = fmaf(ci[r], cj[r], ga);
+          ga = warp_sum(ga);
+          const float al = cnf[i], be = cnf[j];
+          if (!(ga * ga > epsf * epsf * al * be)) continue;
+          float c = 1.0f, sn = 0.0f;
+          if (lane == 0) {
+            const float dd = be - al;
+            const float t = (dd >= 0.0f ? 2.0f * ga : -2.0f * ga) / (fabsf(dd) + sqrtf(fmaf(dd, dd, 4.0f * ga * ga)));
+            c = rsqrtf(fmaf(t, t, 1.0f));
+            sn = c * t;
+            cnf[i] = fmaf(-t, ga, al);
+            cnf[j] = fmaf(t, ga, be);
+          }
+          c = __shfl_sync(0xffffffffu, c, 0);
+          sn = __shfl_sync(0xffffffffu, sn, 0);
+          for (int r = lane; r < p; r += 32) {
+            const float x = ci[r], y = cj[r];
+            ci[r] = c * x - sn * y;
+            cj[r] = sn * x + c * y;
+          }
+          float* vi = Jf + (size_t)i * pd;
+          float* vj = Jf + (size_t)j * pd;
+          for (int r = lane; r < pd; r += 32) {
+            const float x = vi[r], y = vj[r];
+            vi[r] = c * x - sn * y;
+            vj[r] = sn * x + c * y;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+        __syncthreads();
+      }
+      if (s_rot == 0) break;
+      __syncthreads();
+    }
+    // V0 in FP64 (global scratch), two Newton-Schulz steps back into J
+    for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) Vg[t] = (double)Jf[t];
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+      const double* Vs = (it == 0) ? Vg : J;
+      double* Vd = (it == 0) ? J : Vg;
+      for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) {  // G = V^T V
+        const int a = t % pd, b = t / pd;
+        double g = 0.0;
+        for (int r = 0; r < pd; ++r) g = fma(Vs[r + (size_t)a * pd], Vs[r + (size_t)b * pd], g);
+        Gg[t] = g;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) {  // Vd = 1.5 V - 0.5 V G
+        const int r = t % pd, b = t / pd;
+        double u = 0.0;
+        for (int a = 0; a < pd; ++a) u = fma(Vs[r + (size_t)a * pd], Gg[a + (size_t)b * pd], u);
+        Vd[t] = fma(-0.5, u, 1.5 * Vs[t]);
+      }
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) J[t] = Vg[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < p * pd; t += blockDim.x) {  // T = L V0
+      const int r = t % p, b = t / p;
+      double u = 0.0;
+      for (int a = 0; a < pd; ++a) u = fma(A[r + (size_t)a * p], J[a + (size_t)b * pd], u);
+      Tg[t] = u;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < p * pd; t += blockDim.x) A[t] = Tg[t];
+    __syncthreads();
+  }
   const double eps = DBL_EPSILON * p, eps2 = eps * eps;
   int sweep = 0;
   for (; sweep < SVD_MAX_SWEEPS && pd > 1; ++sweep) {
@@ -1060,7 +1166,10 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
       sq = warp_sum(sq);
       if (lane == 0) cn[j] = sq;
     }
-    if (threadIdx.x == 0) s_rot = 0;
+    if (threadIdx.x == 0) {
+      s_rot = 0;
+      s_tmax = 0;
+    }
     __syncthreads();
     for (int step = 0; step < q - 1; ++step) {
       for (int pr = w; pr < q / 2; pr += nw) {
@@ -1083,6 +1192,8 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
           sn = c * t;
           cn[i] = fma(-t, ga, al);
           cn[j] = fma(t, ga, be);
+          // |t| as its float bit pattern: non-negative floats order like ints
+          atomicMax(&s_tmax, __float_as_int(fminf((float)fabs(t), 1.0f)));
         }
         c = __shfl_sync(0xffffffffu, c, 0);
         sn = __shfl_sync(0xffffffffu, sn, 0);
@@ -1103,6 +1214,13 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
       __syncthreads();
     }
     if (s_rot == 0) break;
+    // every rotation of this sweep was below 1e-7: quadratic convergence puts
+    // the remaining off-diagonal at ~1e-14 relative, so the confirming sweep
+    // (which would rotate nothing above the threshold) is skipped
+    if (__int_as_float(s_tmax) < 1e-7f) {
+      ++sweep;
+      break;
+    }
     __syncthreads();
   }
   // ---- 3. singular values, order, truncation
@@ -1195,7 +1313,7 @@ void jacobi_svd(Exec& ex, const double* M, int p, double tol, int cap, double* U
                 int* k_out, double* tail_out) {
   TT_REQUIRE(p >= 1 && p <= 112, TT_ERR_ARG);
   Scope sc(*ex.ar);
-  double* scr = ex.ar->get<double>((size_t)p * p + p);
+  double* scr = ex.ar->get<double>((size_t)4 * p * p + p);
   if (ex.dry) return;
   const size_t smem = 2 * (size_t)p * p * 8;
   smem_attr_once(k_svd_small);
