@@ -51,6 +51,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x):
+    """The maximum of x over the ranks of the process group (x itself when
+    there is none): the job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, world, total_ms):
+    """Whole-job throughput of N independent replicas: the units all ranks
+    processed over the slowest rank's time."""
+    return units_per_rank * world / (total_ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -269,9 +288,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms)
         dist.barrier()
 
     # ---- end-to-end through the public API from pinned host buffers
@@ -306,7 +323,7 @@ def run_ours(args):
 
     if rank != 0:
         return
-    value = n * n * args.steps * world / (total_ms / 1e3)
+    value = replica_value(n * n * args.steps, world, total_ms)
     # ---- roofline of the dominant kernel class (FP64 ALU bound)
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
@@ -406,9 +423,7 @@ def run_ensemble(args):
     total_ms = ms
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms)
     dev = max(b.stats(i)["device_status"] for i in range(count))
     b.close()
     # the plain path on the same steps: one instance at a time with its own
@@ -432,7 +447,7 @@ def run_ensemble(args):
         b2.close()
     if rank != 0:
         return
-    value = cells * args.steps * world / (total_ms / 1e3)
+    value = replica_value(cells * args.steps, world, total_ms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": 2 * len(cands), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
