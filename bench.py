@@ -151,9 +151,15 @@ def traffic_for(kernel_class):
     src = os.path.join(ROOT, ent["source"])
     try:
         with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
+            text = f.read()
     except OSError:
         return None
+    # the hash covers the kernel's own section of the source file when the
+    # entry names its bounding markers, else the whole file
+    b, e = ent.get("begin", "").encode(), ent.get("end", "").encode()
+    if b and e and b in text and e in text:
+        text = text[text.index(b):text.index(e)]
+    h = hashlib.sha256(text).hexdigest()[:16]
     return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
 
 
@@ -248,6 +254,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+    sec0 = s.stats()["section_ms"]
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = api.launch_count()
@@ -269,6 +276,7 @@ def run_ours(args):
     torch.cuda.profiler.stop()
     launches = api.launch_count() - launches0
     clk = clocks.stop()
+    sec1 = s.stats()["section_ms"]
     # ---- per-kernel profile: further steps with every launch event-timed and
     # the independent tasks serialised (so each time is the kernel's own)
     prof_steps = max(1, min(args.steps, 2))
@@ -281,6 +289,9 @@ def run_ours(args):
     st_all = s.stats()
     ranks_after = st_all["rank"]
     dev_status = st_all["device_status"]
+    sections = {name: round((b - a) / args.steps, 2) for name, a, b in
+                zip(("faces", "side_fluxes_and_lambda", "llf", "quadrature_difference", "forward_euler",
+                     "ssp_combination"), sec0, sec1)}
     cross_info = {"calls": st_all["cross_calls"], "sweeps": st_all["cross_sweeps"],
                   "sweeps_per_call": st_all["cross_sweeps"] / max(st_all["cross_calls"], 1),
                   "learned_calls": st_all["learned_calls"], "learned_accepted": st_all["learned_accepted"],
@@ -355,7 +366,8 @@ def run_ours(args):
                        "rank_cap": cap, "tol": w["tol"], "steps_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
                        "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
             "clocks": clk, "gpu_launches": launches, "roofline": roofline, "kernel_classes": classes,
-            "ranks_after": ranks_after, "device_status": dev_status, "cross": cross_info, "wall_s_timed": wall,
+            "ranks_after": ranks_after, "device_status": dev_status, "cross": cross_info,
+            "section_host_ms_per_step": sections, "wall_s_timed": wall,
             "e2e": {"value": n * n * args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                     "d2h_bytes_per_step": d2h // args.steps}}
     # ---- CPU oracle baseline and the parity of the first step

@@ -403,24 +403,27 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, Merg
   }
   Real* T = sm;                       // block 0 (p x p)
   Real* part = sm + (size_t)ng * p * p;  // [slice][column] partial sums
-  __shared__ Real s_tau, s_vj, s_sig;
+  __shared__ Real s_tau, s_vj;
+  __shared__ Real s_nrm[QR_THREADS / 32];  // per-slice partial norms of the next column
   for (int t = threadIdx.x; t < ng * p * p; t += blockDim.x) T[t] = Ri[t];
   const int G = (p + 31) / 32;
   const int S = max(1, nw / G);
   const int grp = w % G, sl = w / G;
   const int c = grp * 32 + lane;  // this lane's column
   const bool active = (sl < S) && (c < p);
-  // norm below the diagonal of column 0: sum over bottoms of B_b[0,0]^2
+  // norm below the diagonal of column 0: B_b[0,0]^2 over this slice's bottoms
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (active && c == 0) {
     Real sg = Real(0);
-    for (int b = 1; b < ng; ++b) sg = fma(T[(size_t)b * p * p], T[(size_t)b * p * p], sg);
-    s_sig = sg;
+    for (int b = 1 + sl; b < ng; b += S) sg = fma(T[(size_t)b * p * p], T[(size_t)b * p * p], sg);
+    s_nrm[sl] = sg;
   }
   __syncthreads();
   for (int j = 0; j < p; ++j) {
     if (threadIdx.x == 0) {
-      const Real sg = s_sig, alpha = T[j + (size_t)j * p];
+      Real sg = Real(0);
+      for (int q = 0; q < S; ++q) sg += s_nrm[q];
+      const Real alpha = T[j + (size_t)j * p];
       Real tau = Real(0), vj = Real(0), beta = alpha;
       if (sg > Real(0) && fma(alpha, alpha, sg) >= hh_safe_norm<Real>() * hh_safe_norm<Real>()) {
         const Real nrm = sqrt(fma(alpha, alpha, sg));
@@ -462,25 +465,18 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, Merg
         }
       }
     }
-    __syncthreads();
-    // norm of column j+1 below its diagonal: bottoms' rows 0..j+1
-    if (j + 1 < p) {
-      if (active && c == j + 1) {
-        Real sg = Real(0);
-        for (int b = 1 + sl; b < ng; b += S) {
-          const Real* Bb = T + (size_t)b * p * p;
-          for (int i = 0; i <= j + 1; ++i) sg = fma(Bb[i + (size_t)c * p], Bb[i + (size_t)c * p], sg);
-        }
-        part[(size_t)sl * p + c] = sg;
+    // the thread of column j+1 in each slice continues with that column's
+    // norm below its diagonal (bottoms' rows 0..j+1) over its own bottoms;
+    // thread 0 adds the slices' partials at the start of the next column
+    if (active && c == j + 1) {
+      Real sg = Real(0);
+      for (int b = 1 + sl; b < ng; b += S) {
+        const Real* Bb = T + (size_t)b * p * p;
+        for (int i = 0; i <= j + 1; ++i) sg = fma(Bb[i + (size_t)c * p], Bb[i + (size_t)c * p], sg);
       }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        Real sg = Real(0);
-        for (int q = 0; q < S; ++q) sg += part[(size_t)q * p + j + 1];
-        s_sig = sg;
-      }
-      __syncthreads();
+      s_nrm[sl] = sg;
     }
+    __syncthreads();
   }
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
     const int i = t % p, jj = t / p;
