@@ -864,7 +864,8 @@ template void tsqr_apply<float, double, double>(Exec&, const QRTreeT<float>&, co
 constexpr int SVD_THREADS = 1024;
 constexpr int SVD_MAX_SWEEPS = 30;
 constexpr int SVD_MIXED_MIN = 8;      // FP32 pre-rotation from this deflated rank up
-constexpr int SVD_MIXED_SWEEPS = 12;  // cap of FP32 sweeps
+constexpr int SVD_MIXED_SWEEPS = 6;   // cap of FP32 sweeps
+constexpr float SVD_MIXED_TOL = 1e-5f;  // FP32 phase: rotate while |g| > 1e-5 sqrt(a b)
 
 __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restrict__ Min, int p, double tol, int cap,
                                                           double defl, double* US, double* Vout, double* sig,
@@ -880,6 +881,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   __shared__ double s_tau, s_fro2, s_trail;
   __shared__ int s_jmax, s_stop, s_rot, s_k, s_tmax;
   __shared__ float cnf[128];
+  __shared__ double gam[64], rc_c[64], rc_s[64];  // per pair of a round (q/2 <= 56)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* HV = scr;                  // Householder vectors, p x p
   double* htau = scr + (size_t)p * p;
@@ -1066,7 +1068,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     for (int t = threadIdx.x; t < p * pd; t += blockDim.x) Af[t] = (float)(A[t] * fscale);
     for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) Jf[t] = ((t % pd) == (t / pd)) ? 1.0f : 0.0f;
     __syncthreads();
-    const float epsf = 4.0f * FLT_EPSILON;
+    const float epsf = SVD_MIXED_TOL;
     for (int sw = 0; sw < SVD_MIXED_SWEEPS; ++sw) {
       for (int j = w; j < pd; j += nw) {
         float sq = 0.0f;
@@ -1168,31 +1170,68 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     }
     __syncthreads();
     for (int step = 0; step < q - 1; ++step) {
+      // (a) one warp per pair: the off-diagonal g = <c_i, c_j>
       for (int pr = w; pr < q / 2; pr += nw) {
         const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
         const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
         if (i >= pd || j >= pd) continue;
-        double* ci = A + (size_t)i * p;
-        double* cj = A + (size_t)j * p;
+        const double* ci = A + (size_t)i * p;
+        const double* cj = A + (size_t)j * p;
         double ga = 0.0;
         for (int r = lane; r < p; r += 32) ga = fma(ci[r], cj[r], ga);
         ga = warp_sum(ga);
-        const double al = cn[i], be = cn[j];
-        // |ga| <= eps sqrt(al be), compared in squares (no FP64 roots per lane)
-        if (al <= thr || be <= thr || ga * ga <= eps2 * al * be) continue;
-        double c = 1.0, sn = 0.0;
-        if (lane == 0) {  // rotation in one lane, then broadcast
-          const double dd = be - al;
-          const double t = (dd >= 0.0 ? 2.0 * ga : -2.0 * ga) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * ga * ga)));
-          c = rsqrt(fma(t, t, 1.0));
-          sn = c * t;
-          cn[i] = fma(-t, ga, al);
-          cn[j] = fma(t, ga, be);
-          // |t| as its float bit pattern: non-negative floats order like ints
-          atomicMax(&s_tmax, __float_as_int(fminf((float)fabs(t), 1.0f)));
+        if (lane == 0) gam[pr] = ga;
+      }
+      __syncthreads();
+      // (b) warp 0, one lane per pair: the rotations of the whole round (an
+      // FP64 instruction costs its SMSP the same with 1 or 32 active lanes)
+      if (w == 0) {
+        for (int pr = lane; pr < q / 2; pr += 32) {
+          const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
+          const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
+          double c = 1.0, sn = 0.0;
+          if (i < pd && j < pd) {
+            const double ga = gam[pr], al = cn[i], be = cn[j];
+            // |ga| <= eps sqrt(al be), compared in squares (no FP64 roots)
+            if (!(al <= thr || be <= thr || ga * ga <= eps2 * al * be)) {
+              // The angle only steers convergence: it is formed in FP32 from
+              // dd and ga scaled by the same power of two (exact; the larger
+              // lands in [1, 2)), while c = 1/sqrt(1 + t^2) in FP64 keeps the
+              // applied rotation orthogonal to FP64 accuracy (no FP64 square
+              // root or division per rotation).
+              const double dd = be - al;
+              const unsigned long long ebits = __double_as_longlong(fmax(fabs(dd), fabs(ga)));
+              const int ex = (int)((ebits >> 52) & 0x7FF);
+              const double sc = __longlong_as_double((unsigned long long)(2046 - min(ex, 2045)) << 52);
+              const float dds = (float)(dd * sc), gas = (float)(ga * sc);
+              const float tf =
+                  (dds >= 0.0f ? 2.0f * gas : -2.0f * gas) / (fabsf(dds) + sqrtf(fmaf(dds, dds, 4.0f * gas * gas)));
+              double t = (double)tf;
+              if (!(fabsf(tf) > 0.0f && isfinite(tf)))  // FP64 formula where FP32 cannot resolve the angle
+                t = (dd >= 0.0 ? 2.0 * ga : -2.0 * ga) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * ga * ga)));
+              c = rsqrt(fma(t, t, 1.0));
+              sn = c * t;
+              cn[i] = fma(-t, ga, al);
+              cn[j] = fma(t, ga, be);
+              // |t| as its float bit pattern: non-negative floats order like ints
+              atomicMax(&s_tmax, __float_as_int(fminf((float)fabs(t), 1.0f)));
+              s_rot = 1;
+            }
+          }
+          rc_c[pr] = c;
+          rc_s[pr] = sn;
         }
-        c = __shfl_sync(0xffffffffu, c, 0);
-        sn = __shfl_sync(0xffffffffu, sn, 0);
+      }
+      __syncthreads();
+      // (c) one warp per pair: apply the rotation to L and V
+      for (int pr = w; pr < q / 2; pr += nw) {
+        const double sn = rc_s[pr];
+        if (sn == 0.0) continue;
+        const double c = rc_c[pr];
+        const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
+        const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
+        double* ci = A + (size_t)i * p;
+        double* cj = A + (size_t)j * p;
         for (int r = lane; r < p; r += 32) {
           const double x = ci[r], y = cj[r];
           ci[r] = c * x - sn * y;
@@ -1205,7 +1244,6 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
           vi[r] = c * x - sn * y;
           vj[r] = sn * x + c * y;
         }
-        if (lane == 0) s_rot = 1;
       }
       __syncthreads();
     }
@@ -1273,35 +1311,40 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     const int r = t % p, c = t / p;
     US[piv[r] + (size_t)c * p] = c < pd ? A[r + (size_t)order[c] * p] : 0.0;
   }
-  // Vout = Q [V; 0]: one warp per column, reflectors applied last-to-first
-  for (int c = w; c < k; c += nw) {
-    double z[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = lane + 32 * u;
-      z[u] = (c < pd && r < pd) ? J[r + (size_t)order[c] * pd] : ((c >= pd && r == c) ? 1.0 : 0.0);
-    }
+  // Vout = Q [V; 0]: one thread per column (a warp instruction then serves
+  // 32 columns), reflectors applied last-to-first to Z in shared memory,
+  // row-major with an odd stride so that the columns' threads hit distinct banks
+  __syncthreads();  // A (L V) has been read into US: reuse it for Z
+  const int kz = (k < p) ? (k | 1) : k;  // Z must fit in A's p x p doubles
+  double* Z = A;                          // p x kz
+  for (int t = threadIdx.x; t < p * k; t += blockDim.x) {
+    const int r = t / k, c = t % k;
+    Z[(size_t)r * kz + c] = (c < pd && r < pd) ? J[r + (size_t)order[c] * pd] : ((c >= pd && r == c) ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
     for (int kk = pd - 1; kk >= 0; --kk) {
       const double tk = htau[kk];
       if (tk == 0.0) continue;
-      double d = 0.0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = lane + 32 * u;
-        if (r < p && r >= kk) d = fma(r == kk ? 1.0 : HV[r + (size_t)kk * p], z[u], d);
+      const double* hv = HV + (size_t)kk * p;
+      double d0 = Z[(size_t)kk * kz + c], d1 = 0.0, d2 = 0.0, d3 = 0.0;
+      int r = kk + 1;
+      for (; r + 3 < p; r += 4) {
+        d0 = fma(hv[r], Z[(size_t)r * kz + c], d0);
+        d1 = fma(hv[r + 1], Z[(size_t)(r + 1) * kz + c], d1);
+        d2 = fma(hv[r + 2], Z[(size_t)(r + 2) * kz + c], d2);
+        d3 = fma(hv[r + 3], Z[(size_t)(r + 3) * kz + c], d3);
       }
-      d = warp_sum(d) * tk;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = lane + 32 * u;
-        if (r < p && r >= kk) z[u] = fma(-d, r == kk ? 1.0 : HV[r + (size_t)kk * p], z[u]);
-      }
+      for (; r < p; ++r) d0 = fma(hv[r], Z[(size_t)r * kz + c], d0);
+      const double d = ((d0 + d1) + (d2 + d3)) * tk;
+      Z[(size_t)kk * kz + c] -= d;
+      for (r = kk + 1; r < p; ++r) Z[(size_t)r * kz + c] = fma(-d, hv[r], Z[(size_t)r * kz + c]);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = lane + 32 * u;
-      if (r < p) Vout[r + (size_t)c * p] = z[u];
-    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p * k; t += blockDim.x) {
+    const int r = t % p, c = t / p;
+    Vout[r + (size_t)c * p] = Z[(size_t)r * kz + c];
   }
 }
 
