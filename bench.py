@@ -295,6 +295,10 @@ def run_ours(args):
     cross_info = {"calls": st_all["cross_calls"], "sweeps": st_all["cross_sweeps"],
                   "sweeps_per_call": st_all["cross_sweeps"] / max(st_all["cross_calls"], 1),
                   "learned_calls": st_all["learned_calls"], "learned_accepted": st_all["learned_accepted"],
+                  "roundings": st_all["rounds"], "range_finder_attempts": st_all["qb_attempts"],
+                  "range_finder_uncertified": st_all["qb_uncertified"], "svd_calls": st_all["svd_calls"],
+                  "svd_mean_p": st_all["svd_p_sum"] / max(st_all["svd_calls"], 1),
+                  "svd_mean_sweeps": st_all["svd_sweeps_sum"] / max(st_all["svd_calls"], 1),
                   "window": "all steps of the timed solver (warm-up, timed, profile)"}
     total_ms = sum(step_ms)
     if world > 1:

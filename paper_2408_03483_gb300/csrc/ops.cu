@@ -452,7 +452,9 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
   sumsq(ex, Yf, n1, n2, n1, kbuf);
   double nrm2[1];
   fetch_doubles(ex, kbuf, 1, nrm2);
-  int p = std::min({112, s, ((std::max(2 * cap, cap + 16) + 7) / 8) * 8});
+  // first sketch: cap + 8 columns (rounded to 8); the explicit residual check
+  // doubles it, up to 112, whenever the range is not yet captured
+  int p = std::min({112, s, ((cap + 8 + 7) / 8) * 8});
   Real* Om = ex.ar->get<Real>((size_t)l * 112);
   Real* S = ex.ar->get<Real>((size_t)s * 112);
   Real* Q = ex.ar->get<Real>((size_t)s * 112);
