@@ -312,32 +312,6 @@ static void flux_linear(Solver& S, const TT qm[3], const TT qp[3], int d, std::v
 // u = round(hu o 1/h), v = round(hv o 1/h), then F = (hu, round(round(hu o u)
 // + g/2 round(h o h)), round(hu o v)) for x faces and G = (hv, round(hv o u),
 // round(round(hv o v) + g/2 round(h o h))) for y faces.  F[0] is left to the caller.
-static void side_flux(Solver& S, Exec& ex, const TT Q[3], int d, TT F[3]) {
-  const tt_fv_params& p = S.p;
-  const double tol = p.tol, g = p.g;
-  const int cap = p.rank_cap, mi = p.max_iter > 0 ? p.max_iter : 50;
-  const int n1 = Q[0].n1, n2 = Q[0].n2;
-  Scope sc(*ex.ar);
-  TT rh = alloc_tt(*ex.ar, n1, n2, cap);
-  bool nc = false;
-  reciprocal(ex, Q[0], tol, cap, mi, rh, &nc);
-  TT_REQUIRE(!nc, TT_ERR_NOCONV);
-  TT u = alloc_tt(*ex.ar, n1, n2, cap), v = alloc_tt(*ex.ar, n1, n2, cap), hh = alloc_tt(*ex.ar, n1, n2, cap);
-  TT t1 = alloc_tt(*ex.ar, n1, n2, cap);
-  round_hadamard(ex, Q[1], rh, tol, cap, u);
-  round_hadamard(ex, Q[2], rh, tol, cap, v);
-  round_hadamard(ex, Q[0], Q[0], tol, cap, hh);
-  if (d == 0) {
-    round_hadamard(ex, Q[1], u, tol, cap, t1);
-    round_sum(ex, {Term{1.0, t1}, Term{0.5 * g, hh}}, tol, cap, F[1]);
-    round_hadamard(ex, Q[1], v, tol, cap, F[2]);
-  } else {
-    round_hadamard(ex, Q[2], u, tol, cap, F[1]);
-    round_hadamard(ex, Q[2], v, tol, cap, t1);
-    round_sum(ex, {Term{1.0, t1}, Term{0.5 * g, hh}}, tol, cap, F[2]);
-  }
-}
-
 // lambda = max(|u-| + sqrt(g h-), |u+| + sqrt(g h+)) on the faces by cross
 static void face_lambda(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int d, unsigned seed, TT& lam) {
   const tt_fv_params& p = S.p;
@@ -353,16 +327,10 @@ static void face_lambda(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int
   cross(ex, fl, qm[0].n1, qm[0].n2, qp[0], p.tol, p.rank_cap, kick, sweeps, seed, lam);
 }
 
-// LLF combination of one component: round(F-/2 + F+/2 - round(lambda o round(Q+ - Q-))/2)
-static void llf_component(Solver& S, Exec& ex, const TT& Fm, const TT& Fp, const TT& lam, const TT& qm,
-                          const TT& qp, TT& out) {
-  const double tol = S.p.tol;
-  const int cap = S.p.rank_cap;
-  Scope sc(*ex.ar);
-  TT dd = alloc_tt(*ex.ar, qm.n1, qm.n2, cap), ld = alloc_tt(*ex.ar, qm.n1, qm.n2, cap);
-  round_sum(ex, {Term{1.0, qp}, Term{-1.0, qm}}, tol, cap, dd);
-  round_hadamard(ex, lam, dd, tol, cap, ld);
-  round_sum(ex, {Term{0.5, Fm}, Term{0.5, Fp}, Term{-0.5, ld}}, tol, cap, out);
+// LLF combination of one component (Eq. LLF-TT): with dd = round(Q+ - Q-) and
+// ld = round(lambda o dd) computed earlier, out = round(F-/2 + F+/2 - ld/2)
+static void llf_combine(Solver& S, Exec& ex, const TT& Fm, const TT& Fp, const TT& ld, TT& out) {
+  round_sum(ex, {Term{0.5, Fm}, Term{0.5, Fp}, Term{-0.5, ld}}, S.p.tol, S.p.rank_cap, out);
 }
 
 // sum_m w_m over the stacked index, then (T - 1)/h on the normal core:
@@ -396,9 +364,10 @@ static TT quad_and_difference(Solver& S, Exec& ex, const TT& Fh, int d) {
 }
 
 // F(u) = round(u + dt L(u)) for the three fields (Eq. tt-forward-euler).
-// Independent pieces run as concurrent tasks: the 12 WENO face crosses, the
-// 4 side fluxes with the 2 lambda crosses, the 6 LLF combinations, the 3
-// final rounds.
+// Independent pieces run as concurrent tasks: the 12 WENO face crosses; the
+// nonlinear fluxes in three waves (1/h, h o h, the 2 lambda crosses and the 6
+// LLF jumps; the velocities and the 6 lambda o jump products; the flux
+// components); the 6 LLF combinations; the 3 final rounds.
 struct SectionTimer {
   double& acc;
   std::chrono::steady_clock::time_point t0;
@@ -450,7 +419,7 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
     }
   }
   if (p.eqn != TT_LINEAR) {
-    TT F[2][2][3], lam[2], Fh[2][3];
+    TT F[2][2][3], lam[2], Fh[2][3], dd[2][3], ld[2][3];
     for (int d = 0; d < 2; ++d) {
       for (int sd = 0; sd < 2; ++sd)
         for (int c = 1; c < 3; ++c) F[d][sd][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
@@ -458,16 +427,68 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
       for (int c = 0; c < 3; ++c) Fh[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
     }
     {
-    SectionTimer st1(S.section_ms[1]);
-    parallel_tasks(ex, 6, [&](Exec& cx, int t) {
-      if (t < 4) {
-        const int d = t / 2, sd = t % 2;
-        side_flux(S, cx, sd == 0 ? qm[d] : qp[d], d, F[d][sd]);
-      } else {
-        const int d = t - 4;
-        face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, lam[d]);
+      // The nonlinear flux of each side (Sec. 4.2) in three waves of
+      // independent roundings: (A) 1/h by Algorithm 1, h o h and the two
+      // lambda crosses; (B) u = hu o (1/h), v = hv o (1/h); (C) the two flux
+      // components.  Each quantity is the same sequence of roundings as in a
+      // serial evaluation; only independent ones run side by side.
+      SectionTimer st1(S.section_ms[1]);
+      const double tol = p.tol, g = p.g;
+      const int mi = p.max_iter > 0 ? p.max_iter : 50;
+      TT rh[2][2], hh[2][2], uu[2][2], vv[2][2];
+      for (int d = 0; d < 2; ++d) {
+        for (int sd = 0; sd < 2; ++sd) {
+          rh[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+          hh[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+          uu[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+          vv[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+        }
+        for (int c = 0; c < 3; ++c) {
+          dd[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+          ld[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+        }
       }
-    });
+      auto side = [&](int d, int sd) -> const TT* { return sd == 0 ? qm[d] : qp[d]; };
+      parallel_tasks(ex, 16, [&](Exec& cx, int t) {
+        if (t >= 10) {  // the LLF jump dd = round(Q+ - Q-) of each component
+          const int d = (t - 10) / 3, c = (t - 10) % 3;
+          round_sum(cx, {Term{1.0, qp[d][c]}, Term{-1.0, qm[d][c]}}, tol, cap, dd[d][c]);
+        } else if (t < 4) {
+          const int d = t / 2, sd = t % 2;
+          bool nc = false;
+          reciprocal(cx, side(d, sd)[0], tol, cap, mi, rh[d][sd], &nc);
+          TT_REQUIRE(!nc, TT_ERR_NOCONV);
+        } else if (t < 8) {
+          const int d = (t - 4) / 2, sd = (t - 4) % 2;
+          round_hadamard(cx, side(d, sd)[0], side(d, sd)[0], tol, cap, hh[d][sd]);
+        } else {
+          const int d = t - 8;
+          face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, lam[d]);
+        }
+      });
+      parallel_tasks(ex, 14, [&](Exec& cx, int t) {
+        if (t >= 8) {  // ld = round(lambda o dd)
+          const int d = (t - 8) / 3, c = (t - 8) % 3;
+          round_hadamard(cx, lam[d], dd[d][c], tol, cap, ld[d][c]);
+          return;
+        }
+        const int d = t / 4, sd = (t / 2) % 2, comp = t % 2;
+        round_hadamard(cx, side(d, sd)[1 + comp], rh[d][sd], tol, cap, comp == 0 ? uu[d][sd] : vv[d][sd]);
+      });
+      parallel_tasks(ex, 8, [&](Exec& cx, int t) {
+        const int d = t / 4, sd = (t / 2) % 2, comp = 1 + t % 2;
+        const TT* Qs = side(d, sd);
+        const TT& qn = Qs[d == 0 ? 1 : 2];  // the normal momentum hu (x) or hv (y)
+        const TT& vel = comp == 1 ? uu[d][sd] : vv[d][sd];
+        if (comp == 1 + d) {  // normal component: q_n o u_n + g h^2 / 2
+          Scope s2(*cx.ar);
+          TT t1 = alloc_tt(*cx.ar, f1[d], f2[d], cap);
+          round_hadamard(cx, qn, vel, tol, cap, t1);
+          round_sum(cx, {Term{1.0, t1}, Term{0.5 * g, hh[d][sd]}}, tol, cap, F[d][sd][comp]);
+        } else {
+          round_hadamard(cx, qn, vel, tol, cap, F[d][sd][comp]);
+        }
+      });
     }
     for (int d = 0; d < 2; ++d) {
       const int k = d == 0 ? 1 : 2;
@@ -478,7 +499,7 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
       SectionTimer st2(S.section_ms[2]);
       parallel_tasks(ex, 6, [&](Exec& cx, int t) {
         const int d = t / 3, c = t % 3;
-        llf_component(S, cx, F[d][0][c], F[d][1][c], lam[d], qm[d][c], qp[d][c], Fh[d][c]);
+        llf_combine(S, cx, F[d][0][c], F[d][1][c], ld[d][c], Fh[d][c]);
       });
     }
     SectionTimer st3(S.section_ms[3]);
