@@ -327,7 +327,7 @@ static std::vector<int> fetch_idx(Exec& ex, const int* d, int n) {
     return out;
   }
   TT_CUDA(cudaMemcpyAsync(out.data(), d, sizeof(int) * n, cudaMemcpyDeviceToHost, ex.s));
-  TT_CUDA(cudaStreamSynchronize(ex.s));
+  host_wait(ex);
   ex.syncs++;
   return out;
 }
@@ -336,7 +336,7 @@ static void upload_idx(Exec& ex, int* d, const std::vector<int>& h) {
   if (ex.dry || h.empty()) return;
   // pageable source: the copy is staged before the call returns
   TT_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, ex.s));
-  TT_CUDA(cudaStreamSynchronize(ex.s));
+  host_wait(ex);
 }
 
 // ============================================================== cross

@@ -13,6 +13,7 @@
 // Face convention: face row i of an x-face TT is the face x_{i-1/2}; Qm holds
 // cell i-1's right-face value, Qp cell i's left-face value.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <algorithm>
@@ -51,37 +52,121 @@ static TT const_tt(Exec& ex, int n1, int n2, double c) {
 }
 
 // ============================================================== Algorithm 1
-int reciprocal(Exec& ex, const TT& x, double tol, int cap, int max_iter, TT& y, bool* noconv) {
-  tol = effective_tol(ex, tol);  // a precision form stops at its own rounding level
-  Scope sc(*ex.ar);
+// One reciprocal laid out as task-graph nodes.  The roundings are those of the
+// serial loop, in its order per chain: xt = round(1 - x / x_avg), then for
+// k = 1, 2, ...: dy <- round(dy o xt) and its norm (the stop test), y <-
+// round(y + dy).  dy alternates between two buffers, so the y update of
+// iteration k runs beside the dy rounding of iteration k + 1; the last node
+// scales y by 1 / x_avg.
+struct Reciprocal {
+  TaskGraph* G = nullptr;
+  const TT* x = nullptr;
+  TT* y = nullptr;
+  double tol = 0.0, x_avg = 1.0, err = 1.0;
+  int cap = 0, max_iter = 0, prio = 0, it = 0;
+  TT xt, dy[2];
+  int reader[2] = {-1, -1};  // the y update that reads dy[b]
+  int last_y = -1;
+  int done = -1;
+  bool noconv = false;
+};
+
+static void taylor_dy(Reciprocal& R, int k, int prev);
+
+static void taylor_y(Reciprocal& R, int b, int dy_node) {
+  const int yk = R.G->add(
+      "taylor_y", R.prio,
+      [&R, b](Exec& cx) { round_sum(cx, {Term{1.0, *R.y}, Term{1.0, R.dy[b]}}, R.tol, R.cap, *R.y); },
+      {dy_node, R.last_y});
+  R.reader[b] = yk;
+  R.last_y = yk;
+}
+
+// iteration k >= 1 writes dy[k & 1] from dy[(k - 1) & 1] (node prev); the
+// buffer it overwrites was last read by the y update of iteration k - 2
+static void taylor_dy(Reciprocal& R, int k, int prev) {
+  const int b = k & 1;
+  R.G->add(
+      "taylor_dy", R.prio,
+      [&R, k, b](Exec& cx) {
+        round_hadamard(cx, R.dy[b ^ 1], R.xt, R.tol, R.cap, R.dy[b]);
+        double* sn = cx.ar->get<double>(2);
+        tt_sum_norm(cx, R.dy[b], sn);
+        double v[2];
+        fetch_doubles(cx, sn, 2, v);
+        R.err = cx.dry ? 0.0 : v[1] / std::sqrt((double)R.x->n1 * R.x->n2);
+        R.it = k;
+        const int me = TaskGraph::self();
+        taylor_y(R, b, me);
+        if (R.err > R.tol && k < R.max_iter) {
+          taylor_dy(R, k + 1, me);
+        } else {
+          R.G->depend(R.done, R.last_y);
+          R.G->release(R.done);
+        }
+      },
+      {prev, R.reader[b]});
+}
+
+// Adds the nodes of y = 1/x (x and y preallocated; x's cores are read when
+// the first node runs, after `after`).  Returns the node after which y holds
+// the result; R must outlive G.run(), after which R.noconv and R.it hold the
+// stop-test outcome and the iteration count.
+static int reciprocal_nodes(TaskGraph& G, Exec& ex, const TT& x, double tol, int cap, int max_iter, TT& y,
+                            int after, int prio, Reciprocal& R) {
   const int n1 = x.n1, n2 = x.n2;
-  const double N = (double)n1 * n2;
-  double* sn = ex.ar->get<double>(2);
-  tt_sum_norm(ex, x, sn);
-  double v[2];
-  fetch_doubles(ex, sn, 2, v);
-  const double x_avg = ex.dry ? 1.0 : v[0] / N;
-  TT one = const_tt(ex, n1, n2, 1.0);
-  TT xt = alloc_tt(*ex.ar, n1, n2, cap);
-  round_sum(ex, {Term{1.0, one}, Term{-1.0 / x_avg, x}}, tol, cap, xt);
-  TT dy = alloc_tt(*ex.ar, n1, n2, cap);
-  copy_tt(ex, one, dy);
   TT_REQUIRE(y.cap >= cap && y.n1 == n1 && y.n2 == n2, TT_ERR_ARG);
-  copy_tt(ex, one, y);
-  double err = 1.0;
-  int it = 0;
-  while (err > tol && it < max_iter) {
-    round_hadamard(ex, dy, xt, tol, cap, dy);
-    round_sum(ex, {Term{1.0, y}, Term{1.0, dy}}, tol, cap, y);
-    tt_sum_norm(ex, dy, sn);
-    fetch_doubles(ex, sn, 2, v);
-    err = ex.dry ? 0.0 : v[1] / std::sqrt(N);
-    ++it;
-  }
-  ex.taylor_iters += it;
-  scaled_copy(ex, y.a, y.a, (long)n1 * y.r, 1.0 / x_avg);
-  if (noconv) *noconv = (err > tol);
-  return it;
+  R.G = &G;
+  R.x = &x;
+  R.y = &y;
+  R.tol = effective_tol(ex, tol);  // a precision form stops at its own rounding level
+  R.cap = cap;
+  R.max_iter = max_iter;
+  R.prio = prio;
+  R.xt = alloc_tt(*ex.ar, n1, n2, cap);
+  R.dy[0] = alloc_tt(*ex.ar, n1, n2, cap);
+  R.dy[1] = alloc_tt(*ex.ar, n1, n2, cap);
+  R.done = G.add(
+      "taylor_scale", prio,
+      [&R](Exec& cx) {
+        cx.taylor_iters += R.it;
+        scaled_copy(cx, R.y->a, R.y->a, (long)R.y->n1 * R.y->r, 1.0 / R.x_avg);
+        R.noconv = R.err > R.tol;
+      },
+      {}, true);
+  G.add(
+      "taylor_init", prio,
+      [&R](Exec& cx) {
+        const TT& xx = *R.x;
+        double* sn = cx.ar->get<double>(2);
+        tt_sum_norm(cx, xx, sn);
+        double v[2];
+        fetch_doubles(cx, sn, 2, v);
+        R.x_avg = cx.dry ? 1.0 : v[0] / ((double)xx.n1 * xx.n2);
+        TT one = const_tt(cx, xx.n1, xx.n2, 1.0);
+        round_sum(cx, {Term{1.0, one}, Term{-1.0 / R.x_avg, xx}}, R.tol, R.cap, R.xt);
+        copy_tt(cx, one, R.dy[0]);
+        copy_tt(cx, one, *R.y);
+        const int me = TaskGraph::self();
+        if (R.err > R.tol && R.max_iter > 0) {
+          taylor_dy(R, 1, me);
+        } else {
+          R.G->depend(R.done, me);
+          R.G->release(R.done);
+        }
+      },
+      {after});
+  return R.done;
+}
+
+int reciprocal(Exec& ex, const TT& x, double tol, int cap, int max_iter, TT& y, bool* noconv) {
+  Scope sc(*ex.ar);
+  TaskGraph G(ex, 2);
+  Reciprocal R;
+  reciprocal_nodes(G, ex, x, tol, cap, max_iter, y, -1, 0, R);
+  G.run();
+  if (noconv) *noconv = R.noconv;
+  return R.it;
 }
 
 // ============================================================== linear recon
@@ -187,7 +272,7 @@ void record_pivots(Exec& ex, const TT& x0, const std::vector<int>& prev, const s
   mlp_features_host_prev(ex, x0, prev, X);
   std::vector<float> h((size_t)n2 * kMlpFeatures);
   TT_CUDA(cudaMemcpyAsync(h.data(), X, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, ex.s));
-  TT_CUDA(cudaStreamSynchronize(ex.s));
+  host_wait(ex);
   ex.syncs++;
   std::vector<float> lab(n2, 0.0f);
   for (int j : J)
@@ -334,15 +419,16 @@ static void llf_combine(Solver& S, Exec& ex, const TT& Fm, const TT& Fp, const T
 }
 
 // sum_m w_m over the stacked index, then (T - 1)/h on the normal core:
-// returns the TT of (F_{i+1/2} - F_{i-1/2}) / h (Eq. SWE-system-TT).
-static TT quad_and_difference(Solver& S, Exec& ex, const TT& Fh, int d) {
+// out = the TT of (F_{i+1/2} - F_{i-1/2}) / h (Eq. SWE-system-TT); out is an
+// nx x ny TT with room for Fh's rank.
+static void quad_and_difference(Solver& S, Exec& ex, const TT& Fh, int d, TT& out) {
   const ReconCoeffs& R = recon_coeffs();
   const int nq = S.nq;
   const double* w = nq == 2 ? R.w2 : R.w3;
   const int n = d == 0 ? S.p.ny : S.p.nx;  // tangential size
   const int nn = d == 0 ? S.p.nx : S.p.ny;
   const double h = d == 0 ? S.p.lx / S.p.nx : S.p.ly / S.p.ny;
-  TT out = alloc_tt(*ex.ar, S.p.nx, S.p.ny, Fh.r);
+  TT_REQUIRE(out.n1 == S.p.nx && out.n2 == S.p.ny && out.cap >= Fh.r, TT_ERR_ARG);
   out.r = Fh.r;
   StencilSet sq;
   sq.nout = 1;
@@ -360,14 +446,8 @@ static TT quad_and_difference(Solver& S, Exec& ex, const TT& Fh, int d) {
   const double cd[2] = {-1.0 / h, 1.0 / h};
   add_taps(sd.out[0], cd, 2, 0, 0);
   stencil(ex, sd, d == 0 ? Fh.a : Fh.b, nn, nn, Fh.r);
-  return out;
 }
 
-// F(u) = round(u + dt L(u)) for the three fields (Eq. tt-forward-euler).
-// Independent pieces run as concurrent tasks: the 12 WENO face crosses; the
-// nonlinear fluxes in three waves (1/h, h o h, the 2 lambda crosses and the 6
-// LLF jumps; the velocities and the 6 lambda o jump products; the flux
-// components); the 6 LLF combinations; the 3 final rounds.
 struct SectionTimer {
   double& acc;
   std::chrono::steady_clock::time_point t0;
@@ -377,7 +457,21 @@ struct SectionTimer {
   }
 };
 
-static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT out[3]) {
+// Host threads (each with a stream and an arena slice) of a stage graph:
+// TT_STAGE_WORKERS, else 16 -- the widest front of the nonlinear graph.
+static int stage_workers() {
+  static const int w = [] {
+    const char* e = std::getenv("TT_STAGE_WORKERS");
+    const int v = e ? std::atoi(e) : 0;
+    return v >= 1 && v <= 48 ? v : 16;
+  }();
+  return w;
+}
+
+// F(u) = round(u + dt L(u)) for the three fields of the linear SWE
+// (Eq. tt-forward-euler): faces (the 12 WENO crosses run as concurrent tasks),
+// the LLF flux as TT sums, the quadrature and difference, the 3 final rounds.
+static void forward_euler_linear(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT out[3]) {
   Scope sc(*ex.ar);
   const tt_fv_params& p = S.p;
   const int cap = p.rank_cap;
@@ -389,125 +483,37 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
     f1[d] = d == 0 ? p.nx : S.nq * p.nx;
     f2[d] = d == 0 ? S.nq * p.ny : p.ny;
   }
-  SectionTimer* st0 = new SectionTimer(S.section_ms[0]);
-  if (p.recon == TT_WENO5) {
-    for (int d = 0; d < 2; ++d)
-      for (int c = 0; c < 3; ++c) {
-        qm[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-        qp[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-      }
-    parallel_tasks(ex, 12, [&](Exec& cx, int t) {
-      const int d = t / 6, c = (t / 2) % 3, k = t % 2;
-      weno_side(S, cx, Q[c], d, c, k, seed, k == 0 ? qm[d][c] : qp[d][c]);
-    });
-  } else {
-    for (int d = 0; d < 2; ++d)
-      for (int c = 0; c < 3; ++c) faces_linear(S, ex, Q[c], d, qm[d][c], qp[d][c]);
+  {
+    SectionTimer st0(S.section_ms[0]);
+    if (p.recon == TT_WENO5) {
+      for (int d = 0; d < 2; ++d)
+        for (int c = 0; c < 3; ++c) {
+          qm[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+          qp[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+        }
+      parallel_tasks(ex, 12, [&](Exec& cx, int t) {
+        const int d = t / 6, c = (t / 2) % 3, k = t % 2;
+        weno_side(S, cx, Q[c], d, c, k, seed, k == 0 ? qm[d][c] : qp[d][c]);
+      });
+    } else {
+      for (int d = 0; d < 2; ++d)
+        for (int c = 0; c < 3; ++c) faces_linear(S, ex, Q[c], d, qm[d][c], qp[d][c]);
+    }
   }
-  delete st0;
-  for (int d = 0; d < 2; ++d) {
-    if (p.eqn == TT_LINEAR) {
+  {
+    SectionTimer st3(S.section_ms[3]);
+    for (int d = 0; d < 2; ++d) {
       std::vector<Term> fl[3];
       flux_linear(S, qm[d], qp[d], d, fl);
       for (int c = 0; c < 3; ++c) {
         const int R = total_rank(fl[c]);
         TT cat = alloc_tt(*ex.ar, f1[d], f2[d], R);
         tt_concat(ex, fl[c], cat);
-        TT D = quad_and_difference(S, ex, cat, d);
+        TT D = alloc_tt(*ex.ar, p.nx, p.ny, R);
+        quad_and_difference(S, ex, cat, d, D);
         terms[c].push_back(Term{-p.dt, D});
       }
     }
-  }
-  if (p.eqn != TT_LINEAR) {
-    TT F[2][2][3], lam[2], Fh[2][3], dd[2][3], ld[2][3];
-    for (int d = 0; d < 2; ++d) {
-      for (int sd = 0; sd < 2; ++sd)
-        for (int c = 1; c < 3; ++c) F[d][sd][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-      lam[d] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-      for (int c = 0; c < 3; ++c) Fh[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-    }
-    {
-      // The nonlinear flux of each side (Sec. 4.2) in three waves of
-      // independent roundings: (A) 1/h by Algorithm 1, h o h and the two
-      // lambda crosses; (B) u = hu o (1/h), v = hv o (1/h); (C) the two flux
-      // components.  Each quantity is the same sequence of roundings as in a
-      // serial evaluation; only independent ones run side by side.
-      SectionTimer st1(S.section_ms[1]);
-      const double tol = p.tol, g = p.g;
-      const int mi = p.max_iter > 0 ? p.max_iter : 50;
-      TT rh[2][2], hh[2][2], uu[2][2], vv[2][2];
-      for (int d = 0; d < 2; ++d) {
-        for (int sd = 0; sd < 2; ++sd) {
-          rh[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-          hh[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-          uu[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-          vv[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-        }
-        for (int c = 0; c < 3; ++c) {
-          dd[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-          ld[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
-        }
-      }
-      auto side = [&](int d, int sd) -> const TT* { return sd == 0 ? qm[d] : qp[d]; };
-      parallel_tasks(ex, 16, [&](Exec& cx, int t) {
-        if (t >= 10) {  // the LLF jump dd = round(Q+ - Q-) of each component
-          const int d = (t - 10) / 3, c = (t - 10) % 3;
-          round_sum(cx, {Term{1.0, qp[d][c]}, Term{-1.0, qm[d][c]}}, tol, cap, dd[d][c]);
-        } else if (t < 4) {
-          const int d = t / 2, sd = t % 2;
-          bool nc = false;
-          reciprocal(cx, side(d, sd)[0], tol, cap, mi, rh[d][sd], &nc);
-          TT_REQUIRE(!nc, TT_ERR_NOCONV);
-        } else if (t < 8) {
-          const int d = (t - 4) / 2, sd = (t - 4) % 2;
-          round_hadamard(cx, side(d, sd)[0], side(d, sd)[0], tol, cap, hh[d][sd]);
-        } else {
-          const int d = t - 8;
-          face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, lam[d]);
-        }
-      });
-      parallel_tasks(ex, 14, [&](Exec& cx, int t) {
-        if (t >= 8) {  // ld = round(lambda o dd)
-          const int d = (t - 8) / 3, c = (t - 8) % 3;
-          round_hadamard(cx, lam[d], dd[d][c], tol, cap, ld[d][c]);
-          return;
-        }
-        const int d = t / 4, sd = (t / 2) % 2, comp = t % 2;
-        round_hadamard(cx, side(d, sd)[1 + comp], rh[d][sd], tol, cap, comp == 0 ? uu[d][sd] : vv[d][sd]);
-      });
-      parallel_tasks(ex, 8, [&](Exec& cx, int t) {
-        const int d = t / 4, sd = (t / 2) % 2, comp = 1 + t % 2;
-        const TT* Qs = side(d, sd);
-        const TT& qn = Qs[d == 0 ? 1 : 2];  // the normal momentum hu (x) or hv (y)
-        const TT& vel = comp == 1 ? uu[d][sd] : vv[d][sd];
-        if (comp == 1 + d) {  // normal component: q_n o u_n + g h^2 / 2
-          Scope s2(*cx.ar);
-          TT t1 = alloc_tt(*cx.ar, f1[d], f2[d], cap);
-          round_hadamard(cx, qn, vel, tol, cap, t1);
-          round_sum(cx, {Term{1.0, t1}, Term{0.5 * g, hh[d][sd]}}, tol, cap, F[d][sd][comp]);
-        } else {
-          round_hadamard(cx, qn, vel, tol, cap, F[d][sd][comp]);
-        }
-      });
-    }
-    for (int d = 0; d < 2; ++d) {
-      const int k = d == 0 ? 1 : 2;
-      F[d][0][0] = qm[d][k];
-      F[d][1][0] = qp[d][k];
-    }
-    {
-      SectionTimer st2(S.section_ms[2]);
-      parallel_tasks(ex, 6, [&](Exec& cx, int t) {
-        const int d = t / 3, c = t % 3;
-        llf_combine(S, cx, F[d][0][c], F[d][1][c], ld[d][c], Fh[d][c]);
-      });
-    }
-    SectionTimer st3(S.section_ms[3]);
-    for (int d = 0; d < 2; ++d)
-      for (int c = 0; c < 3; ++c) {
-        TT D = quad_and_difference(S, ex, Fh[d][c], d);
-        terms[c].push_back(Term{-p.dt, D});
-      }
   }
   if (p.f != 0.0) {
     terms[1].push_back(Term{p.dt * p.f, Q[2]});
@@ -515,6 +521,169 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
   }
   SectionTimer st4(S.section_ms[4]);
   parallel_tasks(ex, 3, [&](Exec& cx, int c) { round_sum(cx, terms[c], p.tol, cap, out[c]); });
+}
+
+// F(u) = round(u + dt L(u)) for the nonlinear SWE as one task graph.  Every
+// cross, rounding and reciprocal of Sec. 4.2 and Eq. LLF-TT is a node that
+// starts once its inputs exist: per face side, 1/h by Algorithm 1 (its two
+// chains pipelined), u = round(hu o 1/h), v = round(hv o 1/h), h o h and the
+// flux components; per direction the lambda cross; per component the LLF jump
+// dd = round(Q+ - Q-), round(lambda o dd), the LLF combination and the
+// quadrature/difference; per field the final round.  A node waits only for
+// what it reads, so the reciprocal of one side starts when that side's h
+// faces exist while other fields' faces are still being reconstructed.  Each
+// quantity is the same sequence of roundings as in a serial evaluation.
+static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT out[3]) {
+  Scope sc(*ex.ar);
+  const tt_fv_params& p = S.p;
+  const int cap = p.rank_cap;
+  const double tol = p.tol, g = p.g;
+  const int mi = p.max_iter > 0 ? p.max_iter : 50;
+  int f1[2], f2[2];
+  for (int d = 0; d < 2; ++d) {
+    f1[d] = d == 0 ? p.nx : S.nq * p.nx;
+    f2[d] = d == 0 ? S.nq * p.ny : p.ny;
+  }
+  // phase milestones (ms from the start): the last face, flux, LLF,
+  // quadrature and final-round node to finish
+  const auto t_start = std::chrono::steady_clock::now();
+  std::mutex mmu;
+  double last[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  auto mark = [&](int phase) {
+    const double t =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    std::lock_guard<std::mutex> lk(mmu);
+    last[phase] = std::max(last[phase], t);
+  };
+  TaskGraph G(ex, stage_workers());
+  TT qm[2][3], qp[2][3];
+  int face[2][3][2];
+  for (int d = 0; d < 2; ++d)
+    for (int c = 0; c < 3; ++c) face[d][c][0] = face[d][c][1] = -1;
+  if (p.recon == TT_WENO5) {
+    for (int d = 0; d < 2; ++d)
+      for (int c = 0; c < 3; ++c) {
+        qm[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+        qp[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      }
+    for (int d = 0; d < 2; ++d)
+      for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 2; ++k)
+          face[d][c][k] = G.add("weno_face", c == 0 ? 100 : 90, [&, d, c, k](Exec& cx) {
+            weno_side(S, cx, Q[c], d, c, k, seed, k == 0 ? qm[d][c] : qp[d][c]);
+            mark(0);
+          });
+  } else {
+    for (int d = 0; d < 2; ++d)
+      for (int c = 0; c < 3; ++c) faces_linear(S, ex, Q[c], d, qm[d][c], qp[d][c]);
+    mark(0);
+  }
+  TT F[2][2][3], lam[2], Fh[2][3], dd[2][3], ld[2][3], D[2][3];
+  TT rh[2][2], hh[2][2], uu[2][2], vv[2][2];
+  for (int d = 0; d < 2; ++d) {
+    lam[d] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+    for (int sd = 0; sd < 2; ++sd) {
+      for (int c = 1; c < 3; ++c) F[d][sd][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      rh[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      hh[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      uu[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      vv[d][sd] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+    }
+    for (int c = 0; c < 3; ++c) {
+      Fh[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      dd[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      ld[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+      D[d][c] = alloc_tt(*ex.ar, p.nx, p.ny, cap);
+    }
+  }
+  auto side = [&](int d, int sd) -> const TT* { return sd == 0 ? qm[d] : qp[d]; };
+  Reciprocal R[2][2];
+  int hh_node[2][2], vel_node[2][2][2], flux_node[2][2][3], lam_node[2], ld_node[2][3], qd_node[2][3];
+  for (int d = 0; d < 2; ++d) {
+    const int k = d == 0 ? 1 : 2;  // the normal momentum hu (x) or hv (y)
+    for (int sd = 0; sd < 2; ++sd) {
+      const int rdone = reciprocal_nodes(G, ex, side(d, sd)[0], tol, cap, mi, rh[d][sd], face[d][0][sd], 80,
+                                         R[d][sd]);
+      hh_node[d][sd] = G.add("h_o_h", 60, [&, d, sd](Exec& cx) {
+        round_hadamard(cx, side(d, sd)[0], side(d, sd)[0], tol, cap, hh[d][sd]);
+        mark(1);
+      }, {face[d][0][sd]});
+      for (int comp = 0; comp < 2; ++comp)
+        vel_node[d][sd][comp] = G.add("velocity", 75, [&, d, sd, comp](Exec& cx) {
+          round_hadamard(cx, side(d, sd)[1 + comp], rh[d][sd], tol, cap, comp == 0 ? uu[d][sd] : vv[d][sd]);
+          mark(1);
+        }, {rdone, face[d][1 + comp][sd]});
+      flux_node[d][sd][0] = -1;
+      for (int comp = 1; comp < 3; ++comp)
+        flux_node[d][sd][comp] = G.add("flux", 70, [&, d, sd, comp, k](Exec& cx) {
+          const TT& qn = side(d, sd)[k];
+          const TT& vel = comp == 1 ? uu[d][sd] : vv[d][sd];
+          if (comp == k) {  // normal component: q_n o u_n + g h^2 / 2
+            Scope s2(*cx.ar);
+            TT t1 = alloc_tt(*cx.ar, f1[d], f2[d], cap);
+            round_hadamard(cx, qn, vel, tol, cap, t1);
+            round_sum(cx, {Term{1.0, t1}, Term{0.5 * g, hh[d][sd]}}, tol, cap, F[d][sd][comp]);
+          } else {
+            round_hadamard(cx, qn, vel, tol, cap, F[d][sd][comp]);
+          }
+          mark(1);
+        }, {vel_node[d][sd][comp - 1], face[d][k][sd], comp == k ? hh_node[d][sd] : -1});
+    }
+    lam_node[d] = G.add("llf_lambda", 85, [&, d](Exec& cx) {
+      face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, lam[d]);
+      mark(1);
+    }, {face[d][0][0], face[d][0][1], face[d][k][0], face[d][k][1]});
+    for (int c = 0; c < 3; ++c) {
+      const int dd_node = G.add("llf_jump", 50, [&, d, c](Exec& cx) {
+        round_sum(cx, {Term{1.0, qp[d][c]}, Term{-1.0, qm[d][c]}}, tol, cap, dd[d][c]);
+        mark(1);
+      }, {face[d][c][0], face[d][c][1]});
+      ld_node[d][c] = G.add("lambda_o_jump", 55, [&, d, c](Exec& cx) {
+        round_hadamard(cx, lam[d], dd[d][c], tol, cap, ld[d][c]);
+        mark(1);
+      }, {lam_node[d], dd_node});
+    }
+    for (int c = 0; c < 3; ++c) {
+      // the mass flux is the normal momentum itself
+      std::vector<int> deps = c == 0 ? std::vector<int>{face[d][k][0], face[d][k][1]}
+                                     : std::vector<int>{flux_node[d][0][c], flux_node[d][1][c]};
+      deps.push_back(ld_node[d][c]);
+      const int llf = G.add("llf_combine", 40, [&, d, c, k](Exec& cx) {
+        llf_combine(S, cx, c == 0 ? qm[d][k] : F[d][0][c], c == 0 ? qp[d][k] : F[d][1][c], ld[d][c], Fh[d][c]);
+        mark(2);
+      }, deps);
+      qd_node[d][c] = G.add("quad_difference", 40, [&, d, c](Exec& cx) {
+        quad_and_difference(S, cx, Fh[d][c], d, D[d][c]);
+        mark(3);
+      }, {llf});
+    }
+  }
+  for (int c = 0; c < 3; ++c)
+    G.add("forward_euler", 30, [&, c](Exec& cx) {
+      std::vector<Term> terms{Term{1.0, Q[c]}, Term{-p.dt, D[0][c]}, Term{-p.dt, D[1][c]}};
+      if (p.f != 0.0 && c == 1) terms.push_back(Term{p.dt * p.f, Q[2]});
+      if (p.f != 0.0 && c == 2) terms.push_back(Term{-p.dt * p.f, Q[1]});
+      round_sum(cx, terms, p.tol, cap, out[c]);
+      mark(4);
+    }, {qd_node[0][c], qd_node[1][c]});
+  G.run();
+  for (int d = 0; d < 2; ++d)
+    for (int sd = 0; sd < 2; ++sd) TT_REQUIRE(!R[d][sd].noconv, TT_ERR_NOCONV);
+  // each phase's share: how far its last node finished after the previous
+  // phase's last node (the phases overlap; the shares add up to the wall time)
+  double prev = 0.0;
+  for (int ph = 0; ph < 5; ++ph) {
+    const double m = std::max(prev, last[ph]);
+    S.section_ms[ph] += m - prev;
+    prev = m;
+  }
+}
+
+static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT out[3]) {
+  if (S.p.eqn == TT_LINEAR)
+    forward_euler_linear(S, ex, Q, seed, out);
+  else
+    forward_euler_graph(S, ex, Q, seed, out);
 }
 
 // kick-index seed of a stage: depends on the stage and call site only, so a
@@ -699,6 +868,10 @@ tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws
   S.nq = nq_of(p->recon);
   try {
     setup_exec(S.ex, S.ar, ws, ws_bytes, S.s, S.h_int, S.h_dbl, false);
+    if (char* ps = S.pool.slot(0)) {
+      S.ex.h_pinned = reinterpret_cast<int*>(ps);
+      S.ex.h_pinned_d = reinterpret_cast<double*>(ps + 64);
+    }
     S.ex.prof = &S.prof;
     S.ex.pool = &S.pool;
     S.ex.precision = p->precision;
@@ -1156,7 +1329,7 @@ size_t tt_reciprocal_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int
   return dry_bytes([&](Exec& ex) {
     TT x = fake_tt(*ex.ar, n1, n2, rank_in);
     TT y = fake_tt(*ex.ar, n1, n2, rank_cap);
-    reciprocal(ex, x, 1.0, rank_cap, 2, y, nullptr);
+    reciprocal(ex, x, 1e-12, rank_cap, 2, y, nullptr);  // the sizing pass stops after one iteration
   });
 }
 

@@ -219,7 +219,7 @@ template void transpose<float>(Exec&, const float*, int, int, long, float*, long
 int fetch_int(Exec& ex, const int* d) {
   if (ex.dry) return -1;
   TT_CUDA(cudaMemcpyAsync(ex.h_pinned, d, sizeof(int), cudaMemcpyDeviceToHost, ex.s));
-  TT_CUDA(cudaStreamSynchronize(ex.s));
+  host_wait(ex);
   ex.syncs++;
   prof_flush(ex);
   return ex.h_pinned[0];
@@ -227,7 +227,7 @@ int fetch_int(Exec& ex, const int* d) {
 int fetch_svd_info(Exec& ex, const int* d, int p) {
   if (ex.dry) return -1;
   TT_CUDA(cudaMemcpyAsync(ex.h_pinned, d, 3 * sizeof(int), cudaMemcpyDeviceToHost, ex.s));
-  TT_CUDA(cudaStreamSynchronize(ex.s));
+  host_wait(ex);
   ex.syncs++;
   prof_flush(ex);
   ex.svd_calls++;
@@ -245,7 +245,7 @@ void fetch_doubles(Exec& ex, const double* d, int n, double* out) {
   }
   TT_REQUIRE(n <= 16, TT_ERR_ARG);
   TT_CUDA(cudaMemcpyAsync(ex.h_pinned_d, d, sizeof(double) * n, cudaMemcpyDeviceToHost, ex.s));
-  TT_CUDA(cudaStreamSynchronize(ex.s));
+  host_wait(ex);
   ex.syncs++;
   prof_flush(ex);
   for (int i = 0; i < n; ++i) out[i] = ex.h_pinned_d[i];

@@ -1,9 +1,15 @@
 // Concurrent host tasks over CUDA streams: independent rounds, crosses and
 // reciprocals of one stage run side by side so their one-CTA factorisations
 // occupy different SMs.
-#include <mutex>
-#include <thread>
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <deque>
+#include <mutex>
+#include <queue>
+#include <thread>
 
 #include "tt_common.cuh"
 
@@ -69,10 +75,28 @@ cudaEvent_t StreamPool::event(size_t i) {
   return events[i];
 }
 
+char* StreamPool::slot(size_t i) {
+  if (i >= kSlots || pinned_failed) return nullptr;
+  if (!pinned) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&pinned), kSlots * kSlotBytes, cudaHostAllocPortable) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      pinned = nullptr;
+      pinned_failed = true;
+      return nullptr;
+    }
+  }
+  return pinned + i * kSlotBytes;
+}
+
+void host_wait(Exec& ex) { TT_CUDA(cudaStreamSynchronize(ex.s)); }
+
 StreamPool::~StreamPool() {
   for (cudaStream_t s : streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
+  if (pinned) cudaFreeHost(pinned);
 }
+
 
 static void merge_counters(Exec& dst, const Exec& src) {
   dst.rounds += src.rounds;
@@ -92,6 +116,48 @@ static void merge_counters(Exec& dst, const Exec& src) {
   dst.svd_sweeps += src.svd_sweeps;
   dst.flops += src.flops;
   dst.bytes += src.bytes;
+}
+
+static void zero_counters(Exec& e) {
+  e.rounds = e.qb_attempts = e.qb_uncertified = e.syncs = 0;
+  e.jacobi_sweeps = e.cross_calls = e.cross_sweeps = e.taylor_iters = e.cap_hits = 0;
+  e.svd_calls = e.svd_p = e.svd_pd = e.svd_sweeps = 0;
+  e.learned_calls = e.learned_accepted = 0;
+  e.flops = e.bytes = 0.0;
+}
+
+// A child context on stream s over arena a, sharing the parent's device status
+// word, precision, pivot network and recorder; no stream pool (no nesting).
+static void child_exec(const Exec& parent, Exec& c, Arena* a, cudaStream_t s, Prof* prof, int* hi, double* hd,
+                       size_t slot) {
+  if (char* p = parent.pool ? parent.pool->slot(slot) : nullptr) {
+    hi = reinterpret_cast<int*>(p);
+    hd = reinterpret_cast<double*>(p + 64);
+  }
+  c = Exec{};
+  c.s = s;
+  c.ar = a;
+  c.dev_status = parent.dev_status;
+  c.precision = parent.precision;
+  c.pivot_net = parent.pivot_net;
+  c.pivot_rec = parent.pivot_rec;
+  c.h_pinned = hi;
+  c.h_pinned_d = hd;
+  prof->on = parent.prof && parent.prof->on;
+  c.prof = prof;
+  c.pool = nullptr;
+}
+
+static void merge_prof(Exec& ex, const Prof& p) {
+  if (!ex.prof) return;
+  ex.prof->pending.insert(ex.prof->pending.end(), p.pending.begin(), p.pending.end());
+  ex.prof->pool.insert(ex.prof->pool.end(), p.pool.begin(), p.pool.end());
+  for (int k = 0; k < K_NCLASS; ++k) {
+    ex.prof->ms[k] += p.ms[k];
+    ex.prof->flops[k] += p.flops[k];
+    ex.prof->bytes[k] += p.bytes[k];
+    ex.prof->n[k] += p.n[k];
+  }
 }
 
 namespace {
@@ -119,11 +185,7 @@ void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>&
       c.ar.dry = ex.dry;
       c.ex = ex;
       c.ex.ar = ex.dry ? &c.ar : ex.ar;
-      c.ex.rounds = c.ex.qb_attempts = c.ex.qb_uncertified = c.ex.syncs = 0;
-      c.ex.jacobi_sweeps = c.ex.cross_calls = c.ex.cross_sweeps = c.ex.taylor_iters = c.ex.cap_hits = 0;
-      c.ex.svd_calls = c.ex.svd_p = c.ex.svd_pd = c.ex.svd_sweeps = 0;
-      c.ex.learned_calls = c.ex.learned_accepted = 0;
-      c.ex.flops = c.ex.bytes = 0.0;
+      zero_counters(c.ex);
       body(c.ex, i);
       merge_counters(ex, c.ex);
       maxpeak = std::max(maxpeak, c.ar.peak);
@@ -143,18 +205,7 @@ void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>&
     Child& c = ch[i];
     c.ar.base = par.base + par.off + slice * (size_t)i;
     c.ar.cap = slice;
-    c.ex = Exec{};
-    c.ex.s = ex.pool->stream((size_t)i);
-    c.ex.ar = &c.ar;
-    c.ex.dev_status = ex.dev_status;
-    c.ex.precision = ex.precision;
-    c.ex.pivot_net = ex.pivot_net;
-    c.ex.pivot_rec = ex.pivot_rec;
-    c.ex.h_pinned = c.hi;
-    c.ex.h_pinned_d = c.hd;
-    c.prof.on = ex.prof && ex.prof->on;
-    c.ex.prof = &c.prof;
-    c.ex.pool = nullptr;  // no nesting
+    child_exec(ex, c.ex, &c.ar, ex.pool->stream((size_t)i), &c.prof, c.hi, c.hd, (size_t)i + 1);
     TT_CUDA(cudaStreamWaitEvent(c.ex.s, start, 0));
   }
   std::vector<std::thread> th;
@@ -179,19 +230,300 @@ void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>&
     TT_CUDA(cudaEventRecord(done, c.ex.s));
     TT_CUDA(cudaStreamWaitEvent(ex.s, done, 0));
     merge_counters(ex, c.ex);
-    if (ex.prof) {
-      ex.prof->pending.insert(ex.prof->pending.end(), c.prof.pending.begin(), c.prof.pending.end());
-      ex.prof->pool.insert(ex.prof->pool.end(), c.prof.pool.begin(), c.prof.pool.end());
-      for (int k = 0; k < K_NCLASS; ++k) {
-        ex.prof->ms[k] += c.prof.ms[k];
-        ex.prof->flops[k] += c.prof.flops[k];
-        ex.prof->bytes[k] += c.prof.bytes[k];
-        ex.prof->n[k] += c.prof.n[k];
-      }
-    }
+    merge_prof(ex, c.prof);
     if (c.err != TT_OK && first == TT_OK) first = c.err;
   }
   if (first != TT_OK) throw Error{first};
+}
+
+// ---------------------------------------------------------------- task graph
+namespace {
+struct GNode {
+  const char* name = "";
+  int prio = 0;
+  TaskGraph::Fn fn;
+  std::vector<int> in;   // every dependency (the GPU-side waits)
+  std::vector<int> out;  // dependents still counting on this node
+  int pending = 0;       // unfinished dependencies, plus one while held
+  bool done = false;
+  cudaEvent_t ev = nullptr;
+};
+
+struct GWorker {
+  Arena ar;
+  Exec ex;
+  Prof prof;
+  int hi[16];
+  double hd[16];
+};
+
+struct TraceRec {
+  const char* name;
+  int worker;
+  double t0, t1;  // microseconds from the start of run()
+  // the node's own work: host syncs, range-finder attempts, small SVDs and
+  // the sum of their sizes
+  long long syncs, qb, svd, svd_p;
+};
+
+struct Tally {
+  long long syncs, qb, svd, svd_p;
+  explicit Tally(const Exec& e) : syncs(e.syncs), qb(e.qb_attempts), svd(e.svd_calls), svd_p(e.svd_p) {}
+};
+
+// Events of graph nodes are taken from the stream pool above those that
+// parallel_tasks uses (one per task plus the start event).
+constexpr size_t kGraphEvent0 = 64;
+
+thread_local int t_self = -1;
+
+// Runs fn as node id on this thread (TaskGraph::self() answers id meanwhile).
+struct SelfScope {
+  int saved;
+  explicit SelfScope(int id) : saved(t_self) { t_self = id; }
+  ~SelfScope() { t_self = saved; }
+};
+
+const char* trace_path() {
+  static const char* p = std::getenv("TT_TRACE");
+  return (p && *p) ? p : nullptr;
+}
+}  // namespace
+
+struct TaskGraph::Impl {
+  Exec& ex;
+  int workers;
+  bool serial;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<GNode> nodes;
+  std::priority_queue<std::pair<int, int>> ready;  // (priority, -id): high priority, then oldest
+  int remaining = 0;  // nodes not yet finished (held ones included)
+  int running = 0;
+  tt_status err = TT_OK;
+  std::vector<TraceRec> trace;
+  std::chrono::steady_clock::time_point t_start;
+
+  Impl(Exec& e, int w)
+      : ex(e), workers(std::max(1, w)), serial(e.dry || e.pool == nullptr || (e.prof && e.prof->on)) {}
+
+  double now_us() const {
+    return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  void push_ready(int id) {
+    ready.push({nodes[id].prio, -id});
+    cv.notify_one();
+  }
+  // under mu
+  void finish(int id, tt_status st, int worker, double t0, const Tally& before, const Exec& after) {
+    GNode& n = nodes[id];
+    n.done = true;
+    --remaining;
+    --running;
+    for (int o : n.out)
+      if (--nodes[o].pending == 0) push_ready(o);
+    n.out.clear();
+    if (st != TT_OK && err == TT_OK) err = st;
+    if (trace_path())
+      trace.push_back(TraceRec{n.name, worker, t0, now_us(), after.syncs - before.syncs,
+                               after.qb_attempts - before.qb, after.svd_calls - before.svd,
+                               after.svd_p - before.svd_p});
+    cv.notify_all();
+  }
+  void write_trace() {
+    static std::mutex fmu;
+    static long long graph_seq = 0;
+    std::lock_guard<std::mutex> lk(fmu);
+    FILE* f = std::fopen(trace_path(), "a");
+    if (!f) return;
+    const long long g = graph_seq++;
+    for (const TraceRec& r : trace)
+      std::fprintf(f,
+                   "{\"graph\": %lld, \"name\": \"%s\", \"worker\": %d, \"t0_us\": %.1f, \"t1_us\": %.1f, "
+                   "\"syncs\": %lld, \"qb\": %lld, \"svd\": %lld, \"svd_p\": %lld}\n",
+                   g, r.name, r.worker, r.t0, r.t1, r.syncs, r.qb, r.svd, r.svd_p);
+    std::fclose(f);
+  }
+  void run_serial();
+  void run_parallel();
+};
+
+TaskGraph::TaskGraph(Exec& ex, int workers) : im(new Impl(ex, workers)) {}
+TaskGraph::~TaskGraph() { delete im; }
+int TaskGraph::self() { return t_self; }
+
+int TaskGraph::add(const char* name, int priority, Fn fn, const std::vector<int>& deps, bool hold) {
+  std::lock_guard<std::mutex> lk(im->mu);
+  const int id = (int)im->nodes.size();
+  for (int d : deps) TT_REQUIRE(d < id, TT_ERR_ARG);
+  im->nodes.emplace_back();
+  GNode& n = im->nodes.back();
+  n.name = name;
+  n.prio = priority;
+  n.fn = std::move(fn);
+  n.pending = hold ? 1 : 0;
+  for (int d : deps) {
+    if (d < 0) continue;  // "no node": lets callers pass optional dependencies
+    n.in.push_back(d);
+    if (!im->nodes[d].done) {
+      im->nodes[d].out.push_back(id);
+      n.pending++;
+    }
+  }
+  if (!im->serial) n.ev = im->ex.pool->event(kGraphEvent0 + (size_t)id);
+  im->remaining++;
+  if (n.pending == 0) im->push_ready(id);
+  return id;
+}
+
+void TaskGraph::depend(int node, int dep) {
+  std::lock_guard<std::mutex> lk(im->mu);
+  TT_REQUIRE(node >= 0 && node < (int)im->nodes.size() && dep < (int)im->nodes.size(), TT_ERR_ARG);
+  GNode& n = im->nodes[node];
+  TT_REQUIRE(n.pending > 0 && !n.done, TT_ERR_ARG);  // only a held node takes new dependencies
+  if (dep < 0) return;
+  n.in.push_back(dep);
+  if (!im->nodes[dep].done) {
+    im->nodes[dep].out.push_back(node);
+    n.pending++;
+  }
+}
+
+void TaskGraph::release(int node) {
+  std::lock_guard<std::mutex> lk(im->mu);
+  TT_REQUIRE(node >= 0 && node < (int)im->nodes.size(), TT_ERR_ARG);
+  GNode& n = im->nodes[node];
+  TT_REQUIRE(n.pending > 0 && !n.done, TT_ERR_ARG);
+  if (--n.pending == 0) im->push_ready(node);
+}
+
+void TaskGraph::Impl::run_serial() {
+  size_t maxpeak = 0;
+  for (;;) {
+    int id;
+    Fn fn;
+    double t0;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (ready.empty()) break;
+      id = -ready.top().second;
+      ready.pop();
+      running++;
+      fn = std::move(nodes[id].fn);
+      t0 = now_us();
+    }
+    if (ex.dry) {
+      // sizing pass: each node on an arena of its own; the parallel run gives
+      // every worker a slice of the largest footprint
+      Arena a;
+      a.dry = true;
+      Exec e = ex;
+      e.ar = &a;
+      zero_counters(e);
+      SelfScope me(id);
+      fn(e);
+      merge_counters(ex, e);
+      maxpeak = std::max(maxpeak, a.peak);
+      std::lock_guard<std::mutex> lk(mu);
+      finish(id, TT_OK, 0, t0, Tally(ex), ex);
+      continue;
+    }
+    const Tally before(ex);
+    {
+      Scope sc(*ex.ar);
+      SelfScope me(id);
+      fn(ex);
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    finish(id, TT_OK, 0, t0, before, ex);
+  }
+  TT_REQUIRE(remaining == 0, TT_ERR_ARG);  // a held node was never released
+  if (ex.dry) {
+    const size_t need = ex.ar->off + (maxpeak + 256) * (size_t)workers;
+    if (need > ex.ar->peak) ex.ar->peak = need;
+  }
+}
+
+void TaskGraph::Impl::run_parallel() {
+  Arena& par = *ex.ar;
+  const size_t free = par.cap > par.off ? par.cap - par.off : 0;
+  const size_t slice = (free / (size_t)workers) & ~size_t(255);
+  std::vector<GWorker> wk(workers);
+  cudaEvent_t start = ex.pool->event(0);
+  TT_CUDA(cudaEventRecord(start, ex.s));
+  for (int i = 0; i < workers; ++i) {
+    GWorker& w = wk[i];
+    w.ar.base = par.base + par.off + slice * (size_t)i;
+    w.ar.cap = slice;
+    child_exec(ex, w.ex, &w.ar, ex.pool->stream((size_t)i), &w.prof, w.hi, w.hd, (size_t)i + 1);
+    TT_CUDA(cudaStreamWaitEvent(w.ex.s, start, 0));
+  }
+  auto loop = [&](int wi) {
+    GWorker& w = wk[wi];
+    std::vector<cudaEvent_t> waits;
+    for (;;) {
+      int id;
+      Fn fn;
+      cudaEvent_t ev;
+      double t0;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return !ready.empty() || err != TT_OK || remaining == 0 || running == 0; });
+        if (err != TT_OK || remaining == 0) return;
+        if (ready.empty()) {  // nothing runs and nothing is ready: a held node was never released
+          err = TT_ERR_ARG;
+          cv.notify_all();
+          return;
+        }
+        id = -ready.top().second;
+        ready.pop();
+        running++;
+        GNode& n = nodes[id];
+        fn = std::move(n.fn);
+        ev = n.ev;
+        waits.clear();
+        for (int d : n.in) waits.push_back(nodes[d].ev);
+        t0 = now_us();
+      }
+      tt_status st = TT_OK;
+      const Tally before(w.ex);
+      try {
+        for (cudaEvent_t e : waits) TT_CUDA(cudaStreamWaitEvent(w.ex.s, e, 0));
+        Scope sc(w.ar);
+        SelfScope me(id);
+        fn(w.ex);
+        TT_CUDA(cudaEventRecord(ev, w.ex.s));
+      } catch (const Error& e) {
+        st = e.code;
+      } catch (...) {
+        st = TT_ERR_CUDA;
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      finish(id, st, wi, t0, before, w.ex);
+    }
+  };
+  std::vector<std::thread> th;
+  th.reserve(workers);
+  for (int i = 0; i < workers; ++i) th.emplace_back(loop, i);
+  for (std::thread& t : th) t.join();
+  for (int i = 0; i < workers; ++i) {
+    GWorker& w = wk[i];
+    cudaEvent_t done = ex.pool->event((size_t)i + 1);
+    TT_CUDA(cudaEventRecord(done, w.ex.s));
+    TT_CUDA(cudaStreamWaitEvent(ex.s, done, 0));
+    merge_counters(ex, w.ex);
+    merge_prof(ex, w.prof);
+  }
+  if (err != TT_OK) throw Error{err};
+}
+
+void TaskGraph::run() {
+  im->t_start = std::chrono::steady_clock::now();
+  if (im->serial)
+    im->run_serial();
+  else
+    im->run_parallel();
+  if (trace_path() && !im->ex.dry) im->write_trace();
 }
 
 }  // namespace ttfv

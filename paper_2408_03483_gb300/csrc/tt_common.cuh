@@ -105,11 +105,19 @@ struct TT {
 };
 
 // Streams and events for concurrent host tasks (owned by a solver context).
+// Also a block of page-locked host slots, one per concurrent task, for the
+// small device-to-host reads at sync points (a read into pageable memory goes
+// through the driver's staging buffer, which concurrent tasks would share).
 struct StreamPool {
+  static constexpr size_t kSlots = 64, kSlotBytes = 256;  // int[16] then double[16]
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
+  char* pinned = nullptr;
+  bool pinned_failed = false;
   cudaStream_t stream(size_t i);
   cudaEvent_t event(size_t i);
+  // slot i (< kSlots), or null if page-locked memory is unavailable
+  char* slot(size_t i);
   ~StreamPool();
 };
 
@@ -141,11 +149,47 @@ struct Exec {
   StreamPool* pool = nullptr;       // streams for parallel_tasks (null: run tasks in order)
 };
 
+// Wait on the host until ex.s has drained (the sync point of a read-back).
+// A stream synchronize: polling an event with a yield measured the same on
+// the stage graph, a blocking-sync event 6 % slower.
+void host_wait(Exec& ex);
+
 // Run body(child, i) for i < ntasks as concurrent host threads, each on its
 // own stream (ordered after ex.s) with its own slice of the free arena; ex.s
 // then waits for every task.  Counters and profile records merge into ex.
 // Tasks must be independent.  The first task error is rethrown.
 void parallel_tasks(Exec& ex, int ntasks, const std::function<void(Exec&, int)>& body);
+
+// Dependency-driven execution of host tasks.  A node is a host function that
+// queues GPU work on the stream of the Exec it is given; it runs once every
+// node it depends on has run, on one of `workers` host threads, each with its
+// own stream and arena slice, and that stream first waits for the GPU work of
+// its dependencies.  Nodes may add nodes while the graph runs (loops whose trip
+// count is read back from the device); a node added with hold = true also
+// waits for release(), and depend() may give it further dependencies until
+// then.  Scratch a node takes from its arena is released when it returns, so
+// results that outlive a node live in the caller's arena.  Without a stream
+// pool, in the sizing pass and when profiling, nodes run one at a time on ex
+// in priority order.  run() returns once every node has run and ex.s is
+// ordered after their work; it rethrows the first node error.
+class TaskGraph {
+ public:
+  using Fn = std::function<void(Exec&)>;
+  TaskGraph(Exec& ex, int workers);
+  ~TaskGraph();
+  TaskGraph(const TaskGraph&) = delete;
+  TaskGraph& operator=(const TaskGraph&) = delete;
+  int add(const char* name, int priority, Fn fn, const std::vector<int>& deps = {}, bool hold = false);
+  void depend(int node, int dep);
+  void release(int node);
+  void run();
+  // id of the node the calling thread is running (-1 outside a node)
+  static int self();
+
+ private:
+  struct Impl;
+  Impl* im;
+};
 
 // Bracket one kernel launch: counts it, checks the launch, adds its
 // algorithmic flops/bytes to the totals and, when profiling, times it.
