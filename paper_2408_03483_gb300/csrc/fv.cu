@@ -94,7 +94,9 @@ static void taylor_dy(Reciprocal& R, int k, int prev) {
         tt_sum_norm(cx, R.dy[b], sn);
         double v[2];
         fetch_doubles(cx, sn, 2, v);
-        R.err = cx.dry ? 0.0 : v[1] / std::sqrt((double)R.x->n1 * R.x->n2);
+        // the sizing pass runs two iterations: the second multiplies a dy of
+        // full rank, the largest product of the loop
+        R.err = cx.dry ? (k < 2 ? 1.0 : 0.0) : v[1] / std::sqrt((double)R.x->n1 * R.x->n2);
         R.it = k;
         const int me = TaskGraph::self();
         taylor_y(R, b, me);
@@ -872,6 +874,7 @@ tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws
       S.ex.h_pinned = reinterpret_cast<int*>(ps);
       S.ex.h_pinned_d = reinterpret_cast<double*>(ps + 64);
     }
+    S.ex.sync_ev = S.pool.sync_event(0);
     S.ex.prof = &S.prof;
     S.ex.pool = &S.pool;
     S.ex.precision = p->precision;
@@ -1329,7 +1332,7 @@ size_t tt_reciprocal_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int
   return dry_bytes([&](Exec& ex) {
     TT x = fake_tt(*ex.ar, n1, n2, rank_in);
     TT y = fake_tt(*ex.ar, n1, n2, rank_cap);
-    reciprocal(ex, x, 1e-12, rank_cap, 2, y, nullptr);  // the sizing pass stops after one iteration
+    reciprocal(ex, x, 1e-12, rank_cap, 2, y, nullptr);
   });
 }
 

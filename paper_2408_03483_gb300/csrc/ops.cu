@@ -369,6 +369,32 @@ static void finish_counts(Exec& ex, int k, int cap, int rin) {
   if (k == cap && rin > cap) ex.cap_hits++;
 }
 
+// First sketch of the range finder: cap + 8 columns (rounded to 8, at most
+// 112 and the short mode s); the explicit residual check doubles it, up to
+// 112, whenever the range is not yet captured (cap + 8 measured faster than
+// 2 cap and than cap / 2 + 8 on the WENO5 workload).
+static int rf_first_sketch(int s, int cap) { return std::min({112, s, ((cap + 8 + 7) / 8) * 8}); }
+
+// Route of the rounding of a Hadamard product with R = r1 r2 terms.  The
+// factored route (QR of both Khatri-Rao cores, SVD of an R x R factor) costs
+// O(R^3) on one SM per factorisation; when both modes exceed 112 the
+// alternative is the range finder on the formed product, whose cost is set by
+// its sketch width p0 instead, and a product of smooth fields has far lower
+// numerical rank than R, so the first sketch usually certifies.  On the 256^2
+// faces (cap 32, p0 = 40) a factored rounding took 3.7 ms at R = 64 and
+// 9-11 ms at R = 104-112, a range finder certified on its first sketch
+// 3.6 ms, so the factored route is kept up to R = 1.5 p0.  (Sums keep the
+// factored route up to R = 112: their terms are already rounded, so their
+// numerical rank is close to R and the sketch would often have to grow.)
+// Either route gives the truncated SVD, the range finder to within its
+// certified residual.
+static bool factored_route(int n1, int n2, int R, int cap) {
+  const int s = std::min(n1, n2);
+  if (R > 112 || R > s) return false;
+  if (s <= 112) return true;  // the full route would be as exact and no cheaper
+  return 2 * R <= 3 * rf_first_sketch(s, cap);
+}
+
 // (i) Factored route, R <= 112 and R <= min(n1, n2): QR of both cores
 // (TSQR), SVD of the R x R product of the triangular factors.
 template <typename Real>
@@ -452,10 +478,7 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
   sumsq(ex, Yf, n1, n2, n1, kbuf);
   double nrm2[1];
   fetch_doubles(ex, kbuf, 1, nrm2);
-  // first sketch: cap + 8 columns (rounded to 8); the explicit residual check
-  // doubles it, up to 112, whenever the range is not yet captured (cap + 8
-  // measured faster than 2 cap and than cap / 2 + 8 on the WENO5 workload)
-  int p = std::min({112, s, ((cap + 8 + 7) / 8) * 8});
+  int p = rf_first_sketch(s, cap);
   Real* Om = ex.ar->get<Real>((size_t)l * 112);
   Real* S = ex.ar->get<Real>((size_t)s * 112);
   Real* Q = ex.ar->get<Real>((size_t)s * 112);
@@ -590,7 +613,7 @@ RoundInfo round_hadamard(Exec& ex, const TT& X, const TT& Z, double tol, int cap
   debug_finite(ex, Z.b, (long)Z.n2 * Z.r, "round_hadamard Z.b (n1, n2, r)", Z.n1, Z.n2, Z.r);
   Scope sc(*ex.ar);
   const int n1 = X.n1, n2 = X.n2, R = X.r * Z.r;
-  if (R <= 112 && R <= std::min(n1, n2)) {
+  if (factored_route(n1, n2, R, cap)) {
     double* A = ex.ar->get<double>((size_t)n1 * R);
     double* B = ex.ar->get<double>((size_t)n2 * R);
     khatri_rao(ex, X.a, X.r, Z.a, Z.r, n1, A);

@@ -89,11 +89,50 @@ char* StreamPool::slot(size_t i) {
   return pinned + i * kSlotBytes;
 }
 
-void host_wait(Exec& ex) { TT_CUDA(cudaStreamSynchronize(ex.s)); }
+static int sync_mode() {
+  static const int m = [] {
+    const char* e = std::getenv("TT_SYNC");
+    if (!e) return 0;
+    if (e[0] == 'y') return 1;
+    if (e[0] == 'b') return 2;
+    return 0;
+  }();
+  return m;
+}
+
+void host_wait(Exec& ex) {
+  const int m = sync_mode();
+  if (m == 0 || !ex.sync_ev) {
+    TT_CUDA(cudaStreamSynchronize(ex.s));
+    return;
+  }
+  TT_CUDA(cudaEventRecord(ex.sync_ev, ex.s));
+  if (m == 2) {
+    TT_CUDA(cudaEventSynchronize(ex.sync_ev));
+    return;
+  }
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ex.sync_ev);
+    if (e == cudaSuccess) return;
+    if (e != cudaErrorNotReady) throw Error{TT_ERR_CUDA};
+    std::this_thread::yield();
+  }
+}
+
+cudaEvent_t StreamPool::sync_event(size_t i) {
+  if (sync_mode() == 0) return nullptr;
+  while (sync_events.size() <= i) {
+    cudaEvent_t e;
+    TT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming | (sync_mode() == 2 ? cudaEventBlockingSync : 0u)));
+    sync_events.push_back(e);
+  }
+  return sync_events[i];
+}
 
 StreamPool::~StreamPool() {
   for (cudaStream_t s : streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
+  for (cudaEvent_t e : sync_events) cudaEventDestroy(e);
   if (pinned) cudaFreeHost(pinned);
 }
 
@@ -146,6 +185,7 @@ static void child_exec(const Exec& parent, Exec& c, Arena* a, cudaStream_t s, Pr
   prof->on = parent.prof && parent.prof->on;
   c.prof = prof;
   c.pool = nullptr;
+  c.sync_ev = parent.pool ? parent.pool->sync_event(slot) : nullptr;
 }
 
 static void merge_prof(Exec& ex, const Prof& p) {
@@ -262,13 +302,14 @@ struct TraceRec {
   int worker;
   double t0, t1;  // microseconds from the start of run()
   // the node's own work: host syncs, range-finder attempts, small SVDs and
-  // the sum of their sizes
-  long long syncs, qb, svd, svd_p;
+  // the sum of their sizes, cross sweeps
+  long long syncs, qb, svd, svd_p, sweeps;
 };
 
 struct Tally {
-  long long syncs, qb, svd, svd_p;
-  explicit Tally(const Exec& e) : syncs(e.syncs), qb(e.qb_attempts), svd(e.svd_calls), svd_p(e.svd_p) {}
+  long long syncs, qb, svd, svd_p, sweeps;
+  explicit Tally(const Exec& e)
+      : syncs(e.syncs), qb(e.qb_attempts), svd(e.svd_calls), svd_p(e.svd_p), sweeps(e.cross_sweeps) {}
 };
 
 // Events of graph nodes are taken from the stream pool above those that
@@ -327,7 +368,7 @@ struct TaskGraph::Impl {
     if (trace_path())
       trace.push_back(TraceRec{n.name, worker, t0, now_us(), after.syncs - before.syncs,
                                after.qb_attempts - before.qb, after.svd_calls - before.svd,
-                               after.svd_p - before.svd_p});
+                               after.svd_p - before.svd_p, after.cross_sweeps - before.sweeps});
     cv.notify_all();
   }
   void write_trace() {
@@ -340,8 +381,8 @@ struct TaskGraph::Impl {
     for (const TraceRec& r : trace)
       std::fprintf(f,
                    "{\"graph\": %lld, \"name\": \"%s\", \"worker\": %d, \"t0_us\": %.1f, \"t1_us\": %.1f, "
-                   "\"syncs\": %lld, \"qb\": %lld, \"svd\": %lld, \"svd_p\": %lld}\n",
-                   g, r.name, r.worker, r.t0, r.t1, r.syncs, r.qb, r.svd, r.svd_p);
+                   "\"syncs\": %lld, \"qb\": %lld, \"svd\": %lld, \"svd_p\": %lld, \"sweeps\": %lld}\n",
+                   g, r.name, r.worker, r.t0, r.t1, r.syncs, r.qb, r.svd, r.svd_p, r.sweeps);
     std::fclose(f);
   }
   void run_serial();

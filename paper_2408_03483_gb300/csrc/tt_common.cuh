@@ -118,6 +118,8 @@ struct StreamPool {
   cudaEvent_t event(size_t i);
   // slot i (< kSlots), or null if page-locked memory is unavailable
   char* slot(size_t i);
+  cudaEvent_t sync_event(size_t i);  // host-wait event of slot i (TT_SYNC), or null
+  std::vector<cudaEvent_t> sync_events;
   ~StreamPool();
 };
 
@@ -147,6 +149,7 @@ struct Exec {
   double flops = 0.0, bytes = 0.0;
   Prof* prof = nullptr;             // per-class event timing when prof->on
   StreamPool* pool = nullptr;       // streams for parallel_tasks (null: run tasks in order)
+  cudaEvent_t sync_ev = nullptr;    // host_wait event (null: stream synchronize)
 };
 
 // Wait on the host until ex.s has drained (the sync point of a read-back).
