@@ -15,7 +15,10 @@ et al.) with rank adaptation by "kick" fibres, written from that principle:
      right singular vectors, choose new columns J by maxvol;
   3. stop when the current skeleton predicts the next sweep's column fibres to
      relative Frobenius error <= tol, when the rank cap is reached with
-     stationary column pivots, or after max_sweeps sweeps;
+     stationary column pivots, when the skeleton is at the rank cap and a
+     sweep no longer halves that prediction error (a cap-limited skeleton
+     cannot reach tol; further sweeps only reshuffle its pivots), or after
+     max_sweeps sweeps;
   4. return the skeleton X = U_c U_c[I]^{-1} F(I, :), then TT-round it.
 
 Kick indices come from SplitMix64 (Steele, Lea & Flood, 2014) driven by a
@@ -122,8 +125,11 @@ def cross2d(evalF, n1, n2, x0, tol, cap, kick=4, max_sweeps=10, seed=0,
             Uc, I, RI = prev
             pred = Uc @ np.linalg.solve(Uc[I, :], RI[:, Jx])
             nc = np.linalg.norm(C)
+            err_prev = err
             err = np.linalg.norm(C - pred) / nc if nc > 0 else 0.0
             if err <= tol:
+                break
+            if len(I) >= cap and np.isfinite(err_prev) and err > 0.5 * err_prev:
                 break
         Uc = _orth_left(C, tol, cap)
         I = maxvol(Uc)

@@ -395,6 +395,7 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
   std::vector<int> I, Iprev;
   int kprev = 0;
   bool have_prev = false;
+  double prev_err = -1.0;  // prediction error of the previous check
   int sweeps = 0;
   for (int s = 0; s < max_sweeps; ++s) {
     sweeps = s + 1;
@@ -437,6 +438,11 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
         first_check_converged = (s == 1);
         break;
       }
+      // at the rank cap the skeleton cannot reach tol: stop once a sweep no
+      // longer halves the prediction error (further sweeps only reshuffle
+      // the pivots of a cap-limited approximation)
+      if (kprev >= cap && prev_err >= 0.0 && err > 0.5 * prev_err) break;
+      prev_err = err;
     }
     const int kc = orth_left(ex, C, n1, cj, tol, cap, Uc);
     maxvol(ex, Uc, n1, kc, 1e-2, 200, dI);

@@ -247,6 +247,13 @@ struct Solver {
   // converged column pivots of each cross site at its previous call:
   // WENO (direction, field, side, step) = 24 sites, then LLF lambda per direction
   std::vector<int> sites[26];
+  // range-finder sketch width that certified the previous lambda o jump
+  // rounding of each (direction, component) within the current step
+  int rf_hint[2][3] = {};
+  // the previous stage's LLF lambda of each direction (nonlinear SWE) within
+  // the current step: the initial guess of the next lambda cross
+  TT lam_prev[2];
+  bool lam_prev_ok[2] = {false, false};
   ~Solver();
 };
 
@@ -399,8 +406,11 @@ static void flux_linear(Solver& S, const TT qm[3], const TT qp[3], int d, std::v
 // u = round(hu o 1/h), v = round(hv o 1/h), then F = (hu, round(round(hu o u)
 // + g/2 round(h o h)), round(hu o v)) for x faces and G = (hv, round(hv o u),
 // round(round(hv o v) + g/2 round(h o h))) for y faces.  F[0] is left to the caller.
-// lambda = max(|u-| + sqrt(g h-), |u+| + sqrt(g h+)) on the faces by cross
-static void face_lambda(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int d, unsigned seed, TT& lam) {
+// lambda = max(|u-| + sqrt(g h-), |u+| + sqrt(g h+)) on the faces by cross,
+// from the initial guess x0 (the paper leaves it open: h+ at the first
+// stage, then the previous stage's lambda of the same direction)
+static void face_lambda(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int d, unsigned seed, const TT& x0,
+                        TT& lam) {
   const tt_fv_params& p = S.p;
   const int k = d == 0 ? 1 : 2;
   TT ins[4] = {qm[0], qm[k], qp[0], qp[k]};
@@ -411,7 +421,7 @@ static void face_lambda(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int
   fl.site = &S.sites[24 + d];
   fl.prm[0] = p.g;
   const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
-  cross(ex, fl, qm[0].n1, qm[0].n2, qp[0], p.tol, p.rank_cap, kick, sweeps, seed, lam);
+  cross(ex, fl, qm[0].n1, qm[0].n2, x0, p.tol, p.rank_cap, kick, sweeps, seed, lam);
 }
 
 // LLF combination of one component (Eq. LLF-TT): with dd = round(Q+ - Q-) and
@@ -632,7 +642,16 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
         }, {vel_node[d][sd][comp - 1], face[d][k][sd], comp == k ? hh_node[d][sd] : -1});
     }
     lam_node[d] = G.add("llf_lambda", 85, [&, d](Exec& cx) {
-      face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, lam[d]);
+      // lambda moves little from one stage to the next: the previous
+      // stage's lambda is the initial guess (its pivots sit on the kinks
+      // of the max), except for the learned start, whose proposals are
+      // features of h+ as in training
+      const bool warm = S.lam_prev_ok[d] && cx.pivot_net == nullptr;
+      face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, warm ? S.lam_prev[d] : qp[d][0], lam[d]);
+      if (!cx.dry) {
+        copy_tt(cx, lam[d], S.lam_prev[d]);
+        S.lam_prev_ok[d] = true;
+      }
       mark(1);
     }, {face[d][0][0], face[d][0][1], face[d][k][0], face[d][k][1]});
     for (int c = 0; c < 3; ++c) {
@@ -641,7 +660,16 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
         mark(1);
       }, {face[d][c][0], face[d][c][1]});
       ld_node[d][c] = G.add("lambda_o_jump", 55, [&, d, c](Exec& cx) {
-        round_hadamard(cx, lam[d], dd[d][c], tol, cap, ld[d][c]);
+        // the product of a non-smooth lambda and a jump keeps a wide numerical
+        // rank: its sketch starts at the width that certified last time
+        cx.rf_hint = &S.rf_hint[d][c];
+        try {
+          round_hadamard(cx, lam[d], dd[d][c], tol, cap, ld[d][c]);
+        } catch (...) {
+          cx.rf_hint = nullptr;
+          throw;
+        }
+        cx.rf_hint = nullptr;
         mark(1);
       }, {lam_node[d], dd_node});
     }
@@ -694,6 +722,14 @@ static unsigned stage_seed(const Solver& S, int stage) { return S.p.seed + 1000u
 
 static void run_stage(Solver& S, Exec& ex, int stage) {
   TT_REQUIRE(stage == S.next_stage, TT_ERR_ARG);
+  if (stage == 0) {
+    // the lambda guesses and sketch widths carried between stages are
+    // per-step state: a solver restarted from a checkpoint of Q (taken
+    // between steps) repeats the next step bit for bit
+    S.lam_prev_ok[0] = S.lam_prev_ok[1] = false;
+    for (int d = 0; d < 2; ++d)
+      for (int c = 0; c < 3; ++c) S.rf_hint[d][c] = 0;
+  }
   Scope sc(*ex.ar);
   const tt_fv_params& p = S.p;
   TT f[3];
@@ -824,6 +860,13 @@ extern "C" {
 
 const char* tt_fv_version(void) { return "tt_fv 0.2 (sm_103a, FP64 path + FP32/TF32/BF16 precision forms)"; }
 
+// persistent state beside Q: the previous stage's lambda of each direction
+static void alloc_lambda_prev(Solver& S) {
+  if (S.p.eqn == TT_LINEAR) return;
+  S.lam_prev[0] = alloc_tt(S.ar, S.p.nx, S.nq * S.p.ny, S.p.rank_cap);
+  S.lam_prev[1] = alloc_tt(S.ar, S.nq * S.p.nx, S.p.ny, S.p.rank_cap);
+}
+
 static size_t solver_bytes(const tt_fv_params* p, bool with_state) {
   // dry run of one stage at the rank cap
   Solver S;
@@ -842,6 +885,7 @@ static size_t solver_bytes(const tt_fv_params* p, bool with_state) {
       S.Qs[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
       S.Qn[c].r = S.Qs[c].r = p->rank_cap;
     }
+    alloc_lambda_prev(S);
     (void)with_state;
     for (int st = 0; st < 3; ++st) run_stage(S, ex, st);
   } catch (const Error&) {
@@ -874,7 +918,6 @@ tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws
       S.ex.h_pinned = reinterpret_cast<int*>(ps);
       S.ex.h_pinned_d = reinterpret_cast<double*>(ps + 64);
     }
-    S.ex.sync_ev = S.pool.sync_event(0);
     S.ex.prof = &S.prof;
     S.ex.pool = &S.pool;
     S.ex.precision = p->precision;
@@ -884,6 +927,7 @@ tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws
       copy_tt(S.ex, to_tt(q0[c]), S.Qn[c]);
       copy_tt(S.ex, to_tt(q0[c]), S.Qs[c]);
     }
+    alloc_lambda_prev(S);
     S.ar.peak = S.ar.off;
   } catch (const Error& e) {
     delete ctx;

@@ -479,6 +479,9 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
   double nrm2[1];
   fetch_doubles(ex, kbuf, 1, nrm2);
   int p = rf_first_sketch(s, cap);
+  // a call site that keeps needing a wider sketch starts at the width that
+  // certified its previous rounding
+  if (ex.rf_hint && *ex.rf_hint > p) p = std::min({112, s, *ex.rf_hint});
   Real* Om = ex.ar->get<Real>((size_t)l * 112);
   Real* S = ex.ar->get<Real>((size_t)s * 112);
   Real* Q = ex.ar->get<Real>((size_t)s * 112);
@@ -486,6 +489,26 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
   Real* E = ex.ar->get<Real>((size_t)s * l);
   Real* I = ex.ar->get<Real>((size_t)112 * 112);
   double resid2 = 0.0;
+  // SVD of Q^T W0 = WT^T = (Q_W R_W)^T = R_W^T Q_W^T for the current sketch
+  QRTreeT<Real> tw;
+  double* US = nullptr;
+  double* V = nullptr;
+  int k = 0;
+  double tl[2] = {0.0, 0.0};
+  auto svd_of_projection = [&] {
+    tsqr(ex, WT, l, p, l, tw);
+    Real* Mr = ex.ar->get<Real>((size_t)p * p);
+    transpose(ex, tw.R, p, p, p, Mr, p);
+    const double* M = as_double(ex, Mr, (long)p * p);
+    debug_finite(ex, M, (long)p * p, "range-finder core M (n1, n2, p)", n1, n2, p);
+    US = ex.ar->get<double>((size_t)p * p);
+    V = ex.ar->get<double>((size_t)p * p);
+    double* sig = ex.ar->get<double>(p);
+    jacobi_svd(ex, M, p, tol, cap, US, V, sig, kd, tail);
+    k = fetch_svd_info(ex, kd, p);
+    if (ex.dry) k = std::min(cap, p);
+    fetch_doubles(ex, tail, 2, tl);
+  };
   for (int attempt = 0;; ++attempt) {
     ex.qb_attempts++;
     const size_t mk = ex.ar->mark();
@@ -512,8 +535,10 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
     fetch_doubles(ex, kbuf + 1, 1, r2);
     resid2 = r2[0];
     const bool ok = resid2 <= tau * tau * nrm2[0];
-    if (ok || p >= std::min(112, s) || ex.dry) {
+    const bool accept = ok || p >= std::min(112, s) || ex.dry;
+    if (accept) {
       if (!ok && !ex.dry) ex.qb_uncertified++;
+      if (ex.rf_hint && !ex.dry) *ex.rf_hint = p;
       // keep S/ts scratch alive: release nothing allocated after mark
       (void)mk;
       break;
@@ -521,21 +546,7 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
     ex.ar->reset(mk);
     p = std::min({112, s, 2 * p});
   }
-  // SVD of Q^T W0 = WT^T = (Q_W R_W)^T = R_W^T Q_W^T
-  QRTreeT<Real> tw;
-  tsqr(ex, WT, l, p, l, tw);
-  Real* Mr = ex.ar->get<Real>((size_t)p * p);
-  transpose(ex, tw.R, p, p, p, Mr, p);
-  const double* M = as_double(ex, Mr, (long)p * p);
-  debug_finite(ex, M, (long)p * p, "range-finder core M (n1, n2, p)", n1, n2, p);
-  double* US = ex.ar->get<double>((size_t)p * p);
-  double* V = ex.ar->get<double>((size_t)p * p);
-  double* sig = ex.ar->get<double>(p);
-  jacobi_svd(ex, M, p, tol, cap, US, V, sig, kd, tail);
-  int k = fetch_svd_info(ex, kd, p);
-  if (ex.dry) k = std::min(cap, p);
-  double tl[2];
-  fetch_doubles(ex, tail, 2, tl);
+  svd_of_projection();
   // s-side core Q (U S)_k, l-side core Q_W V_k
   if constexpr (std::is_same<Real, double>::value) {
     gemm(ex, s, k, p, 1.0, Q, 1, s, US, 1, p, 0.0, Aw, s);

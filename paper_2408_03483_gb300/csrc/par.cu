@@ -89,50 +89,11 @@ char* StreamPool::slot(size_t i) {
   return pinned + i * kSlotBytes;
 }
 
-static int sync_mode() {
-  static const int m = [] {
-    const char* e = std::getenv("TT_SYNC");
-    if (!e) return 0;
-    if (e[0] == 'y') return 1;
-    if (e[0] == 'b') return 2;
-    return 0;
-  }();
-  return m;
-}
-
-void host_wait(Exec& ex) {
-  const int m = sync_mode();
-  if (m == 0 || !ex.sync_ev) {
-    TT_CUDA(cudaStreamSynchronize(ex.s));
-    return;
-  }
-  TT_CUDA(cudaEventRecord(ex.sync_ev, ex.s));
-  if (m == 2) {
-    TT_CUDA(cudaEventSynchronize(ex.sync_ev));
-    return;
-  }
-  for (;;) {
-    const cudaError_t e = cudaEventQuery(ex.sync_ev);
-    if (e == cudaSuccess) return;
-    if (e != cudaErrorNotReady) throw Error{TT_ERR_CUDA};
-    std::this_thread::yield();
-  }
-}
-
-cudaEvent_t StreamPool::sync_event(size_t i) {
-  if (sync_mode() == 0) return nullptr;
-  while (sync_events.size() <= i) {
-    cudaEvent_t e;
-    TT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming | (sync_mode() == 2 ? cudaEventBlockingSync : 0u)));
-    sync_events.push_back(e);
-  }
-  return sync_events[i];
-}
+void host_wait(Exec& ex) { TT_CUDA(cudaStreamSynchronize(ex.s)); }
 
 StreamPool::~StreamPool() {
   for (cudaStream_t s : streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
-  for (cudaEvent_t e : sync_events) cudaEventDestroy(e);
   if (pinned) cudaFreeHost(pinned);
 }
 
@@ -185,7 +146,6 @@ static void child_exec(const Exec& parent, Exec& c, Arena* a, cudaStream_t s, Pr
   prof->on = parent.prof && parent.prof->on;
   c.prof = prof;
   c.pool = nullptr;
-  c.sync_ev = parent.pool ? parent.pool->sync_event(slot) : nullptr;
 }
 
 static void merge_prof(Exec& ex, const Prof& p) {

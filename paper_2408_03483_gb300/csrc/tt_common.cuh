@@ -118,8 +118,6 @@ struct StreamPool {
   cudaEvent_t event(size_t i);
   // slot i (< kSlots), or null if page-locked memory is unavailable
   char* slot(size_t i);
-  cudaEvent_t sync_event(size_t i);  // host-wait event of slot i (TT_SYNC), or null
-  std::vector<cudaEvent_t> sync_events;
   ~StreamPool();
 };
 
@@ -149,12 +147,15 @@ struct Exec {
   double flops = 0.0, bytes = 0.0;
   Prof* prof = nullptr;             // per-class event timing when prof->on
   StreamPool* pool = nullptr;       // streams for parallel_tasks (null: run tasks in order)
-  cudaEvent_t sync_ev = nullptr;    // host_wait event (null: stream synchronize)
+  // range-finder sketch width of the calling site: read as the first
+  // sketch's width when larger than the default, set to the certified width
+  // (null: default first sketch)
+  int* rf_hint = nullptr;
 };
 
 // Wait on the host until ex.s has drained (the sync point of a read-back).
 // A stream synchronize: polling an event with a yield measured the same on
-// the stage graph, a blocking-sync event 6 % slower.
+// the stage graph (16 to 32 workers), a blocking-sync event 6 % slower.
 void host_wait(Exec& ex);
 
 // Run body(child, i) for i < ntasks as concurrent host threads, each on its

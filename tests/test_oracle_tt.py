@@ -181,6 +181,26 @@ def test_cross_recovers_low_rank(r):
     assert info["rank"] == r
 
 
+def test_cross_cap_limited_stops_on_stagnation():
+    # singular values 0.7^k: at cap 10 the skeleton cannot reach tol 1e-12;
+    # the cross stops once a sweep no longer halves its prediction error,
+    # well before max_sweeps, with an error within a small factor of the
+    # best rank-10 approximation's (sigma_10 / ||F|| ~ 2.8e-2 here)
+    n1, n2, r = 90, 120, 40
+    rng = np.random.default_rng(31)
+    U, _ = np.linalg.qr(rng.standard_normal((n1, r)))
+    V, _ = np.linalg.qr(rng.standard_normal((n2, r)))
+    s = 0.7 ** np.arange(r)
+    F = (U * s) @ V.T
+    best = np.sqrt(np.sum(s[10:] ** 2)) / np.linalg.norm(s)
+    x0 = random_tt(n1, n2, 2, seed=5)
+    Y, info = CR.cross2d(lambda I, J: F[np.ix_(I, J)], n1, n2, x0, 1e-12, 10, kick=4,
+                         max_sweeps=30, return_info=True)
+    assert info["rank"] == 10
+    assert info["sweeps"] < 30
+    assert best <= rel(T.full(Y), F) <= 10 * best
+
+
 def test_cross_weno_step1_against_full():
     n = 40
     w = workload("nonlinear256_weno5", n=n)
