@@ -224,10 +224,18 @@ int fetch_int(Exec& ex, const int* d) {
   prof_flush(ex);
   return ex.h_pinned[0];
 }
-int fetch_svd_info(Exec& ex, const int* d, int p) {
-  if (ex.dry) return -1;
+int fetch_svd_info(Exec& ex, const int* d, int p, const double* tail, double* tl) {
+  if (ex.dry) {
+    if (tl) tl[0] = tl[1] = 0.0;
+    return -1;
+  }
   TT_CUDA(cudaMemcpyAsync(ex.h_pinned, d, 3 * sizeof(int), cudaMemcpyDeviceToHost, ex.s));
+  if (tail) TT_CUDA(cudaMemcpyAsync(ex.h_pinned_d, tail, 2 * sizeof(double), cudaMemcpyDeviceToHost, ex.s));
   host_wait(ex);
+  if (tail) {
+    tl[0] = ex.h_pinned_d[0];
+    tl[1] = ex.h_pinned_d[1];
+  }
   ex.syncs++;
   prof_flush(ex);
   ex.svd_calls++;
@@ -416,10 +424,9 @@ static RoundInfo round_factored(Exec& ex, const double* A, const double* B, int 
   int* kd = ex.ar->get<int>(4);
   double* tail = ex.ar->get<double>(2);
   jacobi_svd(ex, M, R, tol, cap, US, V, sig, kd, tail);
-  int k = fetch_svd_info(ex, kd, R);
-  if (ex.dry) k = std::min(cap, R);
   double tl[2];
-  fetch_doubles(ex, tail, 2, tl);
+  int k = fetch_svd_info(ex, kd, R, tail, tl);
+  if (ex.dry) k = std::min(cap, R);
   tsqr_apply2(ex, ta, (const double*)US, (long)R, Y.a, (long)Y.n1, tb, (const double*)V, (long)R, Y.b,
               (long)Y.n2, k);
   Y.r = k;
@@ -462,10 +469,9 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
     double* V = ex.ar->get<double>((size_t)s * s);
     double* sig = ex.ar->get<double>(s);
     jacobi_svd(ex, M, s, tol, cap, US, V, sig, kd, tail);
-    int k = fetch_svd_info(ex, kd, s);
-    if (ex.dry) k = std::min(cap, s);
     double tl[2];
-    fetch_doubles(ex, tail, 2, tl);
+    int k = fetch_svd_info(ex, kd, s, tail, tl);
+    if (ex.dry) k = std::min(cap, s);
     // W0 = R^T Q_W^T = U S V^T Q_W^T: s-side core U S, l-side core Q_W V
     scaled_copy(ex, Aw, US, (long)s * k, 1.0);
     apply_to_core(ex, tw, V, k, s, Bw);
@@ -475,9 +481,8 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
   }
   // ---- randomized range finder (s > 112)
   const double tau = qb_target_t<Real>(tol);
-  sumsq(ex, Yf, n1, n2, n1, kbuf);
-  double nrm2[1];
-  fetch_doubles(ex, kbuf, 1, nrm2);
+  sumsq(ex, Yf, n1, n2, n1, kbuf);  // ||W0||^2, read with the first residual
+  double nrm2 = 0.0;
   int p = rf_first_sketch(s, cap);
   // a call site that keeps needing a wider sketch starts at the width that
   // certified its previous rounding
@@ -505,9 +510,8 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
     V = ex.ar->get<double>((size_t)p * p);
     double* sig = ex.ar->get<double>(p);
     jacobi_svd(ex, M, p, tol, cap, US, V, sig, kd, tail);
-    k = fetch_svd_info(ex, kd, p);
+    k = fetch_svd_info(ex, kd, p, tail, tl);
     if (ex.dry) k = std::min(cap, p);
-    fetch_doubles(ex, tail, 2, tl);
   };
   for (int attempt = 0;; ++attempt) {
     ex.qb_attempts++;
@@ -531,10 +535,11 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
       convert(ex, E, Yf, (long)s * l);
     lp_gemm<Real>(ex, s, l, p, Real(-1), Q, 1, s, WT, l, 1, Real(1), E, s);
     sumsq(ex, E, s, l, s, kbuf + 1);
-    double r2[1];
-    fetch_doubles(ex, kbuf + 1, 1, r2);
-    resid2 = r2[0];
-    const bool ok = resid2 <= tau * tau * nrm2[0];
+    double v[2];
+    fetch_doubles(ex, kbuf, 2, v);
+    nrm2 = v[0];
+    resid2 = v[1];
+    const bool ok = resid2 <= tau * tau * nrm2;
     const bool accept = ok || p >= std::min(112, s) || ex.dry;
     if (accept) {
       if (!ok && !ex.dry) ex.qb_uncertified++;

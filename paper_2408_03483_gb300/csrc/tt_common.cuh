@@ -224,8 +224,9 @@ inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
 // Copy n ints/doubles from device to the pinned buffer and wait (a sync point).
 int fetch_int(Exec& ex, const int* d);
 // Reads the small-SVD info triple (k, deflated rank, sweeps) of a p x p SVD,
-// accounts it, and returns k.
-int fetch_svd_info(Exec& ex, const int* d, int p);
+// accounts it, and returns k; with tail, also its two tail doubles into tl
+// (one sync for both).
+int fetch_svd_info(Exec& ex, const int* d, int p, const double* tail = nullptr, double* tl = nullptr);
 void fetch_doubles(Exec& ex, const double* d, int n, double* out);
 
 // TT_DEBUG_SYNC=1: every launch is waited for, and debug_finite() copies an
