@@ -10,9 +10,12 @@ et al.) with rank adaptation by "kick" fibres, written from that principle:
   1. column pivots J from the maxvol rows of an orthonormal basis of the
      initial guess's second core;
   2. sweep: evaluate the column fibres F(:, J u kick), take their leading
-     left singular vectors (truncated at tol and the rank cap), choose rows I
-     by maxvol; evaluate the row fibres F(I u kick, :), take their leading
-     right singular vectors, choose new columns J by maxvol;
+     left singular vectors (truncated at tol / 2 and the rank cap), choose
+     rows I by maxvol; evaluate the row fibres F(I u kick, :), take their
+     leading right singular vectors (same truncation), choose new columns J
+     by maxvol.  The fibre truncation sits below the convergence test's tol:
+     a skeleton truncated at tol itself predicts fresh fibres to about tol,
+     and the test of step 3 would pass or fail on their noise;
   3. stop when the current skeleton predicts the next sweep's column fibres to
      relative Frobenius error <= tol, when the rank cap is reached with
      stationary column pivots, when the skeleton is at the rank cap and a
@@ -131,12 +134,12 @@ def cross2d(evalF, n1, n2, x0, tol, cap, kick=4, max_sweeps=10, seed=0,
                 break
             if len(I) >= cap and np.isfinite(err_prev) and err > 0.5 * err_prev:
                 break
-        Uc = _orth_left(C, tol, cap)
+        Uc = _orth_left(C, 0.5 * tol, cap)
         I = maxvol(Uc)
         Ix = list(I) + kick_indices(n1, min(kick, n1 - len(I)), seed, 2 * s + 1, I)
         R = evalF(np.array(Ix), cols)
         prev = (Uc, I, R[:len(I), :])
-        Vr = _orth_left(R.T, tol, cap)
+        Vr = _orth_left(R.T, 0.5 * tol, cap)
         Jn = maxvol(Vr)
         if len(Jn) >= cap and set(Jn) == set(J):
             break  # rank cap reached with stationary pivots: no further gain

@@ -444,7 +444,10 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
       if (kprev >= cap && prev_err >= 0.0 && err > 0.5 * prev_err) break;
       prev_err = err;
     }
-    const int kc = orth_left(ex, C, n1, cj, tol, cap, Uc);
+    // fibre bases truncated at tol / 2: a skeleton truncated at the test's
+    // own tol would sit at the convergence threshold and its check would
+    // pass or fail on the noise of the fresh kick fibres
+    const int kc = orth_left(ex, C, n1, cj, 0.5 * tol, cap, Uc);
     maxvol(ex, Uc, n1, kc, 1e-2, 200, dI);
     I = fetch_idx(ex, dI, kc);
     std::vector<int> Ix = I;
@@ -497,7 +500,7 @@ int cross(Exec& ex, const CrossFn& f, int n1, int n2, const TT& x0, double tol, 
         break;
       }
     }
-    const int kr = orth_left(ex, RT, n2, ri, tol, cap, Vr);
+    const int kr = orth_left(ex, RT, n2, ri, 0.5 * tol, cap, Vr);
     maxvol(ex, Vr, n2, kr, 1e-2, 200, dJ);
     std::vector<int> Jn = fetch_idx(ex, dJ, kr);
     // rank cap reached with stationary pivots: a further sweep gains nothing

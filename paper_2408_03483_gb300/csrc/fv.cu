@@ -644,10 +644,19 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
     lam_node[d] = G.add("llf_lambda", 85, [&, d](Exec& cx) {
       // lambda moves little from one stage to the next: the previous
       // stage's lambda is the initial guess (its pivots sit on the kinks
-      // of the max), except for the learned start, whose proposals are
-      // features of h+ as in training
-      const bool warm = S.lam_prev_ok[d] && cx.pivot_net == nullptr;
-      face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, warm ? S.lam_prev[d] : qp[d][0], lam[d]);
+      // of the max), started by maxvol on it also in the learned form,
+      // whose network was trained on h+ guesses (it proposes the first
+      // stage's lambda pivots and every WENO face's)
+      const bool warm = S.lam_prev_ok[d];
+      const MlpNet* net = cx.pivot_net;
+      if (warm) cx.pivot_net = nullptr;
+      try {
+        face_lambda(S, cx, qm[d], qp[d], d, seed + 64u * d + 40u, warm ? S.lam_prev[d] : qp[d][0], lam[d]);
+      } catch (...) {
+        cx.pivot_net = net;
+        throw;
+      }
+      cx.pivot_net = net;
       if (!cx.dry) {
         copy_tt(cx, lam[d], S.lam_prev[d]);
         S.lam_prev_ok[d] = true;

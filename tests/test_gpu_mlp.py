@@ -187,7 +187,10 @@ def test_shipped_network_gain_over_plain_maxvol(api):
             st = s.stats()
             sweeps[mode] += st["cross_sweeps"]
             if mode == "learned":
-                assert st["learned_calls"] == st["cross_calls"] > 0
+                # every cross starts from the network's proposal except the
+                # lambda crosses of stages 1 and 2 (2 directions each), which
+                # start from the previous stage's lambda by maxvol
+                assert st["learned_calls"] == st["cross_calls"] - 4 > 0
                 got = s.get()
                 ref = FA.ssprk3_step([T.full(q) for q in Q], "nonlinear", "weno5", p, p["dt"])
                 scale = np.linalg.norm(ref[0])
