@@ -340,16 +340,12 @@ static void weno_side(Solver& S, Exec& ex, const TT& q, int d, int fieldc, int k
   // initial guess of Step 2: the Step-1 result repeated over the Gauss points
   TT x0 = d == 0 ? alloc_tt(*ex.ar, n1, 3 * n2, vt.r) : alloc_tt(*ex.ar, 3 * n1, n2, vt.r);
   x0.r = vt.r;
-  for (int c = 0; c < vt.r; ++c) {
-    if (d == 0) {
-      scaled_copy(ex, x0.a + (size_t)c * n1, vt.a + (size_t)c * n1, n1, 1.0);
-      for (int m = 0; m < 3; ++m)
-        scaled_copy(ex, x0.b + (size_t)c * 3 * n2 + m * n2, vt.b + (size_t)c * n2, n2, 1.0);
-    } else {
-      scaled_copy(ex, x0.b + (size_t)c * n2, vt.b + (size_t)c * n2, n2, 1.0);
-      for (int m = 0; m < 3; ++m)
-        scaled_copy(ex, x0.a + (size_t)c * 3 * n1 + m * n1, vt.a + (size_t)c * n1, n1, 1.0);
-    }
+  if (d == 0) {
+    scaled_copy(ex, x0.a, vt.a, (long)n1 * vt.r, 1.0);
+    repeat_rows(ex, x0.b, vt.b, n2, vt.r, 3);
+  } else {
+    scaled_copy(ex, x0.b, vt.b, (long)n2 * vt.r, 1.0);
+    repeat_rows(ex, x0.a, vt.a, n1, vt.r, 3);
   }
   CrossFn f2n;
   f2n.fn = TT_FN_WENO_S2;

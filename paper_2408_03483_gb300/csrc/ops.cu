@@ -18,6 +18,13 @@ __global__ void k_scaled_copy(double* __restrict__ dst, const double* __restrict
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
     dst[t] = a * src[t];
 }
+__global__ void k_repeat_rows(double* __restrict__ dst, const double* __restrict__ src, int n, int r, int reps) {
+  const long per = (long)n * reps, total = per * r;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long c = t / per;
+    dst[t] = src[c * n + (t - c * per) % n];
+  }
+}
 __global__ void k_fill(double* __restrict__ dst, long n, double v) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) dst[t] = v;
 }
@@ -27,6 +34,12 @@ static int grid_for(long n) { return std::max(1, std::min(ceil_div(n, 256), 1184
 void scaled_copy(Exec& ex, double* dst, const double* src, long n, double alpha) {
   if (n <= 0 || ex.dry) return;
   TT_KERNEL(ex, K_OTHER, n, 16.0 * n, k_scaled_copy<<<grid_for(n), 256, 0, ex.s>>>(dst, src, n, alpha));
+}
+void repeat_rows(Exec& ex, double* dst, const double* src, int n, int r, int reps) {
+  const long total = (long)n * reps * r;
+  if (total <= 0 || ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, 0, 8.0 * (total + (double)n * r),
+            k_repeat_rows<<<grid_for(total), 256, 0, ex.s>>>(dst, src, n, r, reps));
 }
 void fill(Exec& ex, double* dst, long n, double v) {
   if (n <= 0 || ex.dry) return;
@@ -62,6 +75,7 @@ bool debug_sync() {
 
 void prof_end(Exec& ex, cudaEvent_t a, int cls, double flops, double bytes, const char* what) {
   const unsigned long long idx = g_launches.fetch_add(1, std::memory_order_relaxed);
+  ex.launches++;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && debug_sync()) e = cudaStreamSynchronize(ex.s);
   if (e != cudaSuccess) {
@@ -549,6 +563,9 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
       break;
     }
     ex.ar->reset(mk);
+    // doubled (growing by half, 40 -> 64 -> 96, measured 10 % slower on the
+    // WENO5 step: most lambda o jump products need more than 64 columns and
+    // then took 96 instead of 80)
     p = std::min({112, s, 2 * p});
   }
   svd_of_projection();

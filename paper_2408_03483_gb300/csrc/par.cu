@@ -102,6 +102,7 @@ static void merge_counters(Exec& dst, const Exec& src) {
   dst.rounds += src.rounds;
   dst.learned_calls += src.learned_calls;
   dst.learned_accepted += src.learned_accepted;
+  dst.launches += src.launches;
   dst.qb_attempts += src.qb_attempts;
   dst.qb_uncertified += src.qb_uncertified;
   dst.syncs += src.syncs;
@@ -122,7 +123,7 @@ static void zero_counters(Exec& e) {
   e.rounds = e.qb_attempts = e.qb_uncertified = e.syncs = 0;
   e.jacobi_sweeps = e.cross_calls = e.cross_sweeps = e.taylor_iters = e.cap_hits = 0;
   e.svd_calls = e.svd_p = e.svd_pd = e.svd_sweeps = 0;
-  e.learned_calls = e.learned_accepted = 0;
+  e.learned_calls = e.learned_accepted = e.launches = 0;
   e.flops = e.bytes = 0.0;
 }
 
@@ -262,14 +263,15 @@ struct TraceRec {
   int worker;
   double t0, t1;  // microseconds from the start of run()
   // the node's own work: host syncs, range-finder attempts, small SVDs and
-  // the sum of their sizes, cross sweeps
-  long long syncs, qb, svd, svd_p, sweeps;
+  // the sum of their sizes, cross sweeps, kernel launches
+  long long syncs, qb, svd, svd_p, sweeps, launches;
 };
 
 struct Tally {
-  long long syncs, qb, svd, svd_p, sweeps;
+  long long syncs, qb, svd, svd_p, sweeps, launches;
   explicit Tally(const Exec& e)
-      : syncs(e.syncs), qb(e.qb_attempts), svd(e.svd_calls), svd_p(e.svd_p), sweeps(e.cross_sweeps) {}
+      : syncs(e.syncs), qb(e.qb_attempts), svd(e.svd_calls), svd_p(e.svd_p), sweeps(e.cross_sweeps),
+        launches(e.launches) {}
 };
 
 // Events of graph nodes are taken from the stream pool above those that
@@ -328,7 +330,8 @@ struct TaskGraph::Impl {
     if (trace_path())
       trace.push_back(TraceRec{n.name, worker, t0, now_us(), after.syncs - before.syncs,
                                after.qb_attempts - before.qb, after.svd_calls - before.svd,
-                               after.svd_p - before.svd_p, after.cross_sweeps - before.sweeps});
+                               after.svd_p - before.svd_p, after.cross_sweeps - before.sweeps,
+                               after.launches - before.launches});
     cv.notify_all();
   }
   void write_trace() {
@@ -341,8 +344,9 @@ struct TaskGraph::Impl {
     for (const TraceRec& r : trace)
       std::fprintf(f,
                    "{\"graph\": %lld, \"name\": \"%s\", \"worker\": %d, \"t0_us\": %.1f, \"t1_us\": %.1f, "
-                   "\"syncs\": %lld, \"qb\": %lld, \"svd\": %lld, \"svd_p\": %lld, \"sweeps\": %lld}\n",
-                   g, r.name, r.worker, r.t0, r.t1, r.syncs, r.qb, r.svd, r.svd_p, r.sweeps);
+                   "\"syncs\": %lld, \"qb\": %lld, \"svd\": %lld, \"svd_p\": %lld, \"sweeps\": %lld, "
+                   "\"launches\": %lld}\n",
+                   g, r.name, r.worker, r.t0, r.t1, r.syncs, r.qb, r.svd, r.svd_p, r.sweeps, r.launches);
     std::fclose(f);
   }
   void run_serial();

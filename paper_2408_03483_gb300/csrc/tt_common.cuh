@@ -144,6 +144,7 @@ struct Exec {
   long long taylor_iters = 0, cap_hits = 0;
   long long svd_calls = 0, svd_p = 0, svd_pd = 0, svd_sweeps = 0;
   long long learned_calls = 0, learned_accepted = 0;
+  long long launches = 0;           // kernels this context launched
   double flops = 0.0, bytes = 0.0;
   Prof* prof = nullptr;             // per-class event timing when prof->on
   StreamPool* pool = nullptr;       // streams for parallel_tasks (null: run tasks in order)
@@ -308,5 +309,8 @@ void tc_gemm(Exec& ex, int precision, bool split, int M, int N, int K, float alp
 // Elementwise helpers (ops.cu)
 void scaled_copy(Exec& ex, double* dst, const double* src, long n, double alpha);
 void fill(Exec& ex, double* dst, long n, double v);
+// dst (reps n x r, column-major) = src (n x r) repeated reps times down each
+// column: dst[c (reps n) + m n + i] = src[c n + i]
+void repeat_rows(Exec& ex, double* dst, const double* src, int n, int r, int reps);
 
 }  // namespace ttfv
