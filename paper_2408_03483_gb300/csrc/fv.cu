@@ -89,14 +89,15 @@ static void taylor_dy(Reciprocal& R, int k, int prev) {
   R.G->add(
       "taylor_dy", R.prio,
       [&R, k, b](Exec& cx) {
-        round_hadamard(cx, R.dy[b ^ 1], R.xt, R.tol, R.cap, R.dy[b]);
-        double* sn = cx.ar->get<double>(2);
-        tt_sum_norm(cx, R.dy[b], sn);
-        double v[2];
-        fetch_doubles(cx, sn, 2, v);
+        const RoundInfo ri = round_hadamard(cx, R.dy[b ^ 1], R.xt, R.tol, R.cap, R.dy[b]);
+        // ||dy||_F of the rounded product from its rounding: the kept part
+        // of the truncated SVD, ||M||^2 - (discarded)^2 (the range finder's
+        // residual is outside M), so the stop test needs no kernel or sync
+        const double kept2 = ri.norm * ri.norm - (ri.err * ri.err - ri.resid * ri.resid);
+        const double dy_norm = std::sqrt(std::max(kept2, 0.0));
         // the sizing pass runs two iterations: the second multiplies a dy of
         // full rank, the largest product of the loop
-        R.err = cx.dry ? (k < 2 ? 1.0 : 0.0) : v[1] / std::sqrt((double)R.x->n1 * R.x->n2);
+        R.err = cx.dry ? (k < 2 ? 1.0 : 0.0) : dy_norm / std::sqrt((double)R.x->n1 * R.x->n2);
         R.it = k;
         const int me = TaskGraph::self();
         taylor_y(R, b, me);

@@ -274,16 +274,69 @@ void fetch_doubles(Exec& ex, const double* d, int n, double* out) {
 }
 
 // ============================================================== TT sums
+// Up to kConcatMax terms of a sum concatenated in one launch: the first core
+// of term t scaled by its coefficient into columns off_t.., the second core
+// copied alike.
+constexpr int kConcatMax = 8;
+struct ConcatDesc {
+  const double* a[kConcatMax];
+  const double* b[kConcatMax];
+  double c[kConcatMax];
+  int off[kConcatMax + 1];  // column offsets; off[nt] = total rank
+  int nt;
+};
+
+__global__ void k_concat(ConcatDesc d, int n1, int n2, double* __restrict__ A, double* __restrict__ B) {
+  const long na = (long)n1 * d.off[d.nt], total = na + (long)n2 * d.off[d.nt];
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const bool first = t < na;
+    const long u = first ? t : t - na;
+    const int n = first ? n1 : n2;
+    const int col = (int)(u / n), i = (int)(u - (long)col * n);
+    int q = 0;
+    while (q + 1 < d.nt && col >= d.off[q + 1]) ++q;
+    const int lc = col - d.off[q];
+    if (first)
+      A[u] = d.c[q] * d.a[q][i + (size_t)lc * n1];
+    else
+      B[u] = d.b[q][i + (size_t)lc * n2];
+  }
+}
+
 void tt_concat(Exec& ex, const std::vector<Term>& terms, TT& out) {
   int off = 0;
   for (const Term& t : terms) {
     TT_REQUIRE(t.x.n1 == out.n1 && t.x.n2 == out.n2, TT_ERR_ARG);
     TT_REQUIRE(off + t.x.r <= out.cap, TT_ERR_ARG);
-    scaled_copy(ex, out.a + (size_t)off * out.n1, t.x.a, (long)out.n1 * t.x.r, t.c);
-    scaled_copy(ex, out.b + (size_t)off * out.n2, t.x.b, (long)out.n2 * t.x.r, 1.0);
     off += t.x.r;
   }
   out.r = off;
+  if (ex.dry || off == 0) return;
+  if ((int)terms.size() > kConcatMax) {
+    int o = 0;
+    for (const Term& t : terms) {
+      scaled_copy(ex, out.a + (size_t)o * out.n1, t.x.a, (long)out.n1 * t.x.r, t.c);
+      scaled_copy(ex, out.b + (size_t)o * out.n2, t.x.b, (long)out.n2 * t.x.r, 1.0);
+      o += t.x.r;
+    }
+    return;
+  }
+  ConcatDesc d{};
+  d.nt = 0;
+  int o = 0;
+  for (const Term& t : terms) {
+    if (t.x.r == 0) continue;
+    d.a[d.nt] = t.x.a;
+    d.b[d.nt] = t.x.b;
+    d.c[d.nt] = t.c;
+    d.off[d.nt] = o;
+    o += t.x.r;
+    d.nt++;
+  }
+  d.off[d.nt] = o;
+  const long total = (long)(out.n1 + out.n2) * o;
+  TT_KERNEL(ex, K_OTHER, (double)out.n1 * o, 16.0 * total,
+            k_concat<<<grid_for(total), 256, 0, ex.s>>>(d, out.n1, out.n2, out.a, out.b));
 }
 
 int total_rank(const std::vector<Term>& terms) {
