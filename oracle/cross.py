@@ -18,9 +18,10 @@ et al.) with rank adaptation by "kick" fibres, written from that principle:
      and the test of step 3 would pass or fail on their noise;
   3. stop when the current skeleton predicts the next sweep's column fibres to
      relative Frobenius error <= tol, when the rank cap is reached with
-     stationary column pivots, when the skeleton is at the rank cap and a
-     sweep no longer halves that prediction error (a cap-limited skeleton
-     cannot reach tol; further sweeps only reshuffle its pivots), or after
+     stationary column pivots, when a sweep no longer halves that
+     prediction error while the skeleton is at the rank cap (a cap-limited
+     skeleton cannot reach tol; further sweeps only reshuffle its pivots) or
+     the error is already within 10 tol (a plateau just above tol), or after
      max_sweeps sweeps;
   4. return the skeleton X = U_c U_c[I]^{-1} F(I, :), then TT-round it.
 
@@ -132,7 +133,7 @@ def cross2d(evalF, n1, n2, x0, tol, cap, kick=4, max_sweeps=10, seed=0,
             err = np.linalg.norm(C - pred) / nc if nc > 0 else 0.0
             if err <= tol:
                 break
-            if len(I) >= cap and np.isfinite(err_prev) and err > 0.5 * err_prev:
+            if np.isfinite(err_prev) and err > 0.5 * err_prev and (len(I) >= cap or err <= 10 * tol):
                 break
         Uc = _orth_left(C, 0.5 * tol, cap)
         I = maxvol(Uc)

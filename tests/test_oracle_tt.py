@@ -201,6 +201,26 @@ def test_cross_cap_limited_stops_on_stagnation():
     assert best <= rel(T.full(Y), F) <= 10 * best
 
 
+def test_cross_plateau_just_above_tol_stops():
+    # a rank-3 field plus full-rank noise of relative size ~3e-9: with tol
+    # 1e-9 the skeleton's prediction error plateaus at the noise, above tol;
+    # the cross stops once a sweep no longer halves it (within 10 tol)
+    # instead of running all max_sweeps, and its result carries the noise's
+    # error only
+    n1, n2 = 80, 100
+    A, B = random_tt(n1, n2, 3, seed=41)
+    F0 = A @ B.T
+    rng = np.random.default_rng(42)
+    N = rng.standard_normal((n1, n2))
+    F = F0 + 3e-9 * np.linalg.norm(F0) / np.linalg.norm(N) * N
+    x0 = random_tt(n1, n2, 2, seed=43)
+    Y, info = CR.cross2d(lambda I, J: F[np.ix_(I, J)], n1, n2, x0, 1e-9, 40, kick=4,
+                         max_sweeps=30, return_info=True)
+    assert info["sweeps"] < 30
+    assert info["err"] <= 10 * 1e-9
+    assert rel(T.full(Y), F) <= 10 * 1e-9
+
+
 def test_cross_weno_step1_against_full():
     n = 40
     w = workload("nonlinear256_weno5", n=n)
