@@ -459,7 +459,10 @@ static int rf_first_sketch(int s, int cap) { return std::min({112, s, ((cap + 8 
 // numerical rank than R, so the first sketch usually certifies.  On the 256^2
 // faces (cap 32, p0 = 40) a factored rounding took 3.7 ms at R = 64 and
 // 9-11 ms at R = 104-112, a range finder certified on its first sketch
-// 3.6 ms, so the factored route is kept up to R = 1.5 p0.  (Sums keep the
+// 3.6 ms, so the factored route is kept up to R = max(64, 1.5 p0).  (With
+// 1.5 p0 alone, small rank caps sent products of R = 24-64 to sketches too
+// narrow to certify: the 64-instance FP32 ensemble ran 1378 instead of
+// 895 ms per step.)  (Sums keep the
 // factored route up to R = 112: their terms are already rounded, so their
 // numerical rank is close to R and the sketch would often have to grow.)
 // Either route gives the truncated SVD, the range finder to within its
@@ -468,7 +471,7 @@ static bool factored_route(int n1, int n2, int R, int cap) {
   const int s = std::min(n1, n2);
   if (R > 112 || R > s) return false;
   if (s <= 112) return true;  // the full route would be as exact and no cheaper
-  return 2 * R <= 3 * rf_first_sketch(s, cap);
+  return R <= 64 || 2 * R <= 3 * rf_first_sketch(s, cap);
 }
 
 // (i) Factored route, R <= 112 and R <= min(n1, n2): QR of both cores
