@@ -61,6 +61,28 @@ def test_workspace_queries_without_gpu(lib):
     assert lib.tt_contract_workspace_size(capi.TT_TF32, 1, 0, 112, 3072) == 0
 
 
+def test_reciprocal_workspace_covers_full_rank_products(lib):
+    # Algorithm 1's second iteration multiplies a dy of full rank by x~: the
+    # reciprocal's workspace must hold that rounding (the cap x cap product
+    # of a stacked 256 x 768 face, which takes the range-finder route), not
+    # only the first iteration's rank-1 product
+    ws = lib.tt_reciprocal_workspace_size(256, 768, 13, 32)
+    assert ws >= lib.tt_round_hadamard_workspace_size(256, 768, 32, 32, 32)
+    assert lib.tt_reciprocal_workspace_size(256, 768, 0, 32) == 0
+
+
+def test_stage_graph_sizing_is_deterministic(lib):
+    # the nonlinear stage is sized by a serial dry run of its task graph
+    # (every node on an arena of its own, one slice per worker): the same
+    # parameters give the same bytes, and WENO5 needs more than Upwind3
+    from paper_2408_03483_gb300 import capi
+    w5 = capi.tt_fv_params(1, 2, 256, 256, 1.0, 1.0, 9.81, 1.0, 0.0, 4.7e-4, 1e-8, 32, 0, 0, 4, 10, 50, 0)
+    u3 = capi.tt_fv_params(1, 0, 256, 256, 1.0, 1.0, 9.81, 1.0, 0.0, 4.7e-4, 1e-8, 32, 0, 0, 4, 10, 50, 0)
+    a = lib.tt_fv_workspace_size(ctypes.byref(w5))
+    assert a > 0 and a == lib.tt_fv_workspace_size(ctypes.byref(w5))
+    assert a > lib.tt_fv_workspace_size(ctypes.byref(u3)) > 0
+
+
 def test_argument_errors_return_codes(lib):
     from paper_2408_03483_gb300 import capi
     x = capi.tt2(0, 0, 0, 0, None, None)
