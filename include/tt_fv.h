@@ -108,7 +108,10 @@ typedef struct {
   int64_t svd_sweeps_sum;     /* sum of their Jacobi sweeps */
   double section_ms[6];       /* host wall time per stage section: faces, side fluxes + lambda,
                                  LLF combination, quadrature/difference, forward-Euler rounds,
-                                 SSP combination rounds */
+                                 SSP combination rounds.  The nonlinear stage runs as one
+                                 dependency graph whose phases overlap: there the first five
+                                 are how far each phase's last task finished after the
+                                 previous phase's (they add up to the graph's wall time) */
   int64_t learned_calls;      /* crosses started from the learned network's pivots */
   int64_t learned_accepted;   /* ... whose first interpolation check passed (no maxvol fallback) */
 } tt_fv_stats;
