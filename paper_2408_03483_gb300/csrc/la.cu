@@ -488,10 +488,14 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, Merg
   }
 }
 
-// fan-in of a merge node: as many triangles as fit in shared memory
+// fan-in of a merge node: as many triangles as fit in shared memory, but at
+// most 4 from p = 32 up, where a merge is FP64-bound on its SM: a level of
+// 4-triangle nodes on separate SMs, then a short second level, beats one SM
+// eliminating 11 triangles in turn (442 us at p = 40)
 static int qr_merge_fanin(int p, size_t elem) {
   const size_t per = ((size_t)p * p + (size_t)16 * p) * elem;
-  return std::max(2, int(QR_SMEM_MAX / per));
+  const int g = std::max(2, int(QR_SMEM_MAX / per));
+  return p >= 32 ? std::min(g, 4) : g;
 }
 
 static int qr_leaf_rows(int p, size_t elem) {
