@@ -95,6 +95,25 @@ def test_nonlinear_weno5_stage_matches_full_tensor(api):
     s.close()
 
 
+def test_weno5_256_step_at_bench_configuration_matches_full_tensor(api):
+    # the timed configuration itself (256^2, WENO5 by cross, rank cap 32,
+    # tol 1e-8, the stage graph on its 16 workers): one SSP-RK3 step against
+    # Oracle A's exact full-tensor step, within the WENO5 bar per stage
+    # (10 tol relative to ||h||) times the three stages
+    w = workload("nonlinear256_weno5")
+    Q, p = initial_tt(w)
+    s = make_solver(api, w, Q, p)
+    s.step(1)
+    got = s.get()
+    ref = FA.ssprk3_step([T.full(q) for q in Q], "nonlinear", "weno5", p, p["dt"])
+    scale = np.linalg.norm(ref[0])
+    for c in range(3):
+        assert np.linalg.norm(got[c].full().numpy() - ref[c]) <= 3 * 10 * w["tol"] * scale, c
+    st = s.stats()
+    assert st["device_status"] == 0 and st["qb_uncertified"] == 0
+    s.close()
+
+
 def test_checkpoint_resume_is_bit_exact(api):
     w = workload("nonlinear256_weno5", n=32, scheme="up3", cap=24)
     Q, p = initial_tt(w)
