@@ -104,3 +104,25 @@ def test_planted_sign_error_breaks_convergence(monkeypatch):
     monkeypatch.setattr(FA, "step1", wrong)
     e = [_igw_error("up3", n) for n in (16, 32)]
     assert math.log2(e[0] / e[1]) < 2.5 or e[1] > 1e-2
+
+
+def test_weno5_step_data_has_no_new_extrema():
+    # a periodic box profile (two unit jumps): the WENO5 reconstructions of
+    # Steps 1 and 2 stay within the cell averages' range up to O(eps), eps =
+    # dx^2 (Sec. 2.3), while the linear Upwind5/Upwind3 stencils overshoot
+    # by 17-18 %; a WENO weight that fell back to the linear weights fails
+    n = 64
+    x = (np.arange(n) + 0.5) / n
+    v = np.where((x > 0.25) & (x < 0.6), 1.0, 0.0)[:, None] * np.ones((1, n))
+    eps = (1.0 / n) ** 2
+    for side in ("-", "+"):
+        f = FA.step1(v, 0, "weno5", side, eps)
+        assert f.min() >= -eps and f.max() <= 1.0 + eps, side
+        for lin in ("up5", "up3"):
+            g = FA.step1(v, 0, lin, side, eps)
+            assert g.min() < -0.1 and g.max() > 1.1, (lin, side)
+    pts = FA.step2(v, 0, "weno5", eps)
+    assert np.min(pts) >= -eps and np.max(pts) <= 1.0 + eps
+    lin = FA.step2(v, 0, "up5", eps)
+    assert np.min(lin) < -0.1 and np.max(lin) > 1.1
+

@@ -128,6 +128,25 @@ def test_reciprocal_constant_is_exact_in_one_iteration():
     np.testing.assert_allclose(T.full(y), np.full((10, 12), 1.0 / 3.0), rtol=1e-15)
 
 
+def test_reciprocal_of_rank1_h_matches_rank1_cross():
+    # h = f(x) g(y) > 0 is rank 1, so 1/h = (1/f)(1/g) is rank 1 too: the
+    # cross of 1/h recovers it exactly (1e-12) from one fibre pair, and
+    # Algorithm 1 reaches the same tensor to its geometric tail and rounds
+    # back to (numerical) rank 1
+    n1, n2 = 40, 56
+    xs = (np.arange(n1) + 0.5) / n1
+    ys = (np.arange(n2) + 0.5) / n2
+    f = (1.0 + 0.04 * np.sin(2 * np.pi * xs))[:, None]
+    g = (1.0 + 0.03 * np.cos(2 * np.pi * ys))[:, None]
+    h = (f, g)
+    F = T.full(h)
+    Yc = CR.cross2d(lambda I, J: 1.0 / F[np.ix_(I, J)], n1, n2, h, 1e-12, 8, kick=4, max_sweeps=8)
+    assert rel(T.full(Yc), 1.0 / F) < 1e-12
+    y, it = RC.reciprocal(h, 1e-10, 16)
+    assert rel(T.full(y), T.full(Yc)) < 1e-8
+    assert T.rank(T.round_tt(y, 1e-9, 16)[0]) == 1
+
+
 def test_planted_taylor_sign_error_is_caught(monkeypatch):
     # flipping the sign of x~ (1 + x/x_avg) must break the 1/h pin
     orig = T.add
