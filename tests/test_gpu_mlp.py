@@ -15,6 +15,7 @@ import pytest
 from oracle import fv_full as FA
 from oracle import mlp as M
 from oracle import tt as T
+from parity import check_fields, field_scales
 from synth import initial_tt, workload
 
 pytestmark = pytest.mark.gpu
@@ -147,9 +148,7 @@ def test_learned_solver_stage_is_exact_whatever_the_proposals(api):
     s.stage(0)
     got = s.get()
     ref = FA.ssprk3_stage([T.full(q) for q in Q], [T.full(q) for q in Q], 0, "nonlinear", "weno5", p, p["dt"])
-    scale = np.linalg.norm(ref[0])
-    for c in range(3):
-        assert np.linalg.norm(got[c].full().numpy() - ref[c]) <= 10 * w["tol"] * scale
+    check_fields(got, ref, 10 * w["tol"], field_scales(ref, "nonlinear", p, p["dt"]))
     st = s.stats()
     assert st["learned_calls"] > 0 and st["device_status"] == 0
     s.close()
@@ -193,8 +192,7 @@ def test_shipped_network_gain_over_plain_maxvol(api):
                 assert st["learned_calls"] == st["cross_calls"] - 4 > 0
                 got = s.get()
                 ref = FA.ssprk3_step([T.full(q) for q in Q], "nonlinear", "weno5", p, p["dt"])
-                scale = np.linalg.norm(ref[0])
-                for c in range(3):  # the WENO5 bar per stage, three stages
-                    assert np.linalg.norm(got[c].full().numpy() - ref[c]) <= 3 * 10 * w["tol"] * scale
+                # the WENO5 bar per stage and field, three stages
+                check_fields(got, ref, 3 * 10 * w["tol"], field_scales(ref, "nonlinear", p, p["dt"]))
             s.close()
     assert sweeps["learned"] < sweeps["maxvol"], sweeps

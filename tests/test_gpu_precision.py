@@ -9,9 +9,9 @@ Bar.  FP32 round-off of a formed face tensor or residual is a few units of
 2^-24 = 6e-8 relative to its norm, so the form never truncates below
 tol_eff = max(tol, 1e-6) (below that it would keep round-off directions).
 It is compared with Oracle B run at the same tol_eff: the truncation decides
-the ranks, so the states must agree within 10 x tol_eff relative to ||h||
-(the bar used for truncation-decided results), and with Oracle A's exact
-full-tensor stage within the same bar.
+the ranks, so each field must agree within 10 x tol_eff of its truncation
+scale (tests/parity.py; the bar used for truncation-decided results), and
+with Oracle A's exact full-tensor stage within the same bar.
 """
 import numpy as np
 import pytest
@@ -19,6 +19,7 @@ import pytest
 from oracle import fv_full as FA
 from oracle import tt as T
 from oracle import tt_fv as TB
+from parity import check_fields, field_scales
 from synth import initial_tt, workload
 
 pytestmark = pytest.mark.gpu
@@ -43,9 +44,9 @@ def make_solver(api, w, Q, p, precision):
                       f=p["f"], seed=0, precision=precision)
 
 
-def rel_err(got, ref_full):
-    scale = np.linalg.norm(ref_full[0])
-    return max(np.linalg.norm(got[c].full().numpy() - ref_full[c]) / scale for c in range(3))
+def check(got, ref_full, p, what):
+    """Per-field bar 10 tol_eff on each field's truncation scale."""
+    return check_fields(got, ref_full, 10 * TOL_EFF_FP32, field_scales(ref_full, "nonlinear", p, p["dt"]), what)
 
 
 def smooth_state(n, r):
@@ -81,8 +82,8 @@ def test_precision_form_stages_match_oracles(api, scheme, n, state, precision):
         Qs = TB.stage(Qn, Qs, k, wb, p, seed=1000 * k)
         Qa_s = FA.ssprk3_stage(Qa_n, Qa_s, k, w["eqn"], scheme, p, p["dt"])
         got = s.get()
-        assert rel_err(got, [T.full(q) for q in Qs]) < 10 * TOL_EFF_FP32, (scheme, k)
-        assert rel_err(got, Qa_s) < 10 * TOL_EFF_FP32, (scheme, k)
+        check(got, [T.full(q) for q in Qs], p, ("oracle B", scheme, k))
+        check(got, Qa_s, p, ("oracle A", scheme, k))
         # no rank inflation from FP32 round-off
         assert all(g.rank <= T.rank(q) + 2 for g, q in zip(got, Qs)), ([g.rank for g in got],
                                                                      [T.rank(q) for q in Qs])
@@ -102,6 +103,6 @@ def test_fp32_form_step_close_to_fp64_path(api):
     s64.step(1)
     a, b = s32.get(), s64.get()
     ref = [q.full().numpy() for q in b]
-    assert rel_err(a, ref) < 10 * TOL_EFF_FP32
+    check(a, ref, p, "fp64 path")
     s32.close()
     s64.close()
