@@ -11,7 +11,9 @@ Composition (Sec. 4.1-4.4):
   * LLF flux in TT (Eq. LLF-TT): linear SWE by plain TT sums with
     lambda = sqrt(gH) and no rounding; nonlinear SWE with 1/h by Algorithm 1,
     products by TT Hadamard products rounded after each product and sum,
-    lambda = max(|u-|+sqrt(g h-), |u+|+sqrt(g h+)) by cross;
+    lambda = max(|u-|+sqrt(g h-), |u+|+sqrt(g h+)) by cross -- or, with
+    w["flux"] == "cross", the whole flux vector by one cross (the LF-cross
+    alternative of Sec. 4.2);
   * face quadrature sum over the stacked index, then (T - 1)/dx on the core
     normal to the face (Eq. SWE-system-TT), plus the source term;
   * forward Euler F(u) = round(u + dt L(u)) and the SSP-RK3 combinations of
@@ -227,6 +229,44 @@ def flux_nonlinear(Qm, Qp, direction, p, w, stats=None, seed=0):
     return out
 
 
+def _llf_flux_eval(Qm, Qp, direction, g):
+    """Entries of the LLF flux vector of Eq. LLF at the faces with its three
+    components stacked along the first mode: row c n1 + i, column j holds
+    component c at face point (i, j), from the six face states' entries with
+    Oracle A's physical flux and wave speed."""
+    n1 = Qm[0][0].shape[0]
+    prm = {"g": g}
+
+    def ev(I, J):
+        I = np.asarray(I)
+        out = np.empty((len(I), len(J)))
+        comp, rows = I // n1, I % n1
+        for c in range(3):
+            sel = np.nonzero(comp == c)[0]
+            if sel.size == 0:
+                continue
+            qm = [_entries(q, rows[sel], J) for q in Qm]
+            qp = [_entries(q, rows[sel], J) for q in Qp]
+            Fm = FA.phys_flux(qm, direction, "nonlinear", prm)
+            Fp = FA.phys_flux(qp, direction, "nonlinear", prm)
+            lam = FA.max_speed(qm, qp, direction, "nonlinear", prm)
+            out[sel] = 0.5 * (Fm[c] + Fp[c]) - 0.5 * lam * (qp[c] - qm[c])
+        return out
+    return ev
+
+
+def flux_cross(Qm, Qp, direction, p, w, seed=0):
+    """The LF-cross alternative of Sec. 4.2: the whole LLF flux vector of one
+    direction by a single cross of the face states (components stacked along
+    the first mode, initial guess the h- faces), split into one TT per
+    component sharing the second core."""
+    n1, n2 = Qm[0][0].shape[0], Qm[0][1].shape[0]
+    ev = _llf_flux_eval(Qm, Qp, direction, p["g"])
+    A, B = CR.cross2d(ev, 3 * n1, n2, Qm[0], w["tol"], w["cap"], w.get("kick", 4), w.get("max_sweeps", 10),
+                      seed=seed)
+    return [(A[c * n1:(c + 1) * n1].copy(), B) for c in range(3)]
+
+
 def quad_and_difference(Fh, direction, nq, n, d):
     """Face average sum_m w_m over the stacked index, then (T - 1)/d on the
     core normal to the face: returns the TT of (F_{i+1/2} - F_{i-1/2})/d."""
@@ -258,6 +298,8 @@ def rhs_terms(Q, w, p, stats=None, seed=0):
         Qp = [f[1] for f in faces]
         if eqn == "linear":
             Fh = flux_linear(Qm, Qp, direction, p)
+        elif w.get("flux", "products") == "cross":
+            Fh = flux_cross(Qm, Qp, direction, p, w, seed=seed + 64 * di + 44)
         else:
             Fh = flux_nonlinear(Qm, Qp, direction, p, w, stats, seed=seed + 64 * di + 40)
         for c in range(3):
@@ -269,13 +311,19 @@ def rhs_terms(Q, w, p, stats=None, seed=0):
     return terms
 
 
+def _tol_u(w, c):
+    """Tolerance of field c's forward-Euler and SSP rounds: eps^u of the step
+    (Eq. modified-eps-tt-formula) when set, else the fixed tol."""
+    return w["tol_u"][c] if "tol_u" in w else w["tol"]
+
+
 def forward_euler(Q, w, p, dt, stats=None, seed=0):
-    """F(u) = round(u + dt L(u), eps) per component (Eq. tt-forward-euler)."""
+    """F(u) = round(u + dt L(u), eps^u) per component (Eq. tt-forward-euler)."""
     terms = rhs_terms(Q, w, p, stats, seed)
     out = []
     for c in range(3):
         X = T.add([(1.0, Q[c])] + [(dt * a, Y) for a, Y in terms[c]])
-        out.append(T.rnd(X, w["tol"], w["cap"]))
+        out.append(T.rnd(X, _tol_u(w, c), w["cap"]))
     return out
 
 
@@ -286,11 +334,34 @@ def stage(Qn, Qs, k, w, p, stats=None, seed=0):
     if k == 0:
         return f
     a, b = (0.75, 0.25) if k == 1 else (1.0 / 3.0, 2.0 / 3.0)
-    return [T.rnd(T.add([(a, Qn[c]), (b, f[c])]), w["tol"], w["cap"]) for c in range(3)]
+    return [T.rnd(T.add([(a, Qn[c]), (b, f[c])]), _tol_u(w, c), w["cap"]) for c in range(3)]
+
+
+def step_tolerances(Qn, w, p):
+    """(eps_TT, [eps^u per field]) of a step (Sec. 4.4).  With
+    w["eps_rule"] == "adaptive": eps^u = min(1e-3, C V^(1/2) dx^(p-1/2) / ||u||_F)
+    at the beginning of the step (Eq. modified-eps-tt-formula) for the
+    variable's own forward-Euler and SSP rounds, and eps_TT of
+    Eq. eps-tt-formula (the same numerator over max_q ||q||_F) for every
+    other rounding; V is the domain area, p the scheme's order (3 for
+    Upwind3, 5 for Upwind5 and WENO5), C = w["c_eps"].  Otherwise the fixed
+    w["tol"] for both."""
+    if w.get("eps_rule", "fixed") != "adaptive":
+        return w["tol"], [w["tol"]] * 3
+    order = 3 if w["scheme"] == "up3" else 5
+    nx = Qn[0][0].shape[0]
+    num = w["c_eps"] * np.sqrt(p["lx"] * p["ly"]) * (p["lx"] / nx) ** (order - 0.5)
+    norms = [T.fro(q) for q in Qn]
+    eps_u = [min(1e-3, num / nm) if nm > 0 else 1e-3 for nm in norms]
+    big = max(norms)
+    return (num / big if big > 0 else 1e-3), eps_u
 
 
 def step(Qn, w, p, stats=None, seed=0):
-    """One full SSP-RK3 step in TT format."""
-    u1 = stage(Qn, Qn, 0, w, p, stats, seed)
-    u2 = stage(Qn, u1, 1, w, p, stats, seed + 1000)
-    return stage(Qn, u2, 2, w, p, stats, seed + 2000)
+    """One full SSP-RK3 step in TT format (Eq. tt-ssprk3), with the step's
+    truncation tolerances of Sec. 4.4."""
+    eps_tt, eps_u = step_tolerances(Qn, w, p)
+    ws = dict(w, tol=eps_tt, tol_u=eps_u)
+    u1 = stage(Qn, Qn, 0, ws, p, stats, seed)
+    u2 = stage(Qn, u1, 1, ws, p, stats, seed + 1000)
+    return stage(Qn, u2, 2, ws, p, stats, seed + 2000)

@@ -284,3 +284,63 @@ def test_tt_stage_nonlinear_matches_full(scheme):
     scale = np.linalg.norm(b[0])
     for c in range(3):
         assert np.linalg.norm(T.full(a[c]) - b[c]) <= 1e3 * 1e-11 * scale
+
+
+# ---------------------------------------------------------------- LF-cross flux
+
+def test_lf_cross_flux_matches_the_exact_llf_flux():
+    # the LF-cross of Sec. 4.2 (one cross of the whole flux vector, components
+    # stacked along the first mode) against Oracle A's LLF flux evaluated on
+    # the full face tensors: within the cross's tolerance class (10 tol of the
+    # stacked flux), per direction
+    w = workload("nonlinear256_weno5", n=32, scheme="up5", flux="cross")
+    Q, p = initial_tt(w)
+    # a state with flow: momentum from one forward-Euler stage
+    Q = TB.forward_euler(Q, dict(w, flux="products"), p, p["dt"])
+    for direction in ("x", "y"):
+        faces = [TB.recon_linear(q, direction, "up5") for q in Q]
+        Qm = [f[0] for f in faces]
+        Qp = [f[1] for f in faces]
+        F = TB.flux_cross(Qm, Qp, direction, p, w, seed=3)
+        ex = FA.llf([T.full(q) for q in Qm], [T.full(q) for q in Qp], direction, "nonlinear", p)
+        num = sum(np.linalg.norm(T.full(F[c]) - ex[c]) ** 2 for c in range(3)) ** 0.5
+        den = sum(np.linalg.norm(ex[c]) ** 2 for c in range(3)) ** 0.5
+        assert num <= 10 * w["tol"] * den, (direction, num / den)
+        # the three components share the second core
+        assert F[0][1] is F[1][1] is F[2][1]
+
+
+@pytest.mark.parametrize("scheme", ["up3", "weno5"])
+def test_lf_cross_step_matches_full_tensor(scheme):
+    from parity import check_fields, field_scales
+    w = workload("nonlinear256_weno5", n=32, scheme=scheme, flux="cross")
+    Q, p = initial_tt(w)
+    out = TB.step(Q, w, p, seed=0)
+    ref = FA.ssprk3_step([T.full(q) for q in Q], "nonlinear", scheme, p, p["dt"])
+    check_fields(out, ref, 3 * 10 * w["tol"], field_scales(ref, "nonlinear", p, p["dt"]))
+
+
+def test_planted_lf_cross_mistake_fails(monkeypatch):
+    # a dissipation term with the wrong sign in the stacked evaluator must
+    # fail the exact-flux pin
+    orig = TB._llf_flux_eval
+
+    def wrong(Qm, Qp, direction, g):
+        ev = orig(Qm, Qp, direction, g)
+        n1 = Qm[0][0].shape[0]
+
+        def ev2(I, J):
+            I = np.asarray(I)
+            out = ev(I, J)
+            comp, rows = I // n1, I % n1
+            for c in range(3):
+                sel = np.nonzero(comp == c)[0]
+                if sel.size:
+                    qm = TB._entries(Qm[c], rows[sel], J)
+                    qp = TB._entries(Qp[c], rows[sel], J)
+                    out[sel] += (qp - qm) * 5.0
+            return out
+        return ev2
+    monkeypatch.setattr(TB, "_llf_flux_eval", wrong)
+    with pytest.raises(AssertionError):
+        test_lf_cross_flux_matches_the_exact_llf_flux()
