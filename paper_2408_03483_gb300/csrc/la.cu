@@ -244,6 +244,26 @@ void sumsq(Exec& ex, const Real* X, int m, int n, long ld, double* out) {
   TT_KERNEL(ex, K_OTHER, blocks, 8.0 * blocks, k_sum_fixed<<<1, 256, 0, ex.s>>>(part, blocks, out));
 }
 
+// sum_t X[t] Y[t] over n contiguous entries, accumulated in FP64 with a fixed
+// reduction order (two launches, like sumsq)
+__global__ void k_fdot_partial(const double* __restrict__ X, const double* __restrict__ Y, long n, double* part) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    s = fma(X[t], Y[t], s);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+void fdot(Exec& ex, const double* X, const double* Y, long n, double* out) {
+  Scope sc(*ex.ar);
+  const int blocks = std::max(1, std::min(ceil_div(n, 256), 2 * sm_count()));
+  double* part = ex.ar->get<double>(blocks);
+  if (ex.dry) return;
+  TT_KERNEL(ex, K_OTHER, 2.0 * n, 16.0 * n, k_fdot_partial<<<blocks, 256, 0, ex.s>>>(X, Y, n, part));
+  TT_KERNEL(ex, K_OTHER, blocks, 8.0 * blocks, k_sum_fixed<<<1, 256, 0, ex.s>>>(part, blocks, out));
+}
+
 // ============================================================== TSQR
 // Householder QR of row blocks held in shared memory (LAPACK sign convention:
 // beta = -sign(alpha) ||x||, v(0) = 1, tau = (beta - alpha) / beta).

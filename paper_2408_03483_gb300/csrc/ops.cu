@@ -641,6 +641,114 @@ static RoundInfo round_full_t(Exec& ex, const Real* Yf, int n1, int n2, double t
   return RoundInfo{k, std::sqrt(tl[0] * tl[0] + resid2), tl[1], std::sqrt(resid2)};
 }
 
+// (iii) Range finder on the cores (FP64), for an input Y = A B^T of R > 112
+// columns whose modes both exceed 112 and whose n1 x n2 tensor would cost
+// more to form and sketch than its cores: the steps of (ii) with every
+// product taken through the cores, so Y is never formed.  With W0 = As Bl^T
+// (As the s-side core, Bl the l-side core):
+//   S  = As (Bl^T Om)                      the sketch,
+//   C  = Q^T As,  WT = W0^T Q = Bl C^T      the projection,
+//   ||W0||_F^2 = sum (As^T As) o (Bl^T Bl),
+//   ||W0 - Q Q^T W0||_F^2 = sum (At^T At) o (Bl^T Bl),  At = As - Q C,
+// the last two exact identities of the Frobenius norm of a product of
+// cores.  At is formed in FP64 before its Gram, so the residual is resolved
+// down to the round-off of At's entries (~1e-16 of ||As||), far below the
+// certified 1e-11 relative residual; the sketch itself only has to span the
+// range, which the residual check decides.
+static double frf_flops(int s, int l, int R, int p) {
+  return 2.0 * R * (double)R * (2.0 * s + l) + 2.0 * R * (double)p * (2.0 * l + 3.0 * s);
+}
+static double full_rf_flops(int n1, int n2, double form, int p) { return form + 6.0 * n1 * (double)n2 * p; }
+
+static RoundInfo round_factored_rf(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol,
+                                   int cap, TT& Y) {
+  Scope sc(*ex.ar);
+  const bool tr = n1 > n2;
+  const int s = tr ? n2 : n1, l = tr ? n1 : n2;
+  const double* As = tr ? B : A;
+  const double* Bl = tr ? A : B;
+  double* Aw = tr ? Y.b : Y.a;  // s-side output core
+  double* Bw = tr ? Y.a : Y.b;  // l-side output core
+  double* kbuf = ex.ar->get<double>(4);
+  int* kd = ex.ar->get<int>(4);
+  double* tail = ex.ar->get<double>(2);
+  const double tau = qb_target(tol);
+  // Grams of both cores and ||W0||^2
+  double* GB = ex.ar->get<double>((size_t)R * R);
+  double* GA = ex.ar->get<double>((size_t)R * R);
+  gemm<double>(ex, R, R, l, 1.0, Bl, l, 1, Bl, 1, l, 0.0, GB, R);
+  gemm<double>(ex, R, R, s, 1.0, As, s, 1, As, 1, s, 0.0, GA, R);
+  fdot(ex, GA, GB, (long)R * R, kbuf);
+  int p = rf_first_sketch(s, cap);
+  if (ex.rf_hint && *ex.rf_hint > p) p = std::min({112, s, *ex.rf_hint});
+  // the sizing pass takes the widest sketch the run may grow to (every
+  // buffer, tree and product partial grows with p)
+  if (ex.dry) p = std::min(112, s);
+  double* Om = ex.ar->get<double>((size_t)l * 112);
+  double* T = ex.ar->get<double>((size_t)R * 112);
+  double* S = ex.ar->get<double>((size_t)s * 112);
+  double* Q = ex.ar->get<double>((size_t)s * 112);
+  double* C = ex.ar->get<double>((size_t)112 * R);
+  double* At = ex.ar->get<double>((size_t)s * R);
+  double* GAt = ex.ar->get<double>((size_t)R * R);
+  double* I = ex.ar->get<double>((size_t)112 * 112);
+  double nrm2 = 0.0, resid2 = 0.0;
+  for (int attempt = 0;; ++attempt) {
+    ex.qb_attempts++;
+    const size_t mk = ex.ar->mark();
+    if (!ex.dry)
+      TT_KERNEL(ex, K_OTHER, 0, 8.0 * l * p,
+                k_rademacher<double><<<grid_for((long)l * p), 256, 0, ex.s>>>(Om, (long)l * p, 0x7A3Dull + attempt));
+    // T = Bl^T Om (R x p), S = As T (s x p)
+    gemm<double>(ex, R, p, l, 1.0, Bl, l, 1, Om, 1, l, 0.0, T, R);
+    gemm<double>(ex, s, p, R, 1.0, As, 1, s, T, 1, R, 0.0, S, s);
+    QRTreeT<double> ts;
+    tsqr(ex, S, s, p, s, ts);
+    set_identity_t(ex, I, p);
+    tsqr_apply(ex, ts, I, p, p, Q, s);
+    // C = Q^T As (p x R); At = As - Q C; resid^2 = sum (At^T At) o GB
+    gemm<double>(ex, p, R, s, 1.0, Q, s, 1, As, 1, s, 0.0, C, p);
+    scaled_copy(ex, At, As, (long)s * R, 1.0);
+    gemm<double>(ex, s, R, p, -1.0, Q, 1, s, C, 1, p, 1.0, At, s);
+    gemm<double>(ex, R, R, s, 1.0, At, s, 1, At, 1, s, 0.0, GAt, R);
+    fdot(ex, GAt, GB, (long)R * R, kbuf + 1);
+    double v[2];
+    fetch_doubles(ex, kbuf, 2, v);
+    nrm2 = v[0];
+    resid2 = std::max(v[1], 0.0);
+    const bool ok = resid2 <= tau * tau * nrm2;
+    const bool accept = ok || p >= std::min(112, s) || ex.dry;
+    if (accept) {
+      if (!ok && !ex.dry) ex.qb_uncertified++;
+      if (ex.rf_hint && !ex.dry) *ex.rf_hint = p;
+      break;
+    }
+    ex.ar->reset(mk);
+    p = std::min({112, s, 2 * p});
+  }
+  // WT = W0^T Q = Bl C^T (l x p); SVD of Q^T W0 = R_W^T Q_W^T (buffers
+  // sized for the widest sketch: the sizing pass never widens it)
+  double* WT = ex.ar->get<double>((size_t)l * 112);
+  gemm<double>(ex, l, p, R, 1.0, Bl, 1, l, C, p, 1, 0.0, WT, l);
+  QRTreeT<double> tw;
+  tsqr(ex, WT, l, p, l, tw);
+  double* M = ex.ar->get<double>((size_t)112 * 112);
+  transpose(ex, tw.R, p, p, p, M, p);
+  debug_finite(ex, M, (long)p * p, "factored range-finder core M (n1, n2, p)", n1, n2, p);
+  double* US = ex.ar->get<double>((size_t)112 * 112);
+  double* V = ex.ar->get<double>((size_t)112 * 112);
+  double* sig = ex.ar->get<double>(112);
+  jacobi_svd(ex, M, p, tol, cap, US, V, sig, kd, tail);
+  double tl[2];
+  int k = fetch_svd_info(ex, kd, p, tail, tl);
+  if (ex.dry) k = std::min(cap, p);
+  gemm(ex, s, k, p, 1.0, Q, 1, s, US, 1, p, 0.0, Aw, s);
+  apply_to_core(ex, tw, V, k, p, Bw);
+  Y.r = k;
+  finish_counts(ex, k, cap, s);
+  return RoundInfo{k, std::sqrt(tl[0] * tl[0] + resid2), tl[1], std::sqrt(resid2)};
+}
+
 RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int cap, TT& Y) {
   tol = effective_tol(ex, tol);
   if (ex.precision == TT_FP64) return round_full_t<double>(ex, Yf, n1, n2, tol, cap, Y);
@@ -652,6 +760,11 @@ template <typename Real>
 static RoundInfo round_cores_t(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol,
                                int cap, TT& Y) {
   if (R <= 112 && R <= std::min(n1, n2)) return round_factored<Real>(ex, A, B, n1, n2, R, tol, cap, Y);
+  if constexpr (std::is_same<Real, double>::value) {
+    const int s = std::min(n1, n2), l = std::max(n1, n2), p = rf_first_sketch(s, cap);
+    if (s > 112 && frf_flops(s, l, R, p) < full_rf_flops(n1, n2, 2.0 * n1 * (double)n2 * R, p))
+      return round_factored_rf(ex, A, B, n1, n2, R, tol, cap, Y);
+  }
   Scope sc(*ex.ar);
   Real* Yf = ex.ar->get<Real>((size_t)n1 * n2);
   if constexpr (std::is_same<Real, float>::value) {
@@ -712,6 +825,16 @@ RoundInfo round_hadamard(Exec& ex, const TT& X, const TT& Z, double tol, int cap
   }
   tol = effective_tol(ex, tol);
   if (ex.precision == TT_FP64) {
+    // cores of the product (Khatri-Rao) and the range finder through them,
+    // when that costs fewer flops than forming the n1 x n2 product
+    const int s = std::min(n1, n2), l = std::max(n1, n2), p = rf_first_sketch(s, cap);
+    if (s > 112 && frf_flops(s, l, R, p) < full_rf_flops(n1, n2, 2.0 * n1 * (double)n2 * (X.r + Z.r), p)) {
+      double* A = ex.ar->get<double>((size_t)n1 * R);
+      double* B = ex.ar->get<double>((size_t)n2 * R);
+      khatri_rao(ex, X.a, X.r, Z.a, Z.r, n1, A);
+      khatri_rao(ex, X.b, X.r, Z.b, Z.r, n2, B);
+      return round_factored_rf(ex, A, B, n1, n2, R, tol, cap, Y);
+    }
     double* Yf = ex.ar->get<double>((size_t)n1 * n2);
     form_hadamard_full(ex, n1, n2, X.a, X.r, X.b, Z.a, Z.r, Z.b, Yf, n1);
     return round_full_t<double>(ex, Yf, n1, n2, tol, cap, Y);

@@ -254,6 +254,10 @@ void form_hadamard_full(Exec& ex, int n1, int n2, const double* A1, int r1, cons
 template <typename Real>
 void sumsq(Exec& ex, const Real* X, int m, int n, long ld, double* out);
 
+// sum_t X[t] Y[t] over n contiguous FP64 entries -> device double (the
+// Frobenius inner product of two equally laid out matrices)
+void fdot(Exec& ex, const double* X, const double* Y, long n, double* out);
+
 // Householder TSQR of a tall m x p matrix (p <= 112): row blocks of mb0
 // rows factored independently, then a g-ary tree of merges of stacked
 // triangular factors (g as many as fit in shared memory); Q is kept implicit.

@@ -49,6 +49,10 @@ def dev(api, X, cap=None):
     (96, 300, 130, "direct"),
     (256, 768, 200, "range-finder"),
     (770, 257, 150, "range-finder"),
+    # R > 112 with modes large enough that sketching through the cores costs
+    # fewer flops than forming the n1 x n2 tensor: the range finder on cores
+    (1024, 3072, 150, "range-finder"),
+    (3000, 1100, 130, "range-finder"),
 ])
 def test_round_matches_oracle(api, n1, n2, R, route):
     # decay 0.75: the spectrum falls below 1e-11 within 112 singular values,
@@ -101,7 +105,10 @@ def smooth_tt(n1, n2, phase, r):
 
 
 @pytest.mark.parametrize("n1,n2,r1,r2", [(40, 70, 6, 5), (256, 768, 16, 16), (768, 256, 24, 20),
-                                         (100, 100, 12, 10)])
+                                         (100, 100, 12, 10),
+                                         # products of R = 120-144 columns on 1024-3072 modes: the
+                                         # range finder through the Khatri-Rao cores
+                                         (1024, 3072, 12, 12), (3072, 1024, 12, 10)])
 def test_round_hadamard_matches_oracle(api, n1, n2, r1, r2):
     X = smooth_tt(n1, n2, 0.3, r1)
     Z = smooth_tt(n1, n2, 1.1, r2)
