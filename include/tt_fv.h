@@ -63,14 +63,18 @@ enum { TT_LINEAR = 0, TT_NONLINEAR = 1 };          /* Eq. linear-SWE / nonlinear
 enum { TT_UP3 = 0, TT_UP5 = 1, TT_WENO5 = 2 };      /* Sec. 2.3 reconstructions */
 enum { TT_FP64 = 0, TT_TF32 = 1, TT_BF16 = 2, TT_FP32 = 3 }; /* contraction precision */
 enum { TT_PIVOT_MAXVOL = 0, TT_PIVOT_LEARNED = 1 };
+enum { TT_EPS_FIXED = 0, TT_EPS_ADAPTIVE = 1 };       /* truncation tolerance rule (Sec. 4.4) */
 
 /* Cross-interpolated functions (tt_cross `fn`). */
 enum {
   TT_FN_ENTRY = 0,       /* F = inputs[0] itself (exact-recovery test)              */
   TT_FN_WENO_S1 = 1,     /* WENO5 Step 1 (Sec. 2.3.1, Algorithm 2) of inputs[0]     */
   TT_FN_WENO_S2 = 2,     /* WENO5 Step 2 at all Gauss points (Algorithm 3)          */
-  TT_FN_LLF_LAMBDA = 3   /* max(|hu-/h-| + sqrt(g h-), |hu+/h+| + sqrt(g h+)) (Sec. 4.2) */
+  TT_FN_LLF_LAMBDA = 3,  /* max(|hu-/h-| + sqrt(g h-), |hu+/h+| + sqrt(g h+)) (Sec. 4.2) */
+  TT_FN_LLF_FLUX = 4     /* the LLF flux vector of Eq. LLF from the face states, its three
+                            components stacked along the first mode (the LF-cross of Sec. 4.2) */
 };
+enum { TT_FLUX_PRODUCTS = 0, TT_FLUX_CROSS = 1 }; /* nonlinear LLF flux in TT (Sec. 4.2) */
 
 typedef struct {
   int32_t eqn;        /* TT_LINEAR | TT_NONLINEAR */
@@ -88,7 +92,30 @@ typedef struct {
   int32_t max_sweeps; /* cross sweep cap (default 10 if <= 0) */
   int32_t max_iter;   /* Taylor reciprocal iteration cap (default 50 if <= 0) */
   uint32_t seed;      /* seed of the cross kick indices */
+  int32_t eps_rule;   /* TT_EPS_FIXED (0): `tol` for every round and cross.  TT_EPS_ADAPTIVE (Sec. 4.4):
+                         at the start of each step, from the step's input state,
+                           eps_u  = min(1e-3, c_eps V^(1/2) dx^(p-1/2) / ||u||_F)   per field u, for its
+                                    forward-Euler and SSP-combination rounds (Eq. modified-eps-tt-formula),
+                           eps_TT = c_eps V^(1/2) dx^(p-1/2) / max_q ||q||_F        for every other round
+                                    and cross (Eq. eps-tt-formula),
+                         with V = lx ly, dx = lx / nx, p = 3 (TT_UP3) or 5; `tol` is then unused */
+  double c_eps;       /* C_eps of Sec. 4.4 (> 0 under TT_EPS_ADAPTIVE; Table 1 gives the paper's values) */
+  int32_t flux;       /* nonlinear SWE, how Eq. LLF-TT is formed (Sec. 4.2): TT_FLUX_PRODUCTS (0): 1/h by
+                         Algorithm 1, the physical fluxes from rounded Hadamard products, lambda by cross,
+                         then the rounded LLF sums; TT_FLUX_CROSS: per direction one cross of the whole
+                         flux vector (TT_FN_LLF_FLUX), the LF-cross the paper compares against */
+  int32_t forcing_waves; /* the most source waves of one field tt_fv_set_forcing may set, 0..TT_MAX_WAVES
+                            (0: no source); the workspace is sized for it */
 } tt_fv_params;
+
+/* One plane wave of an external source: amp cos(kx x + ky y - omega t + phase)
+ * on the right-hand side of field `field` (0: h or eta, 1: hu or u, 2: hv or v),
+ * e.g. the forcing that makes the manufactured solution of Sec. 5.4 exact. */
+typedef struct {
+  int32_t field;
+  double amp, kx, ky, omega, phase;
+} tt_wave;
+enum { TT_MAX_WAVES = 16 };
 
 typedef struct {
   int32_t rank[3];            /* current ranks of the three fields */
@@ -114,6 +141,8 @@ typedef struct {
                                  previous phase's (they add up to the graph's wall time) */
   int64_t learned_calls;      /* crosses started from the learned network's pivots */
   int64_t learned_accepted;   /* ... whose first interpolation check passed (no maxvol fallback) */
+  double eps_u[3];            /* tolerances of the current step's per-field rounds (Sec. 4.4) */
+  double eps_tt;              /* tolerance of the current step's other rounds and crosses */
 } tt_fv_stats;
 
 typedef struct tt_fv_ctx tt_fv_ctx;
@@ -165,6 +194,16 @@ tt_status tt_fv_get(tt_fv_ctx* ctx, tt2 q_out[3]);
 
 /* Replace u^n by caller cores (checkpoint resume). */
 tt_status tt_fv_set(tt_fv_ctx* ctx, const tt2 q[3]);
+
+/* Sets the external source of a solver (method of manufactured solutions,
+ * Sec. 5.4): `nwaves` plane waves (host array, copied; at most
+ * params.forcing_waves per field, else TT_ERR_ARG).  Each stage evaluates
+ * them as exact cell averages -- the centre value times sinc(kx dx/2)
+ * sinc(ky dy/2), a rank-2 TT per wave -- at its own time (t, t + dt,
+ * t + dt/2 for the three stages of Eq. tt-ssprk3) and adds dt times them to
+ * u + dt L(u) before the forward-Euler round.  t0 is the time of the current
+ * state; each step advances it by dt.  nwaves = 0 removes the source. */
+tt_status tt_fv_set_forcing(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwaves, double t0);
 
 tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* out);
 void tt_fv_destroy(tt_fv_ctx* ctx);
@@ -333,6 +372,11 @@ tt_status tt_round_hadamard(const tt2* x, const tt2* z, double tol, int32_t rank
  *   TT_FN_WENO_S2    : {eps, mode (1: output n1 x 3*n2, columns m*n2+j;
  *                       0: output 3*n1 x n2, rows m*n1+i), nq (= 3)};
  *   TT_FN_LLF_LAMBDA : {g}; inputs = {h-, hu-, h+, hu+} (hu = hv for y faces).
+ *   TT_FN_LLF_FLUX   : {g, direction (0: x faces, 1: y faces)}; inputs = {h-, hu-, hv-, h+, hu+, hv+},
+ *                      each n1 x n2; y has 3 n1 rows: entry (c n1 + i, j) is component c of
+ *                      F^(Q-, Q+) = (F(Q-) + F(Q+))/2 - lambda (Q+ - Q-)/2 at face point (i, j), with F the
+ *                      nonlinear physical flux normal to the faces (Eq. nonlinear-SWE) and lambda the
+ *                      larger |u_n| + sqrt(g h) of the two states.
  * The output shape is (y->n1, y->n2). */
 size_t tt_cross_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap,
                                int32_t kick);

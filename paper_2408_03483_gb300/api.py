@@ -170,11 +170,13 @@ class Solver:
     """tt_fv_init / tt_fv_stage / tt_fv_step / tt_fv_get over a torch workspace."""
 
     def __init__(self, q0, eqn, scheme, n, dt, tol, rank_cap, g=9.81, H=1.0, f=0.0, lx=1.0, ly=1.0,
-                 kick=4, max_sweeps=10, max_iter=50, seed=0, precision="fp64", pivots="maxvol", stream=None):
+                 kick=4, max_sweeps=10, max_iter=50, seed=0, precision="fp64", pivots="maxvol", stream=None,
+                 eps_rule="fixed", c_eps=1.0, flux="products", forcing_waves=0):
         _require_cuda()
         self.lib = C.load()
         self.p = C.tt_fv_params(C.EQNS[eqn], C.SCHEMES[scheme], n, n, lx, ly, g, H, f, dt, tol, rank_cap,
-                                C.PRECISIONS[precision], C.PIVOTS[pivots], kick, max_sweeps, max_iter, seed)
+                                C.PRECISIONS[precision], C.PIVOTS[pivots], kick, max_sweeps, max_iter, seed,
+                                C.EPS_RULES[eps_rule], c_eps, C.FLUXES[flux], forcing_waves)
         nbytes = self.lib.tt_fv_workspace_size(ctypes.byref(self.p))
         if nbytes == 0:
             raise C.TTError("tt_fv_workspace_size", C.TT_ERR_ARG)
@@ -205,10 +207,15 @@ class Solver:
         arr = (C.tt2 * 3)(*[t.struct() for t in q])
         C.check("tt_fv_set", self.lib.tt_fv_set(self.h, arr))
 
+    def set_forcing(self, waves, t0=0.0):
+        """waves: (field, amp, kx, ky, omega, phase) plane waves of the source."""
+        arr = (C.tt_wave * max(1, len(waves)))(*[C.tt_wave(int(f), *map(float, rest)) for f, *rest in waves])
+        C.check("tt_fv_set_forcing", self.lib.tt_fv_set_forcing(self.h, arr, len(waves), float(t0)))
+
     def stats(self):
         st = C.tt_fv_stats()
         C.check("tt_fv_stats_get", self.lib.tt_fv_stats_get(self.h, ctypes.byref(st)))
-        return {k: (list(getattr(st, k)) if k in ("rank", "section_ms") else getattr(st, k))
+        return {k: (list(getattr(st, k)) if k in ("rank", "section_ms", "eps_u") else getattr(st, k))
                 for k, _ in st._fields_}
 
     def profile(self, enable=True):
@@ -314,7 +321,7 @@ class Batch:
     def stats(self, i):
         st = C.tt_fv_stats()
         C.check("tt_fv_batch_stats_get", self.lib.tt_fv_batch_stats_get(self.h, i, ctypes.byref(st)))
-        return {k: (list(getattr(st, k)) if k in ("rank", "section_ms") else getattr(st, k))
+        return {k: (list(getattr(st, k)) if k in ("rank", "section_ms", "eps_u") else getattr(st, k))
                 for k, _ in st._fields_}
 
     def close(self):

@@ -15,7 +15,7 @@ TT_LINEAR, TT_NONLINEAR = 0, 1
 TT_UP3, TT_UP5, TT_WENO5 = 0, 1, 2
 TT_FP64, TT_TF32, TT_BF16, TT_FP32 = 0, 1, 2, 3
 TT_PIVOT_MAXVOL, TT_PIVOT_LEARNED = 0, 1
-TT_FN_ENTRY, TT_FN_WENO_S1, TT_FN_WENO_S2, TT_FN_LLF_LAMBDA = 0, 1, 2, 3
+TT_FN_ENTRY, TT_FN_WENO_S1, TT_FN_WENO_S2, TT_FN_LLF_LAMBDA, TT_FN_LLF_FLUX = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "TT_OK", 1: "TT_ERR_ARG", 2: "TT_ERR_OOM", 3: "TT_ERR_CUDA", 4: "TT_ERR_NOCONV",
                 5: "TT_ERR_TIMEOUT", 6: "TT_ERR_RANKCAP",
@@ -25,6 +25,8 @@ SCHEMES = {"up3": TT_UP3, "up5": TT_UP5, "weno5": TT_WENO5}
 EQNS = {"linear": TT_LINEAR, "nonlinear": TT_NONLINEAR}
 PRECISIONS = {"fp64": TT_FP64, "fp32": TT_FP32, "tf32": TT_TF32, "bf16": TT_BF16}
 PIVOTS = {"maxvol": 0, "learned": 1}
+EPS_RULES = {"fixed": 0, "adaptive": 1}
+FLUXES = {"products": 0, "cross": 1}
 
 
 class TTError(RuntimeError):
@@ -44,7 +46,14 @@ class tt_fv_params(ctypes.Structure):
                 ("g", ctypes.c_double), ("H", ctypes.c_double), ("f", ctypes.c_double),
                 ("dt", ctypes.c_double), ("tol", ctypes.c_double), ("rank_cap", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("pivots", ctypes.c_int32), ("kick", ctypes.c_int32),
-                ("max_sweeps", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("seed", ctypes.c_uint32)]
+                ("max_sweeps", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("seed", ctypes.c_uint32),
+                ("eps_rule", ctypes.c_int32), ("c_eps", ctypes.c_double), ("flux", ctypes.c_int32),
+                ("forcing_waves", ctypes.c_int32)]
+
+
+class tt_wave(ctypes.Structure):
+    _fields_ = [("field", ctypes.c_int32), ("amp", ctypes.c_double), ("kx", ctypes.c_double),
+                ("ky", ctypes.c_double), ("omega", ctypes.c_double), ("phase", ctypes.c_double)]
 
 
 class tt_fv_stats(ctypes.Structure):
@@ -56,7 +65,8 @@ class tt_fv_stats(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("device_status", ctypes.c_uint32),
                 ("svd_calls", ctypes.c_int64), ("svd_p_sum", ctypes.c_int64), ("svd_pd_sum", ctypes.c_int64),
                 ("svd_sweeps_sum", ctypes.c_int64), ("section_ms", ctypes.c_double * 6),
-                ("learned_calls", ctypes.c_int64), ("learned_accepted", ctypes.c_int64)]
+                ("learned_calls", ctypes.c_int64), ("learned_accepted", ctypes.c_int64),
+                ("eps_u", ctypes.c_double * 3), ("eps_tt", ctypes.c_double)]
 
 
 TT_K_NAMES = ["gemm", "form_hadamard", "qr", "qr_apply", "jacobi_svd", "maxvol", "cross_eval", "stencil",
@@ -87,6 +97,7 @@ SIGNATURES = {
     "tt_fv_stage": (ctypes.c_int, [_vp, _i32]),
     "tt_fv_get": (ctypes.c_int, [_vp, _P(tt2)]),
     "tt_fv_set": (ctypes.c_int, [_vp, _P(tt2)]),
+    "tt_fv_set_forcing": (ctypes.c_int, [_vp, _P(tt_wave), _i32, _d]),
     "tt_fv_stats_get": (ctypes.c_int, [_vp, _P(tt_fv_stats)]),
     "tt_fv_destroy": (None, [_vp]),
     "tt_fv_profile": (ctypes.c_int, [_vp, _i32]),

@@ -18,9 +18,10 @@ struct DevTT {
   const double* b;
   int n1, n2, r;
 };
+constexpr int kCrossInputs = 6;
 struct EvalArgs {
   int fn;
-  DevTT in[4];
+  DevTT in[kCrossInputs];
   double prm[4];
   WenoConst wc;
 };
@@ -138,6 +139,29 @@ __device__ double eval_fn(const EvalArgs& e, int i, int j) {
       const double lm = fabs(qm / hm) + sqrt(g * hm);
       const double lp = fabs(qp / hp) + sqrt(g * hp);
       return fmax(lm, lp);
+    }
+    case TT_FN_LLF_FLUX: {
+      // component c of the LLF flux vector (Eq. LLF) at face point (ii, j):
+      // rows c n1 + ii stack the three components
+      const double g = e.prm[0];
+      const int k = e.prm[1] == 0.0 ? 1 : 2;  // normal momentum
+      const int n1 = e.in[0].n1;
+      const int c = i / n1, ii = i - c * n1;
+      double qm[3], qp[3];
+      for (int q = 0; q < 3; ++q) {
+        qm[q] = entry(e.in[q], ii, j);
+        qp[q] = entry(e.in[3 + q], ii, j);
+      }
+      const double um = qm[k] / qm[0], up = qp[k] / qp[0];
+      // physical flux normal to the faces, component c (Eq. nonlinear-SWE):
+      // q_n for c = 0, q_c u_n + g h^2 / 2 for c = n, q_c u_n otherwise
+      double fm = c == 0 ? qm[k] : qm[c] * um, fp = c == 0 ? qp[k] : qp[c] * up;
+      if (c == k) {
+        fm += 0.5 * g * qm[0] * qm[0];
+        fp += 0.5 * g * qp[0] * qp[0];
+      }
+      const double lam = fmax(fabs(um) + sqrt(g * qm[0]), fabs(up) + sqrt(g * qp[0]));
+      return 0.5 * (fm + fp) - 0.5 * lam * (qp[c] - qm[c]);
     }
   }
   return 0.0;
@@ -286,7 +310,8 @@ static std::vector<int> kick_indices(int n, int count, unsigned seed, int sweep,
 static EvalArgs make_args(const CrossFn& f) {
   EvalArgs e{};
   e.fn = f.fn;
-  for (int q = 0; q < f.nin && q < 4; ++q) e.in[q] = DevTT{f.in[q].a, f.in[q].b, f.in[q].n1, f.in[q].n2, f.in[q].r};
+  for (int q = 0; q < f.nin && q < kCrossInputs; ++q)
+    e.in[q] = DevTT{f.in[q].a, f.in[q].b, f.in[q].n1, f.in[q].n2, f.in[q].r};
   for (int q = 0; q < 4; ++q) e.prm[q] = f.prm[q];
   e.wc = weno_const();
   return e;

@@ -247,7 +247,8 @@ struct Solver {
   PivotRecorder* rec = nullptr;    // training-data capture, when enabled
   // converged column pivots of each cross site at its previous call:
   // WENO (direction, field, side, step) = 24 sites, then LLF lambda per direction
-  std::vector<int> sites[26];
+  // (then the LF-cross flux per direction)
+  std::vector<int> sites[28];
   // range-finder sketch width that certified the previous lambda o jump
   // rounding of each (direction, component) within the current step
   int rf_hint[2][3] = {};
@@ -255,6 +256,13 @@ struct Solver {
   // the current step: the initial guess of the next lambda cross
   TT lam_prev[2];
   bool lam_prev_ok[2] = {false, false};
+  // tolerances of the current step (Sec. 4.4): p.tol holds eps_TT of the
+  // rounds and crosses, tol_u[c] the per-field forward-Euler and SSP rounds
+  double tol_u[3] = {0.0, 0.0, 0.0};
+  // external source (tt_fv_set_forcing): plane waves, the time of the
+  // current state and the time the current stage evaluates L at
+  std::vector<tt_wave> waves;
+  double time = 0.0, stage_time = 0.0;
   ~Solver();
 };
 
@@ -295,6 +303,71 @@ void record_pivots(Exec& ex, const TT& x0, const std::vector<int>& prev, const s
 }
 
 static int nq_of(int recon) { return recon == TT_UP3 ? 2 : 3; }
+
+// ---------------------------------------------------------------- external source
+struct WaveSet {
+  int n;
+  double amp[TT_MAX_WAVES], kx[TT_MAX_WAVES], ky[TT_MAX_WAVES], om[TT_MAX_WAVES], ph[TT_MAX_WAVES];
+};
+
+__device__ __forceinline__ double sinc_dev(double z) { return z == 0.0 ? 1.0 : sin(z) / z; }
+
+// Cell averages of sum_w amp_w cos(kx_w x + ky_w y - om_w t + ph_w) as a TT of
+// rank 2 n: A[:, 2w] = sx cos(kx xc), A[:, 2w+1] = -sx sin(kx xc),
+// B[:, 2w] = amp sy cos(ky yc - om t + ph), B[:, 2w+1] = amp sy sin(...), with
+// sx = sinc(kx dx/2), sy = sinc(ky dy/2) (the exact average of a plane wave
+// over a cell is its centre value times these factors).
+__global__ void k_wave_cores(WaveSet w, double t, int n1, int n2, double dx, double dy, double* __restrict__ A,
+                             double* __restrict__ B) {
+  const long na = (long)n1 * 2 * w.n, total = na + (long)n2 * 2 * w.n;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+    if (q < na) {
+      const int i = int(q % n1), col = int(q / n1), v = col >> 1;
+      const double a = w.kx[v] * (i + 0.5) * dx, sx = sinc_dev(0.5 * w.kx[v] * dx);
+      A[q] = (col & 1) ? -sx * sin(a) : sx * cos(a);
+    } else {
+      const long r = q - na;
+      const int j = int(r % n2), col = int(r / n2), v = col >> 1;
+      const double b = w.ky[v] * (j + 0.5) * dy - w.om[v] * t + w.ph[v];
+      const double sy = w.amp[v] * sinc_dev(0.5 * w.ky[v] * dy);
+      B[r] = (col & 1) ? sy * sin(b) : sy * cos(b);
+    }
+  }
+}
+
+// Number of source waves of field c (in the sizing pass: the most allowed).
+static int wave_count(const Solver& S, const Exec& ex, int c) {
+  if (ex.dry) return S.p.forcing_waves;
+  int n = 0;
+  for (const tt_wave& w : S.waves) n += w.field == c;
+  return n;
+}
+
+// The source of field c at the current stage's time as a TT allocated from
+// ex's arena (rank 2 per wave); false when the field has no wave.
+static bool source_tt(Solver& S, Exec& ex, int c, TT& out) {
+  const int nw = wave_count(S, ex, c);
+  if (nw <= 0) return false;
+  out = alloc_tt(*ex.ar, S.p.nx, S.p.ny, 2 * nw);
+  out.r = 2 * nw;
+  if (ex.dry) return true;
+  WaveSet ws{};
+  for (const tt_wave& w : S.waves)
+    if (w.field == c) {
+      ws.amp[ws.n] = w.amp;
+      ws.kx[ws.n] = w.kx;
+      ws.ky[ws.n] = w.ky;
+      ws.om[ws.n] = w.omega;
+      ws.ph[ws.n] = w.phase;
+      ws.n++;
+    }
+  const long total = (long)(S.p.nx + S.p.ny) * 2 * nw;
+  const int blocks = std::max(1, std::min(ceil_div(total, 256), 1184));
+  TT_KERNEL(ex, K_OTHER, 20.0 * total, 8.0 * total,
+            k_wave_cores<<<blocks, 256, 0, ex.s>>>(ws, S.stage_time, S.p.nx, S.p.ny, S.p.lx / S.p.nx,
+                                                   S.p.ly / S.p.ny, out.a, out.b));
+  return true;
+}
 
 // Linear (Upwind3/Upwind5) faces of one field for direction d (0: x, 1: y)
 static void faces_linear(Solver& S, Exec& ex, const TT& q, int d, TT& qm, TT& qp) {
@@ -421,6 +494,44 @@ static void face_lambda(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int
   cross(ex, fl, qm[0].n1, qm[0].n2, x0, p.tol, p.rank_cap, kick, sweeps, seed, lam);
 }
 
+// LF-cross (Sec. 4.2, the alternative the paper weighs against the product
+// form): the LLF flux vector of direction d at the faces, F^(Q-, Q+) =
+// (F(Q-) + F(Q+))/2 - lambda (Q+ - Q-)/2, by one cross of the six face states
+// with its three components stacked along the first mode, then split into
+// one TT per component (rows c f1 .. (c+1) f1 of the first core, the second
+// core shared).  Initial guess: the h- faces (their column mode is the
+// flux's); the cross ends in a round at tol like every cross.
+static void flux_by_cross(Solver& S, Exec& ex, const TT qm[3], const TT qp[3], int d, unsigned seed, TT Fh[3]) {
+  const tt_fv_params& p = S.p;
+  const int f1 = qm[0].n1, f2 = qm[0].n2, cap = p.rank_cap;
+  Scope sc(*ex.ar);
+  TT ins[6] = {qm[0], qm[1], qm[2], qp[0], qp[1], qp[2]};
+  CrossFn fl;
+  fl.fn = TT_FN_LLF_FLUX;
+  fl.in = ins;
+  fl.nin = 6;
+  fl.site = &S.sites[26 + d];
+  fl.prm[0] = p.g;
+  fl.prm[1] = d;
+  const int kick = p.kick > 0 ? p.kick : 4, sweeps = p.max_sweeps > 0 ? p.max_sweeps : 10;
+  TT st = alloc_tt(*ex.ar, 3 * f1, f2, cap);
+  cross(ex, fl, 3 * f1, f2, qm[0], p.tol, cap, kick, sweeps, seed, st);
+  StencilSet ss;
+  ss.nout = 3;
+  const double one = 1.0;
+  for (int c = 0; c < 3; ++c) {
+    TT_REQUIRE(Fh[c].n1 == f1 && Fh[c].n2 == f2 && Fh[c].cap >= st.r, TT_ERR_ARG);
+    ss.out[c].dst = Fh[c].a;
+    ss.out[c].ld = f1;
+    add_taps(ss.out[c], &one, 1, 0, c * f1);
+  }
+  stencil(ex, ss, st.a, 3L * f1, f1, st.r);
+  for (int c = 0; c < 3; ++c) {
+    scaled_copy(ex, Fh[c].b, st.b, (long)f2 * st.r, 1.0);
+    Fh[c].r = st.r;
+  }
+}
+
 // LLF combination of one component (Eq. LLF-TT): with dd = round(Q+ - Q-) and
 // ld = round(lambda o dd) computed earlier, out = round(F-/2 + F+/2 - ld/2)
 static void llf_combine(Solver& S, Exec& ex, const TT& Fm, const TT& Fp, const TT& ld, TT& out) {
@@ -528,8 +639,12 @@ static void forward_euler_linear(Solver& S, Exec& ex, const TT Q[3], unsigned se
     terms[1].push_back(Term{p.dt * p.f, Q[2]});
     terms[2].push_back(Term{-p.dt * p.f, Q[1]});
   }
+  for (int c = 0; c < 3; ++c) {
+    TT src;
+    if (source_tt(S, ex, c, src)) terms[c].push_back(Term{p.dt, src});
+  }
   SectionTimer st4(S.section_ms[4]);
-  parallel_tasks(ex, 3, [&](Exec& cx, int c) { round_sum(cx, terms[c], p.tol, cap, out[c]); });
+  parallel_tasks(ex, 3, [&](Exec& cx, int c) { round_sum(cx, terms[c], S.tol_u[c], cap, out[c]); });
 }
 
 // F(u) = round(u + dt L(u)) for the nonlinear SWE as one task graph.  Every
@@ -589,6 +704,30 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
   }
   TT F[2][2][3], lam[2], Fh[2][3], dd[2][3], ld[2][3], D[2][3];
   TT rh[2][2], hh[2][2], uu[2][2], vv[2][2];
+  Reciprocal R[2][2];
+  int qd_node[2][3];
+  if (p.flux == TT_FLUX_CROSS) {
+    // LF-cross: per direction one cross of the whole flux vector, then the
+    // quadrature / difference of each component
+    for (int d = 0; d < 2; ++d) {
+      for (int c = 0; c < 3; ++c) {
+        Fh[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
+        D[d][c] = alloc_tt(*ex.ar, p.nx, p.ny, cap);
+      }
+      std::vector<int> deps;
+      for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 2; ++k) deps.push_back(face[d][c][k]);
+      const int fx = G.add("llf_flux_cross", 85, [&, d](Exec& cx) {
+        flux_by_cross(S, cx, qm[d], qp[d], d, seed + 64u * d + 44u, Fh[d]);
+        mark(2);
+      }, deps);
+      for (int c = 0; c < 3; ++c)
+        qd_node[d][c] = G.add("quad_difference", 40, [&, d, c](Exec& cx) {
+          quad_and_difference(S, cx, Fh[d][c], d, D[d][c]);
+          mark(3);
+        }, {fx});
+    }
+  } else {
   for (int d = 0; d < 2; ++d) {
     lam[d] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
     for (int sd = 0; sd < 2; ++sd) {
@@ -606,8 +745,7 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
     }
   }
   auto side = [&](int d, int sd) -> const TT* { return sd == 0 ? qm[d] : qp[d]; };
-  Reciprocal R[2][2];
-  int hh_node[2][2], vel_node[2][2][2], flux_node[2][2][3], lam_node[2], ld_node[2][3], qd_node[2][3];
+  int hh_node[2][2], vel_node[2][2][2], flux_node[2][2][3], lam_node[2], ld_node[2][3];
   for (int d = 0; d < 2; ++d) {
     const int k = d == 0 ? 1 : 2;  // the normal momentum hu (x) or hv (y)
     for (int sd = 0; sd < 2; ++sd) {
@@ -694,12 +832,16 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
       }, {llf});
     }
   }
+  }  // products form
   for (int c = 0; c < 3; ++c)
     G.add("forward_euler", 30, [&, c](Exec& cx) {
       std::vector<Term> terms{Term{1.0, Q[c]}, Term{-p.dt, D[0][c]}, Term{-p.dt, D[1][c]}};
       if (p.f != 0.0 && c == 1) terms.push_back(Term{p.dt * p.f, Q[2]});
       if (p.f != 0.0 && c == 2) terms.push_back(Term{-p.dt * p.f, Q[1]});
-      round_sum(cx, terms, p.tol, cap, out[c]);
+      Scope s2(*cx.ar);
+      TT src;
+      if (source_tt(S, cx, c, src)) terms.push_back(Term{p.dt, src});
+      round_sum(cx, terms, S.tol_u[c], cap, out[c]);
       mark(4);
     }, {qd_node[0][c], qd_node[1][c]});
   G.run();
@@ -726,9 +868,36 @@ static void forward_euler(Solver& S, Exec& ex, const TT Q[3], unsigned seed, TT 
 // solver restarted from a checkpoint draws the same kicks
 static unsigned stage_seed(const Solver& S, int stage) { return S.p.seed + 1000u * (unsigned)stage; }
 
+// Truncation tolerances of a step (Sec. 4.4), from the step's input state:
+// under TT_EPS_ADAPTIVE eps_u = min(1e-3, C V^(1/2) dx^(p-1/2) / ||u||_F) per
+// field (Eq. modified-eps-tt-formula) and eps_TT = C V^(1/2) dx^(p-1/2) /
+// max_q ||q||_F for the other rounds (Eq. eps-tt-formula); under
+// TT_EPS_FIXED the fixed tol everywhere.
+static void step_tolerances(Solver& S, Exec& ex) {
+  if (S.p.eps_rule != TT_EPS_ADAPTIVE) {
+    for (int c = 0; c < 3; ++c) S.tol_u[c] = S.p.tol;
+    return;
+  }
+  Scope sc(*ex.ar);
+  double* d = ex.ar->get<double>(8);
+  for (int c = 0; c < 3; ++c) tt_sum_norm(ex, S.Qn[c], d + 2 * c);
+  double v[6];
+  fetch_doubles(ex, d, 6, v);
+  const int order = S.p.recon == TT_UP3 ? 3 : 5;
+  const double num = S.p.c_eps * std::sqrt(S.p.lx * S.p.ly) * std::pow(S.p.lx / S.p.nx, order - 0.5);
+  double mx = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double nrm = v[2 * c + 1];
+    mx = std::max(mx, nrm);
+    S.tol_u[c] = nrm > 0.0 ? std::min(1e-3, num / nrm) : 1e-3;
+  }
+  S.p.tol = mx > 0.0 ? num / mx : 1e-3;
+}
+
 static void run_stage(Solver& S, Exec& ex, int stage) {
   TT_REQUIRE(stage == S.next_stage, TT_ERR_ARG);
   if (stage == 0) {
+    step_tolerances(S, ex);
     // the lambda guesses and sketch widths carried between stages are
     // per-step state: a solver restarted from a checkpoint of Q (taken
     // between steps) repeats the next step bit for bit
@@ -740,21 +909,24 @@ static void run_stage(Solver& S, Exec& ex, int stage) {
   const tt_fv_params& p = S.p;
   TT f[3];
   for (int c = 0; c < 3; ++c) f[c] = alloc_tt(*ex.ar, p.nx, p.ny, p.rank_cap);
+  // the stages of Eq. tt-ssprk3 evaluate L at t^n, t^n + dt and t^n + dt/2
+  S.stage_time = S.time + (stage == 0 ? 0.0 : stage == 1 ? p.dt : 0.5 * p.dt);
   forward_euler(S, ex, S.Qs, stage_seed(S, stage), f);
   if (stage == 0) {
     for (int c = 0; c < 3; ++c) copy_tt(ex, f[c], S.Qs[c]);
   } else if (stage == 1) {
     SectionTimer st5(S.section_ms[5]);
     parallel_tasks(ex, 3, [&](Exec& cx, int c) {
-      round_sum(cx, {Term{0.75, S.Qn[c]}, Term{0.25, f[c]}}, p.tol, p.rank_cap, S.Qs[c]);
+      round_sum(cx, {Term{0.75, S.Qn[c]}, Term{0.25, f[c]}}, S.tol_u[c], p.rank_cap, S.Qs[c]);
     });
   } else {
     SectionTimer st5(S.section_ms[5]);
     parallel_tasks(ex, 3, [&](Exec& cx, int c) {
-      round_sum(cx, {Term{1.0 / 3.0, S.Qn[c]}, Term{2.0 / 3.0, f[c]}}, p.tol, p.rank_cap, S.Qn[c]);
+      round_sum(cx, {Term{1.0 / 3.0, S.Qn[c]}, Term{2.0 / 3.0, f[c]}}, S.tol_u[c], p.rank_cap, S.Qn[c]);
     });
     for (int c = 0; c < 3; ++c) copy_tt(ex, S.Qn[c], S.Qs[c]);
     S.step_count++;
+    if (!ex.dry) S.time += p.dt;
   }
   S.next_stage = (stage + 1) % 3;
 }
@@ -781,6 +953,10 @@ static bool valid_params(const tt_fv_params* p) {
   if (p->precision < TT_FP64 || p->precision > TT_FP32) return false;
   if (p->pivots != TT_PIVOT_MAXVOL && p->pivots != TT_PIVOT_LEARNED) return false;
   if (p->eqn == TT_LINEAR && !(p->H > 0.0)) return false;
+  if (p->eps_rule != TT_EPS_FIXED && p->eps_rule != TT_EPS_ADAPTIVE) return false;
+  if (p->eps_rule == TT_EPS_ADAPTIVE && !(p->c_eps > 0.0)) return false;
+  if (p->flux != TT_FLUX_PRODUCTS && p->flux != TT_FLUX_CROSS) return false;
+  if (p->forcing_waves < 0 || p->forcing_waves > TT_MAX_WAVES) return false;
   return true;
 }
 
@@ -916,6 +1092,7 @@ tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws
   if (!ctx) return TT_ERR_OOM;
   Solver& S = ctx->S;
   S.p = *p;
+  for (int c = 0; c < 3; ++c) S.tol_u[c] = p->tol;
   S.s = static_cast<cudaStream_t>(stream);
   S.nq = nq_of(p->recon);
   try {
@@ -1000,6 +1177,22 @@ tt_status tt_fv_set(tt_fv_ctx* ctx, const tt2 q[3]) {
   return TT_OK;
 }
 
+tt_status tt_fv_set_forcing(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwaves, double t0) {
+  if (!ctx || nwaves < 0 || (nwaves > 0 && !waves) || !std::isfinite(t0)) return TT_ERR_ARG;
+  Solver& S = ctx->S;
+  int per[3] = {0, 0, 0};
+  for (int i = 0; i < nwaves; ++i) {
+    const tt_wave& w = waves[i];
+    if (w.field < 0 || w.field > 2 || !std::isfinite(w.amp) || !std::isfinite(w.kx) || !std::isfinite(w.ky) ||
+        !std::isfinite(w.omega) || !std::isfinite(w.phase))
+      return TT_ERR_ARG;
+    if (++per[w.field] > S.p.forcing_waves) return TT_ERR_ARG;
+  }
+  S.waves.assign(waves, waves + nwaves);
+  S.time = t0;
+  return TT_OK;
+}
+
 tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* o) {
   if (!ctx || !o) return TT_ERR_ARG;
   Solver& S = ctx->S;
@@ -1024,6 +1217,8 @@ tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* o) {
   o->learned_calls = ex.learned_calls;
   o->learned_accepted = ex.learned_accepted;
   for (int i = 0; i < 6; ++i) o->section_ms[i] = S.section_ms[i];
+  for (int c = 0; c < 3; ++c) o->eps_u[c] = S.tol_u[c];
+  o->eps_tt = S.p.tol;
   unsigned st = 0;
   if (cudaMemcpyAsync(&st, ex.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, S.s) != cudaSuccess ||
       cudaStreamSynchronize(S.s) != cudaSuccess)
@@ -1332,11 +1527,11 @@ size_t tt_cross_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t 
 tt_status tt_cross(int32_t fn, const tt2* inputs, int32_t ninputs, const tt2* x0, const double* fparams, double tol,
                    int32_t rank_cap, int32_t kick, int32_t max_sweeps, uint32_t seed, tt2* y, int32_t* sweeps_out,
                    void* ws, size_t ws_bytes, void* stream) {
-  if (fn < TT_FN_ENTRY || fn > TT_FN_LLF_LAMBDA || !inputs || ninputs < 1 || ninputs > 4 || !valid_tt(x0) || !y ||
+  if (fn < TT_FN_ENTRY || fn > TT_FN_LLF_FLUX || !inputs || ninputs < 1 || ninputs > 6 || !valid_tt(x0) || !y ||
       !y->a || !y->b || rank_cap < 1 || kick < 0 || max_sweeps < 1 || x0->n2 != y->n2 || !(tol >= 0.0) ||
       y->cap < rank_cap)
     return TT_ERR_ARG;
-  const int need = fn == TT_FN_LLF_LAMBDA ? 4 : 1;
+  const int need = fn == TT_FN_LLF_LAMBDA ? 4 : fn == TT_FN_LLF_FLUX ? 6 : 1;
   if (ninputs != need) return TT_ERR_ARG;
   for (int q = 0; q < ninputs; ++q) {
     if (!valid_tt(&inputs[q])) return TT_ERR_ARG;
@@ -1351,16 +1546,19 @@ tt_status tt_cross(int32_t fn, const tt2* inputs, int32_t ninputs, const tt2* x0
       else
         return TT_ERR_ARG;
       if (y->n1 != e1 || y->n2 != e2) return TT_ERR_ARG;
+    } else if (fn == TT_FN_LLF_FLUX) {
+      if (3 * inputs[q].n1 != e1 || inputs[q].n2 != e2) return TT_ERR_ARG;
     } else if (inputs[q].n1 != e1 || inputs[q].n2 != e2) {
       return TT_ERR_ARG;
     }
   }
+  if (fn == TT_FN_LLF_FLUX && (!fparams || (fparams[1] != 0.0 && fparams[1] != 1.0))) return TT_ERR_ARG;
   if (fn == TT_FN_WENO_S1 && (fparams[2] != 0.0 && fparams[2] != 1.0)) return TT_ERR_ARG;
   if ((fn == TT_FN_WENO_S1 || fn == TT_FN_WENO_S2 || fn == TT_FN_ENTRY) && !fparams && fn != TT_FN_ENTRY)
     return TT_ERR_ARG;
   if (fn == TT_FN_LLF_LAMBDA && !fparams) return TT_ERR_ARG;
   return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
-    TT ins[4];
+    TT ins[6];
     for (int q = 0; q < ninputs; ++q) ins[q] = to_tt(inputs[q]);
     CrossFn f;
     f.fn = fn;
@@ -1369,6 +1567,10 @@ tt_status tt_cross(int32_t fn, const tt2* inputs, int32_t ninputs, const tt2* x0
     if (fparams)
       for (int q = 0; q < 3; ++q) f.prm[q] = fparams[q];
     if (fn == TT_FN_LLF_LAMBDA) f.prm[0] = fparams[0];
+    if (fn == TT_FN_LLF_FLUX) {
+      f.prm[0] = fparams[0];
+      f.prm[1] = fparams[1];
+    }
     TT X0 = to_tt(*x0), Y = to_tt(*y);
     const int sw = cross(ex, f, y->n1, y->n2, X0, tol, rank_cap, kick, max_sweeps, seed, Y);
     y->rank = Y.r;
