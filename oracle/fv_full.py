@@ -190,17 +190,24 @@ def rhs(Q, eqn, scheme, p):
     return out
 
 
-def euler(Q, eqn, scheme, p, dt):
+def euler(Q, eqn, scheme, p, dt, src=None):
+    """Q + dt (L(Q) + src), src the cell averages of an external source at the
+    stage's time (or None)."""
     L = rhs(Q, eqn, scheme, p)
-    return [Q[c] + dt * L[c] for c in range(3)]
+    if src is None:
+        return [Q[c] + dt * L[c] for c in range(3)]
+    return [Q[c] + dt * (L[c] + src[c]) for c in range(3)]
 
 
-def ssprk3_step(Q, eqn, scheme, p, dt):
-    """One SSP-RK3 step (Sec. 4.4, Eq. tt-ssprk3 without rounding)."""
-    u1 = euler(Q, eqn, scheme, p, dt)
-    f1 = euler(u1, eqn, scheme, p, dt)
+def ssprk3_step(Q, eqn, scheme, p, dt, source=None, t=0.0):
+    """One SSP-RK3 step (Sec. 4.4, Eq. tt-ssprk3 without rounding) from time t;
+    source(time) -> cell averages of an external source (a manufactured
+    solution's forcing), evaluated at the stages' times t, t + dt, t + dt/2."""
+    S = (lambda s: None) if source is None else source  # noqa: E731
+    u1 = euler(Q, eqn, scheme, p, dt, S(t))
+    f1 = euler(u1, eqn, scheme, p, dt, S(t + dt))
     u2 = [0.75 * Q[c] + 0.25 * f1[c] for c in range(3)]
-    f2 = euler(u2, eqn, scheme, p, dt)
+    f2 = euler(u2, eqn, scheme, p, dt, S(t + 0.5 * dt))
     return [Q[c] / 3.0 + 2.0 / 3.0 * f2[c] for c in range(3)]
 
 
