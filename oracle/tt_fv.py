@@ -317,20 +317,53 @@ def _tol_u(w, c):
     return w["tol_u"][c] if "tol_u" in w else w["tol"]
 
 
-def forward_euler(Q, w, p, dt, stats=None, seed=0):
-    """F(u) = round(u + dt L(u), eps^u) per component (Eq. tt-forward-euler)."""
+def waves_tt(waves, field, n1, n2, t, lx, ly):
+    """Cell averages of sum amp cos(kx x + ky y - omega t + phase) over the
+    waves of `field` as TT cores: a plane wave averaged over a cell is its
+    centre value times sinc(kx dx/2) sinc(ky dy/2), and cos(a + b) =
+    cos a cos b - sin a sin b is rank 2."""
+    dx, dy = lx / n1, ly / n2
+    xc = (np.arange(n1) + 0.5) * dx
+    yc = (np.arange(n2) + 0.5) * dy
+    A, B = [], []
+    for c, amp, kx, ky, om, ph in waves:
+        if c != field:
+            continue
+        sx = np.sinc(kx * dx / (2 * np.pi))  # numpy's sinc is sin(pi z)/(pi z)
+        sy = np.sinc(ky * dy / (2 * np.pi))
+        a = kx * xc
+        b = ky * yc - om * t + ph
+        A += [sx * np.cos(a), -sx * np.sin(a)]
+        B += [amp * sy * np.cos(b), amp * sy * np.sin(b)]
+    if not A:
+        return None
+    return (np.stack(A, axis=1), np.stack(B, axis=1))
+
+
+def forward_euler(Q, w, p, dt, stats=None, seed=0, t=0.0):
+    """F(u) = round(u + dt (L(u) + S_m(t)), eps^u) per component (Eq.
+    tt-forward-euler), S_m the external source w["forcing"] (plane waves) at
+    time t when present."""
     terms = rhs_terms(Q, w, p, stats, seed)
+    n1, n2 = Q[0][0].shape[0], Q[0][1].shape[0]
     out = []
     for c in range(3):
-        X = T.add([(1.0, Q[c])] + [(dt * a, Y) for a, Y in terms[c]])
-        out.append(T.rnd(X, _tol_u(w, c), w["cap"]))
+        X = [(1.0, Q[c])] + [(dt * a, Y) for a, Y in terms[c]]
+        if w.get("forcing"):
+            Sm = waves_tt(w["forcing"], c, n1, n2, t, p["lx"], p["ly"])
+            if Sm is not None:
+                X.append((dt, Sm))
+        out.append(T.rnd(T.add(X), _tol_u(w, c), w["cap"]))
     return out
 
 
-def stage(Qn, Qs, k, w, p, stats=None, seed=0):
+STAGE_TIME = (0.0, 1.0, 0.5)  # stage k evaluates L at t^n + STAGE_TIME[k] dt
+
+
+def stage(Qn, Qs, k, w, p, stats=None, seed=0, t=0.0):
     """Stage k (0, 1, 2) of the TT SSP-RK3 of Eq. tt-ssprk3 given u^n (Qn) and
-    the stage input Qs (u^n, u^(1), u^(2))."""
-    f = forward_euler(Qs, w, p, p["dt"], stats, seed)
+    the stage input Qs (u^n, u^(1), u^(2)); t = t^n."""
+    f = forward_euler(Qs, w, p, p["dt"], stats, seed, t + STAGE_TIME[k] * p["dt"])
     if k == 0:
         return f
     a, b = (0.75, 0.25) if k == 1 else (1.0 / 3.0, 2.0 / 3.0)
@@ -357,11 +390,11 @@ def step_tolerances(Qn, w, p):
     return (num / big if big > 0 else 1e-3), eps_u
 
 
-def step(Qn, w, p, stats=None, seed=0):
-    """One full SSP-RK3 step in TT format (Eq. tt-ssprk3), with the step's
-    truncation tolerances of Sec. 4.4."""
+def step(Qn, w, p, stats=None, seed=0, t=0.0):
+    """One full SSP-RK3 step in TT format (Eq. tt-ssprk3) from time t, with the
+    step's truncation tolerances of Sec. 4.4."""
     eps_tt, eps_u = step_tolerances(Qn, w, p)
     ws = dict(w, tol=eps_tt, tol_u=eps_u)
-    u1 = stage(Qn, Qn, 0, ws, p, stats, seed)
-    u2 = stage(Qn, u1, 1, ws, p, stats, seed + 1000)
-    return stage(Qn, u2, 2, ws, p, stats, seed + 2000)
+    u1 = stage(Qn, Qn, 0, ws, p, stats, seed, t)
+    u2 = stage(Qn, u1, 1, ws, p, stats, seed + 1000, t)
+    return stage(Qn, u2, 2, ws, p, stats, seed + 2000, t)

@@ -47,12 +47,13 @@ def field_errors(got, ref):
     return out
 
 
-def field_scales(ref, eqn, p, dt):
-    """S_c of the module docstring for the reference state ``ref``."""
+def field_scales(ref, eqn, p, dt, d=None):
+    """S_c of the module docstring for the reference state ``ref`` (cell
+    widths d = (dx, dy); by default the domain of p over ref's shape)."""
     from oracle import fv_full as FA
     r = fulls(ref)
     n1, n2 = r[0].shape
-    dx, dy = p.get("lx", 1.0) / n1, p.get("ly", 1.0) / n2
+    dx, dy = d if d is not None else (p.get("lx", 1.0) / n1, p.get("ly", 1.0) / n2)
     F = FA.phys_flux(r, "x", eqn, p)
     Gf = FA.phys_flux(r, "y", eqn, p)
     return [float(np.linalg.norm(r[c]) + 2 * dt / dx * np.linalg.norm(F[c]) + 2 * dt / dy * np.linalg.norm(Gf[c]))
