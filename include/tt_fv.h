@@ -151,14 +151,16 @@ typedef struct tt_fv_ctx tt_fv_ctx;
 enum {
   TT_K_GEMM = 0,      /* FP64 split-K GEMM (range finder, factor products)     */
   TT_K_FORM = 1,      /* full Hadamard face tensor formation                   */
-  TT_K_QR = 2,        /* Householder TSQR row blocks                           */
-  TT_K_QR_APPLY = 3,  /* application of the TSQR orthogonal factors            */
+  TT_K_QR = 2,        /* Householder TSQR row blocks (leaves)                  */
+  TT_K_QR_APPLY = 3,  /* application of the leaves' orthogonal factors         */
   TT_K_JACOBI = 4,    /* one-sided Jacobi SVD of the small core                */
   TT_K_MAXVOL = 5,    /* maximum-volume row selection                          */
   TT_K_EVAL = 6,      /* cross fibre evaluation (WENO5, LLF speed)             */
   TT_K_STENCIL = 7,   /* core stencils: reconstruction, quadrature, (T-1)/dx   */
   TT_K_OTHER = 8,     /* copies, transposes, norms, small solves               */
-  TT_K_NCLASS = 9
+  TT_K_QR_MERGE = 9,  /* TSQR merges of stacked triangular factors              */
+  TT_K_QR_APPLY_MERGE = 10, /* application of the merges' orthogonal factors    */
+  TT_K_NCLASS = 11
 };
 
 typedef struct {
@@ -349,7 +351,11 @@ tt_status tt_contract(int32_t precision, int32_t split, int32_t m, int32_t n, in
  * the library until process exit) instead of a caller workspace, so sizes
  * whose tt_round_workspace_size exceeds 32 MiB are rejected with TT_ERR_ARG.
  * The first call on a device (with that device current) looks up the array's
- * device address; make that first call before any stream capture.  Every call
+ * device address; make that first call before any stream capture.  The
+ * address is kept for the life of the process: after a cudaDeviceReset the
+ * array lives at a new address, so do not call this entry point on a device
+ * that was reset in the same process.  Like tt_round, the call waits for its
+ * stream before returning (it reads the device status word).  Every call
  * shares the one array and overwrites it: calls that overlap on the GPU (two
  * streams, two threads) race, so serialise them. */
 tt_status tt_round_noalloc(const tt2* x, double tol, int32_t rank_cap, tt2* y, double* err_out,

@@ -70,7 +70,7 @@ class tt_fv_stats(ctypes.Structure):
 
 
 TT_K_NAMES = ["gemm", "form_hadamard", "qr", "qr_apply", "jacobi_svd", "maxvol", "cross_eval", "stencil",
-              "other"]
+              "other", "qr_merge", "qr_apply_merge"]
 
 
 class tt_mlp(ctypes.Structure):

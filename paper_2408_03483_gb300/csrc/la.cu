@@ -6,6 +6,7 @@
 // real FP64 work spreads it over at least ~2 CTAs per SM (split-K, row
 // blocks); the small dense factorisations (p <= 112) run one per CTA with the
 // matrix resident in shared memory.
+#include <cstdlib>
 #include <cfloat>
 #include <cmath>
 #include <algorithm>
@@ -512,10 +513,20 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, Merg
 // most 4 from p = 32 up, where a merge is FP64-bound on its SM: a level of
 // 4-triangle nodes on separate SMs, then a short second level, beats one SM
 // eliminating 11 triangles in turn (442 us at p = 40)
+// TT_QR_FANIN (environment, read once): the largest merge fan-in from p = 32
+// up (default 4), for tuning.
+static int qr_fanin_cap() {
+  static const int v = [] {
+    const char* e = std::getenv("TT_QR_FANIN");
+    const int x = e ? std::atoi(e) : 0;
+    return x >= 2 ? x : 4;
+  }();
+  return v;
+}
 static int qr_merge_fanin(int p, size_t elem) {
   const size_t per = ((size_t)p * p + (size_t)16 * p) * elem;
   const int g = std::max(2, int(QR_SMEM_MAX / per));
-  return p >= 32 ? std::min(g, 4) : g;
+  return p >= 32 ? std::min(g, qr_fanin_cap()) : g;
 }
 
 static int qr_leaf_rows(int p, size_t elem) {
@@ -587,7 +598,8 @@ static void tsqr_run(Exec& ex, int nj, const void* const* X, const int* x64, con
     if (!ex.dry) {
       smem_attr_once(k_qr_merge<Real>);
       const size_t smem = ((size_t)maxin * p * p + (size_t)16 * p) * sizeof(Real);
-      TT_KERNEL(ex, K_QR, mfl, mby, k_qr_merge<Real><<<nodes_total, QR_THREADS, smem, ex.s>>>(mj[0], mj[1], p, g));
+      TT_KERNEL(ex, K_QR_MERGE, mfl, mby,
+                k_qr_merge<Real><<<nodes_total, QR_THREADS, smem, ex.s>>>(mj[0], mj[1], p, g));
     }
   }
   for (int q = 0; q < nj; ++q) t[q]->R = R[q];
@@ -799,7 +811,7 @@ static void tsqr_apply_run(Exec& ex, int nj, const QRTreeT<Real>* const* t, cons
     if (!ex.dry && nodes_total > 0) {
       smem_attr_once(k_qr_apply_merge<Real>);
       const size_t smem = ((size_t)maxin * p * k + (size_t)16 * k) * sizeof(Real);
-      TT_KERNEL(ex, K_QR_APPLY, fl, by,
+      TT_KERNEL(ex, K_QR_APPLY_MERGE, fl, by,
                 k_qr_apply_merge<Real><<<nodes_total, QR_THREADS, smem, ex.s>>>(aj[0], aj[1], p, g, k));
     }
   }
@@ -1433,16 +1445,21 @@ __device__ ArgMax block_argmax(ArgMax x, double* rv, long* ri) {
   return ArgMax{rv[32], ri[32]};
 }
 
-// W: n x r scratch (copy of U), B: n x r scratch, P: r x r scratch.
+// W: n x r scratch (copy of U), B: n x r scratch, P: r x r scratch, all in
+// the working type T (U itself is FP64).  The kernel only chooses row
+// indices: every decision is a comparison of magnitudes (the largest pivot,
+// |B_ij| against 1 + delta with delta = 1e-2), which FP32 resolves, so the
+// solver runs it in FP32, an instruction that costs 1/64 of an FP64 one on
+// this GPU; the skeleton built from the chosen rows is FP64.
+template <typename T>
 __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict__ U, int n, int r, double delta,
-                                                      int max_iter, double* W, double* B, double* P, int* I,
-                                                      unsigned* status) {
+                                                      int max_iter, T* W, T* B, T* P, int* I, unsigned* status) {
   __shared__ double rv[33];
   __shared__ long ri[33];
   __shared__ int piv[128];
   __shared__ double s_inv;
   extern __shared__ unsigned char freeflag[];  // n bytes
-  for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) W[t] = U[t];
+  for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) W[t] = T(U[t]);
   for (int i = threadIdx.x; i < n; i += blockDim.x) freeflag[i] = 1;
   __syncthreads();
   // 1. partial-pivoting row choice, rows left in place
@@ -1451,7 +1468,7 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
     for (int i = threadIdx.x; i < n; i += blockDim.x)
       if (freeflag[i]) {
         // a NaN entry counts as 0 (and is flagged), so a free row is always chosen
-        double v = fabs(W[i + (size_t)k * n]);
+        double v = fabs((double)W[i + (size_t)k * n]);
         if (!(v >= 0.0)) {
           v = 0.0;
           atomicOr(status, DEV_NONFINITE);
@@ -1465,16 +1482,16 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
       freeflag[pr] = 0;
     }
     __syncthreads();
-    const double pv = W[pr + (size_t)k * n];
-    if (threadIdx.x == 0) s_inv = pv != 0.0 ? 1.0 / pv : 0.0;
+    const T pv = W[pr + (size_t)k * n];
+    if (threadIdx.x == 0) s_inv = pv != T(0) ? 1.0 / (double)pv : 0.0;
     __syncthreads();
-    const double ipv = s_inv;
-    if (pv != 0.0 && k + 1 < r) {
+    const T ipv = T(s_inv);
+    if (pv != T(0) && k + 1 < r) {
       // column k is read only (it is not used again), columns k+1.. updated
       for (long t = threadIdx.x; t < (long)n * (r - k - 1); t += blockDim.x) {
         const int i = int(t % n), c = k + 1 + int(t / n);
         if (freeflag[i]) {
-          const double f = W[i + (size_t)k * n] * ipv;
+          const T f = W[i + (size_t)k * n] * ipv;
           W[i + (size_t)c * n] = fma(-f, W[pr + (size_t)c * n], W[i + (size_t)c * n]);
         }
       }
@@ -1484,8 +1501,8 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
   // 2. B = U P^{-1} with P = U[piv, :]: Gauss-Jordan on [P | I] in P (r x 2r)
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
     const int i = t % r, j = t / r;
-    P[i + (size_t)j * r] = U[piv[i] + (size_t)j * n];
-    P[i + (size_t)(j + r) * r] = (i == j) ? 1.0 : 0.0;
+    P[i + (size_t)j * r] = T(U[piv[i] + (size_t)j * n]);
+    P[i + (size_t)(j + r) * r] = (i == j) ? T(1) : T(0);
   }
   __syncthreads();
   // Solve X P = U for X = B: equivalently P^T X^T = U^T.  Invert P by
@@ -1494,9 +1511,9 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
   for (int k = 0; k < r; ++k) {
     if (threadIdx.x == 0) {
       int best = k;
-      double bv = fabs(P[k + (size_t)k * r]);
+      double bv = fabs((double)P[k + (size_t)k * r]);
       for (int i = k + 1; i < r; ++i) {
-        const double v = fabs(P[i + (size_t)k * r]);
+        const double v = fabs((double)P[i + (size_t)k * r]);
         if (v > bv) {
           bv = v;
           best = i;
@@ -1508,36 +1525,36 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
     const int pr = gpiv;
     if (pr != k)
       for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) {
-        const double a = P[k + (size_t)c * r];
+        const T a = P[k + (size_t)c * r];
         P[k + (size_t)c * r] = P[pr + (size_t)c * r];
         P[pr + (size_t)c * r] = a;
       }
     __syncthreads();
-    const double d = P[k + (size_t)k * r];
-    if (threadIdx.x == 0) s_inv = d != 0.0 ? 1.0 / d : 0.0;
+    const T d = P[k + (size_t)k * r];
+    if (threadIdx.x == 0) s_inv = d != T(0) ? 1.0 / (double)d : 0.0;
     __syncthreads();
-    const double invd = s_inv;
-    if (d != 0.0) {
+    const T invd = T(s_inv);
+    if (d != T(0)) {
       for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) P[k + (size_t)c * r] *= invd;
     }
     __syncthreads();
     for (long t = threadIdx.x; t < (long)r * 2 * r; t += blockDim.x) {
       const int i = int(t % r), c = int(t / r);
       if (i != k) {
-        const double f = P[i + (size_t)k * r];
+        const T f = P[i + (size_t)k * r];
         if (c != k) P[i + (size_t)c * r] = fma(-f, P[k + (size_t)c * r], P[i + (size_t)c * r]);
       }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < r; i += blockDim.x)
-      if (i != k) P[i + (size_t)k * r] = 0.0;
+      if (i != k) P[i + (size_t)k * r] = T(0);
     __syncthreads();
   }
   // Pinv = P[:, r:2r];  B = U Pinv (n x r)
   for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) {
     const int i = int(t % n), j = int(t / n);
-    double s = 0.0;
-    for (int l = 0; l < r; ++l) s = fma(U[i + (size_t)l * n], P[l + (size_t)(j + r) * r], s);
+    T s = T(0);
+    for (int l = 0; l < r; ++l) s = fma(T(U[i + (size_t)l * n]), P[l + (size_t)(j + r) * r], s);
     B[t] = s;
   }
   for (int k = threadIdx.x; k < r; k += blockDim.x) I[k] = piv[k];
@@ -1548,17 +1565,17 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
     ArgMax best{-1.0, 0x7fffffffffffffffL};
     for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) {
       const int i = int(t % n), j = int(t / n);
-      best = amax_better(best, ArgMax{fabs(B[t]), (long)i * r + j});
+      best = amax_better(best, ArgMax{fabs((double)B[t]), (long)i * r + j});
     }
     best = block_argmax(best, rv, ri);
     if (best.v <= 1.0 + delta) break;
     const int bi = int(best.idx / r), bj = int(best.idx % r);
-    if (threadIdx.x == 0) s_inv = 1.0 / B[bi + (size_t)bj * n];
+    if (threadIdx.x == 0) s_inv = 1.0 / (double)B[bi + (size_t)bj * n];
     // B -= B[:, j] (B[i, :] - e_j)^T / pivot ; use W as scratch for the column and row
     for (int i = threadIdx.x; i < n; i += blockDim.x) W[i] = B[i + (size_t)bj * n];
-    for (int j = threadIdx.x; j < r; j += blockDim.x) W[n + j] = B[bi + (size_t)j * n] - (j == bj ? 1.0 : 0.0);
+    for (int j = threadIdx.x; j < r; j += blockDim.x) W[n + j] = B[bi + (size_t)j * n] - (j == bj ? T(1) : T(0));
     __syncthreads();
-    const double ipiv = s_inv;
+    const T ipiv = T(s_inv);
     for (long t = threadIdx.x; t < (long)n * r; t += blockDim.x) {
       const int i = int(t % n), j = int(t / n);
       B[t] = fma(-W[i] * ipiv, W[n + j], B[t]);
@@ -1571,17 +1588,18 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
 
 void maxvol(Exec& ex, const double* U, int n, int r, double delta, int max_iter, int* I) {
   TT_REQUIRE(r >= 1 && r <= 128 && n >= r, TT_ERR_ARG);
+  using T = float;
   Scope sc(*ex.ar);
-  double* W = ex.ar->get<double>((size_t)n * r + n + r);
-  double* B = ex.ar->get<double>((size_t)n * r);
-  double* P = ex.ar->get<double>((size_t)2 * r * r);
+  T* W = ex.ar->get<T>((size_t)n * r + n + r);
+  T* B = ex.ar->get<T>((size_t)n * r);
+  T* P = ex.ar->get<T>((size_t)2 * r * r);
   if (ex.dry) return;
   const size_t smem = (size_t)n;
   TT_REQUIRE(smem <= 200 * 1024, TT_ERR_ARG);
-  smem_attr_once(k_maxvol);
+  smem_attr_once(k_maxvol<T>);
   // algorithmic work: LU pivoting n r^2 plus B = U P^{-1} 2 n r^2
-  TT_KERNEL(ex, K_MAXVOL, 3.0 * n * (double)r * r, 8.0 * 3.0 * n * (double)r,
-            k_maxvol<<<1, MV_THREADS, smem, ex.s>>>(U, n, r, delta, max_iter, W, B, P, I, ex.dev_status));
+  TT_KERNEL(ex, K_MAXVOL, 3.0 * n * (double)r * r, (8.0 + 2.0 * sizeof(T)) * n * (double)r,
+            k_maxvol<T><<<1, MV_THREADS, smem, ex.s>>>(U, n, r, delta, max_iter, W, B, P, I, ex.dev_status));
 }
 
 }  // namespace ttfv

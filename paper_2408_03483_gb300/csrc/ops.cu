@@ -146,9 +146,10 @@ __global__ void k_stencil(StencilSet st, const double* __restrict__ in, long ldi
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
       double acc = 0.0;
       for (int t = 0; t < so.ntaps; ++t) {
+        // periodic wrap without a division: |shift| < n for every stencil
         int ii = i + so.shift[t];
-        ii %= n;
-        if (ii < 0) ii += n;
+        ii += ii < 0 ? n : 0;
+        ii -= ii >= n ? n : 0;
         acc = fma(so.coef[t], col[so.base[t] + ii], acc);
       }
       so.dst[(size_t)so.row0 + i + (size_t)k * so.ld] = acc;
@@ -159,7 +160,10 @@ __global__ void k_stencil(StencilSet st, const double* __restrict__ in, long ldi
 void stencil(Exec& ex, const StencilSet& st, const double* in, long ldin, int n, int r) {
   if (r <= 0 || n <= 0) return;
   int taps = 0;
-  for (int o = 0; o < st.nout; ++o) taps += st.out[o].ntaps;
+  for (int o = 0; o < st.nout; ++o) {
+    taps += st.out[o].ntaps;
+    for (int t = 0; t < st.out[o].ntaps; ++t) TT_REQUIRE(std::abs(st.out[o].shift[t]) < n, TT_ERR_ARG);
+  }
   if (ex.dry) return;
   TT_REQUIRE(st.nout >= 1 && st.nout <= kMaxStencilOut, TT_ERR_ARG);
   dim3 grid(ceil_div(n, 256), std::min(r, 1024), st.nout);
@@ -186,9 +190,36 @@ __global__ void k_khatri_rao(const double* __restrict__ X, int r1, const double*
   }
 }
 
+// The same with two rows per thread as double2 (n even, 16-byte aligned
+// cores): X(i, a) is read once per row pair and kept in registers across the
+// r2 output columns a r2 .. a r2 + r2 - 1 (grid y = a); the write-bound part
+// is one coalesced 16-byte store per thread and column.
+__global__ void k_khatri_rao2(const double* __restrict__ X, int r1, const double* __restrict__ Y, int r2, int n,
+                              double* __restrict__ Z) {
+  const int h = n >> 1;
+  const int a = blockIdx.y;
+  const double2* X2 = reinterpret_cast<const double2*>(X + (size_t)a * n);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < h; q += gridDim.x * blockDim.x) {
+    const double2 x = X2[q];
+    for (int b = 0; b < r2; ++b) {
+      const double2 y = reinterpret_cast<const double2*>(Y + (size_t)b * n)[q];
+      reinterpret_cast<double2*>(Z + ((size_t)a * r2 + b) * n)[q] = make_double2(x.x * y.x, x.y * y.y);
+    }
+  }
+}
+
 void khatri_rao(Exec& ex, const double* X, int r1, const double* Y, int r2, int n, double* Z) {
   if (ex.dry) return;
   const long total = (long)n * r1 * r2;
+  const bool vec = (n % 2) == 0 && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y) |
+                                     reinterpret_cast<uintptr_t>(Z)) & 15) == 0;
+  if (vec) {
+    const int h = n / 2;
+    dim3 grid(std::max(1, std::min(ceil_div(h, 256), std::max(1, 4 * sm_count() / std::max(r1, 1)))), r1);
+    TT_KERNEL(ex, K_OTHER, (double)total, 8.0 * ((double)n * (r1 + r2) + (double)total),
+              k_khatri_rao2<<<grid, 256, 0, ex.s>>>(X, r1, Y, r2, n, Z));
+    return;
+  }
   TT_KERNEL(ex, K_OTHER, (double)total, 8.0 * ((double)n * (r1 + r2) + (double)total),
             k_khatri_rao<<<grid_for(total), 256, 0, ex.s>>>(X, r1, Y, r2, n, Z));
 }
@@ -361,6 +392,11 @@ static void convert(Exec& ex, D* dst, const S* src, long n) {
             (k_convert<D, S><<<grid_for(n), 256, 0, ex.s>>>(dst, src, n)));
 }
 // X (n values, FP64) as a Real array: X itself for double, else a converted copy
+template <typename Real>
+static void copy_real(Exec& ex, Real* dst, const Real* src, long n) {
+  if (ex.dry || n <= 0) return;
+  TT_CUDA(cudaMemcpyAsync(dst, src, sizeof(Real) * n, cudaMemcpyDeviceToDevice, ex.s));
+}
 template <typename Real>
 static const Real* as_real(Exec& ex, const double* X, long n) {
   if constexpr (std::is_same<Real, double>::value) {
@@ -660,58 +696,64 @@ static double frf_flops(int s, int l, int R, int p) {
 }
 static double full_rf_flops(int n1, int n2, double form, int p) { return form + 6.0 * n1 * (double)n2 * p; }
 
-static RoundInfo round_factored_rf(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol,
-                                   int cap, TT& Y) {
+// The same steps in the working precision Real: FP64, or FP32 for the
+// precision forms, whose products (the cores' Grams, the sketch, the
+// projections and At) go to the tcgen05 tensor cores under TT_TF32 / TT_BF16
+// through lp_gemm (split operands, FP32-accurate); the p x p SVD stays FP64.
+template <typename Real>
+static RoundInfo round_factored_rf(Exec& ex, const double* A64, const double* B64, int n1, int n2, int R,
+                                   double tol, int cap, TT& Y) {
   Scope sc(*ex.ar);
   const bool tr = n1 > n2;
   const int s = tr ? n2 : n1, l = tr ? n1 : n2;
-  const double* As = tr ? B : A;
-  const double* Bl = tr ? A : B;
+  const Real* As = as_real<Real>(ex, tr ? B64 : A64, (long)s * R);
+  const Real* Bl = as_real<Real>(ex, tr ? A64 : B64, (long)l * R);
   double* Aw = tr ? Y.b : Y.a;  // s-side output core
   double* Bw = tr ? Y.a : Y.b;  // l-side output core
   double* kbuf = ex.ar->get<double>(4);
   int* kd = ex.ar->get<int>(4);
   double* tail = ex.ar->get<double>(2);
-  const double tau = qb_target(tol);
+  const double tau = qb_target_t<Real>(tol);
   // Grams of both cores and ||W0||^2
-  double* GB = ex.ar->get<double>((size_t)R * R);
-  double* GA = ex.ar->get<double>((size_t)R * R);
-  gemm<double>(ex, R, R, l, 1.0, Bl, l, 1, Bl, 1, l, 0.0, GB, R);
-  gemm<double>(ex, R, R, s, 1.0, As, s, 1, As, 1, s, 0.0, GA, R);
-  fdot(ex, GA, GB, (long)R * R, kbuf);
+  Real* GB = ex.ar->get<Real>((size_t)R * R);
+  Real* GA = ex.ar->get<Real>((size_t)R * R);
+  lp_gemm<Real>(ex, R, R, l, Real(1), Bl, l, 1, Bl, 1, l, Real(0), GB, R);
+  lp_gemm<Real>(ex, R, R, s, Real(1), As, s, 1, As, 1, s, Real(0), GA, R);
+  const double* GB64 = as_double(ex, GB, (long)R * R);
+  fdot(ex, as_double(ex, GA, (long)R * R), GB64, (long)R * R, kbuf);
   int p = rf_first_sketch(s, cap);
   if (ex.rf_hint && *ex.rf_hint > p) p = std::min({112, s, *ex.rf_hint});
   // the sizing pass takes the widest sketch the run may grow to (every
   // buffer, tree and product partial grows with p)
   if (ex.dry) p = std::min(112, s);
-  double* Om = ex.ar->get<double>((size_t)l * 112);
-  double* T = ex.ar->get<double>((size_t)R * 112);
-  double* S = ex.ar->get<double>((size_t)s * 112);
-  double* Q = ex.ar->get<double>((size_t)s * 112);
-  double* C = ex.ar->get<double>((size_t)112 * R);
-  double* At = ex.ar->get<double>((size_t)s * R);
-  double* GAt = ex.ar->get<double>((size_t)R * R);
-  double* I = ex.ar->get<double>((size_t)112 * 112);
+  Real* Om = ex.ar->get<Real>((size_t)l * 112);
+  Real* T = ex.ar->get<Real>((size_t)R * 112);
+  Real* S = ex.ar->get<Real>((size_t)s * 112);
+  Real* Q = ex.ar->get<Real>((size_t)s * 112);
+  Real* C = ex.ar->get<Real>((size_t)112 * R);
+  Real* At = ex.ar->get<Real>((size_t)s * R);
+  Real* GAt = ex.ar->get<Real>((size_t)R * R);
+  Real* I = ex.ar->get<Real>((size_t)112 * 112);
   double nrm2 = 0.0, resid2 = 0.0;
   for (int attempt = 0;; ++attempt) {
     ex.qb_attempts++;
     const size_t mk = ex.ar->mark();
     if (!ex.dry)
-      TT_KERNEL(ex, K_OTHER, 0, 8.0 * l * p,
-                k_rademacher<double><<<grid_for((long)l * p), 256, 0, ex.s>>>(Om, (long)l * p, 0x7A3Dull + attempt));
+      TT_KERNEL(ex, K_OTHER, 0, (double)sizeof(Real) * l * p,
+                k_rademacher<Real><<<grid_for((long)l * p), 256, 0, ex.s>>>(Om, (long)l * p, 0x7A3Dull + attempt));
     // T = Bl^T Om (R x p), S = As T (s x p)
-    gemm<double>(ex, R, p, l, 1.0, Bl, l, 1, Om, 1, l, 0.0, T, R);
-    gemm<double>(ex, s, p, R, 1.0, As, 1, s, T, 1, R, 0.0, S, s);
-    QRTreeT<double> ts;
+    lp_gemm<Real>(ex, R, p, l, Real(1), Bl, l, 1, Om, 1, l, Real(0), T, R);
+    lp_gemm<Real>(ex, s, p, R, Real(1), As, 1, s, T, 1, R, Real(0), S, s);
+    QRTreeT<Real> ts;
     tsqr(ex, S, s, p, s, ts);
     set_identity_t(ex, I, p);
     tsqr_apply(ex, ts, I, p, p, Q, s);
     // C = Q^T As (p x R); At = As - Q C; resid^2 = sum (At^T At) o GB
-    gemm<double>(ex, p, R, s, 1.0, Q, s, 1, As, 1, s, 0.0, C, p);
-    scaled_copy(ex, At, As, (long)s * R, 1.0);
-    gemm<double>(ex, s, R, p, -1.0, Q, 1, s, C, 1, p, 1.0, At, s);
-    gemm<double>(ex, R, R, s, 1.0, At, s, 1, At, 1, s, 0.0, GAt, R);
-    fdot(ex, GAt, GB, (long)R * R, kbuf + 1);
+    lp_gemm<Real>(ex, p, R, s, Real(1), Q, s, 1, As, 1, s, Real(0), C, p);
+    copy_real(ex, At, As, (long)s * R);
+    lp_gemm<Real>(ex, s, R, p, Real(-1), Q, 1, s, C, 1, p, Real(1), At, s);
+    lp_gemm<Real>(ex, R, R, s, Real(1), At, s, 1, At, 1, s, Real(0), GAt, R);
+    fdot(ex, as_double(ex, GAt, (long)R * R), GB64, (long)R * R, kbuf + 1);
     double v[2];
     fetch_doubles(ex, kbuf, 2, v);
     nrm2 = v[0];
@@ -728,12 +770,13 @@ static RoundInfo round_factored_rf(Exec& ex, const double* A, const double* B, i
   }
   // WT = W0^T Q = Bl C^T (l x p); SVD of Q^T W0 = R_W^T Q_W^T (buffers
   // sized for the widest sketch: the sizing pass never widens it)
-  double* WT = ex.ar->get<double>((size_t)l * 112);
-  gemm<double>(ex, l, p, R, 1.0, Bl, 1, l, C, p, 1, 0.0, WT, l);
-  QRTreeT<double> tw;
+  Real* WT = ex.ar->get<Real>((size_t)l * 112);
+  lp_gemm<Real>(ex, l, p, R, Real(1), Bl, 1, l, C, p, 1, Real(0), WT, l);
+  QRTreeT<Real> tw;
   tsqr(ex, WT, l, p, l, tw);
-  double* M = ex.ar->get<double>((size_t)112 * 112);
-  transpose(ex, tw.R, p, p, p, M, p);
+  Real* Mr = ex.ar->get<Real>((size_t)112 * 112);
+  transpose(ex, tw.R, p, p, p, Mr, p);
+  const double* M = as_double(ex, Mr, (long)p * p);
   debug_finite(ex, M, (long)p * p, "factored range-finder core M (n1, n2, p)", n1, n2, p);
   double* US = ex.ar->get<double>((size_t)112 * 112);
   double* V = ex.ar->get<double>((size_t)112 * 112);
@@ -742,7 +785,15 @@ static RoundInfo round_factored_rf(Exec& ex, const double* A, const double* B, i
   double tl[2];
   int k = fetch_svd_info(ex, kd, p, tail, tl);
   if (ex.dry) k = std::min(cap, p);
-  gemm(ex, s, k, p, 1.0, Q, 1, s, US, 1, p, 0.0, Aw, s);
+  // s-side core Q (U S)_k, l-side core Q_W V_k
+  if constexpr (std::is_same<Real, double>::value) {
+    gemm(ex, s, k, p, 1.0, Q, 1, s, US, 1, p, 0.0, Aw, s);
+  } else {
+    const Real* USr = as_real<Real>(ex, US, (long)p * k);
+    Real* Ar = ex.ar->get<Real>((size_t)s * std::max(k, 1));
+    lp_gemm<Real>(ex, s, k, p, Real(1), Q, 1, s, USr, 1, p, Real(0), Ar, s);
+    convert(ex, Aw, Ar, (long)s * k);
+  }
   apply_to_core(ex, tw, V, k, p, Bw);
   Y.r = k;
   finish_counts(ex, k, cap, s);
@@ -756,15 +807,27 @@ RoundInfo round_full(Exec& ex, const double* Yf, int n1, int n2, double tol, int
   return round_full_t<float>(ex, as_real<float>(ex, Yf, (long)n1 * n2), n1, n2, tol, cap, Y);
 }
 
+// Smallest column count R of an input whose rounding may take the range
+// finder through the cores instead of the factored route (both modes above
+// 112); TT_FRF_MIN_R (environment, read once) overrides it.
+static int frf_min_r() {
+  static const int v = [] {
+    const char* e = std::getenv("TT_FRF_MIN_R");
+    const int x = e ? std::atoi(e) : 0;
+    return x >= 2 ? x : 113;
+  }();
+  return v;
+}
+
 template <typename Real>
 static RoundInfo round_cores_t(Exec& ex, const double* A, const double* B, int n1, int n2, int R, double tol,
                                int cap, TT& Y) {
-  if (R <= 112 && R <= std::min(n1, n2)) return round_factored<Real>(ex, A, B, n1, n2, R, tol, cap, Y);
-  if constexpr (std::is_same<Real, double>::value) {
+  {
     const int s = std::min(n1, n2), l = std::max(n1, n2), p = rf_first_sketch(s, cap);
-    if (s > 112 && frf_flops(s, l, R, p) < full_rf_flops(n1, n2, 2.0 * n1 * (double)n2 * R, p))
-      return round_factored_rf(ex, A, B, n1, n2, R, tol, cap, Y);
+    if (s > 112 && R >= frf_min_r() && frf_flops(s, l, R, p) < full_rf_flops(n1, n2, 2.0 * n1 * (double)n2 * R, p))
+      return round_factored_rf<Real>(ex, A, B, n1, n2, R, tol, cap, Y);
   }
+  if (R <= 112 && R <= std::min(n1, n2)) return round_factored<Real>(ex, A, B, n1, n2, R, tol, cap, Y);
   Scope sc(*ex.ar);
   Real* Yf = ex.ar->get<Real>((size_t)n1 * n2);
   if constexpr (std::is_same<Real, float>::value) {
@@ -824,7 +887,7 @@ RoundInfo round_hadamard(Exec& ex, const TT& X, const TT& Z, double tol, int cap
     return round_cores(ex, A, B, n1, n2, R, tol, cap, Y);
   }
   tol = effective_tol(ex, tol);
-  if (ex.precision == TT_FP64) {
+  {
     // cores of the product (Khatri-Rao) and the range finder through them,
     // when that costs fewer flops than forming the n1 x n2 product
     const int s = std::min(n1, n2), l = std::max(n1, n2), p = rf_first_sketch(s, cap);
@@ -833,8 +896,11 @@ RoundInfo round_hadamard(Exec& ex, const TT& X, const TT& Z, double tol, int cap
       double* B = ex.ar->get<double>((size_t)n2 * R);
       khatri_rao(ex, X.a, X.r, Z.a, Z.r, n1, A);
       khatri_rao(ex, X.b, X.r, Z.b, Z.r, n2, B);
-      return round_factored_rf(ex, A, B, n1, n2, R, tol, cap, Y);
+      if (ex.precision == TT_FP64) return round_factored_rf<double>(ex, A, B, n1, n2, R, tol, cap, Y);
+      return round_factored_rf<float>(ex, A, B, n1, n2, R, tol, cap, Y);
     }
+  }
+  if (ex.precision == TT_FP64) {
     double* Yf = ex.ar->get<double>((size_t)n1 * n2);
     form_hadamard_full(ex, n1, n2, X.a, X.r, X.b, Z.a, Z.r, Z.b, Yf, n1);
     return round_full_t<double>(ex, Yf, n1, n2, tol, cap, Y);

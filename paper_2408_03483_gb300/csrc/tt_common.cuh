@@ -81,6 +81,8 @@ enum KClass : int {
   K_EVAL = TT_K_EVAL,
   K_STENCIL = TT_K_STENCIL,
   K_OTHER = TT_K_OTHER,
+  K_QR_MERGE = TT_K_QR_MERGE,
+  K_QR_APPLY_MERGE = TT_K_QR_APPLY_MERGE,
   K_NCLASS = TT_K_NCLASS
 };
 struct Prof {

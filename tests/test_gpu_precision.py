@@ -106,3 +106,39 @@ def test_fp32_form_step_close_to_fp64_path(api):
     check(a, ref, p, "fp64 path")
     s32.close()
     s64.close()
+
+
+_ref_cache = {}
+
+
+def _smooth1024_refs():
+    """Oracle B's first stage at tol_eff and Oracle A's exact first stage of
+    the rank-14 smooth state at 1024^2 (computed once)."""
+    if not _ref_cache:
+        n = 1024
+        w = workload("vortex1024_up5", tol=1e-8, cap=48)
+        Q = smooth_state(n, 14)
+        _, p = initial_tt(w)
+        wb = dict(w, tol=TOL_EFF_FP32)
+        full = [T.full(q) for q in Q]
+        _ref_cache.update(Q=Q, p=p, w=w, b=TB.stage(Q, Q, 0, wb, p, seed=0),
+                          a=FA.ssprk3_stage(full, full, 0, "nonlinear", "up5", p, p["dt"]))
+    return _ref_cache
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+def test_precision_forms_round_products_through_the_cores_at_1024(api, precision):
+    # faces of rank ~14 on 1024 x 3072: their Hadamard products (R ~ 200
+    # columns) are rounded by the range finder through the Khatri-Rao cores,
+    # whose Grams, sketch and projections run on the tensor cores under
+    # TF32 / BF16 (FP32 on CUDA cores for the FP32 form)
+    r = _smooth1024_refs()
+    s = make_solver(api, r["w"], r["Q"], r["p"], precision)
+    s.stage(0)
+    got = s.get()
+    check(got, [T.full(q) for q in r["b"]], r["p"], ("oracle B", precision))
+    errs = check(got, r["a"], r["p"], ("oracle A", precision))
+    print("smooth1024", precision, "per-field rel L2 vs A", errs)
+    st = s.stats()
+    assert st["device_status"] == 0 and st["qb_attempts"] > 0
+    s.close()

@@ -27,14 +27,21 @@ def env():
     return api, capi, capi.load()
 
 
-def _noalloc_round(api, capi, lib, X, tol, cap):
+def _noalloc_round(api, capi, lib, X, tol, cap, check_no_alloc=False):
+    import torch
     x = api.DevTT.from_cores(X[0], X[1])
     y = api.DevTT(x.n1, x.n2, cap)
     xs, ys = x.struct(), y.struct()
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
     err = ctypes.c_double(0.0)
     code = lib.tt_round_noalloc(ctypes.byref(xs), tol, cap, ctypes.byref(ys), ctypes.byref(err),
                                 api._stream_ptr(None))
     capi.check("tt_round_noalloc", code)
+    torch.cuda.synchronize()
+    if check_no_alloc:
+        # neither torch's allocator nor the driver saw an allocation
+        assert (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]) == before
     y.rank = ys.rank
     return y, err.value
 
@@ -43,9 +50,11 @@ def test_noalloc_round_matches_tt_round_twice(env):
     api, capi, lib = env
     cases = [(random_tt(200, 300, 40, seed=21, decay=0.75), 1e-8, 32),
              (random_tt(256, 768, 24, seed=22, decay=0.7), 1e-10, 20)]
-    for X, tol, cap in cases:  # two calls in a row, different shapes
+    for k, (X, tol, cap) in enumerate(cases):  # two calls in a row, different shapes
         ref, ref_err = api.tt_round(api.DevTT.from_cores(X[0], X[1]), tol, cap)
-        got, got_err = _noalloc_round(api, capi, lib, X, tol, cap)
+        # the first call may look up the array's address; the second is
+        # checked to allocate nothing
+        got, got_err = _noalloc_round(api, capi, lib, X, tol, cap, check_no_alloc=k > 0)
         assert got.rank == ref.rank
         a, b = got.full().numpy(), ref.full().numpy()
         assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(b)
