@@ -167,9 +167,54 @@ def llf(Qm, Qp, direction, eqn, p):
     return tuple(0.5 * (Fm[c] + Fp[c]) - 0.5 * lam * (Qp[c] - Qm[c]) for c in range(3))
 
 
-def rhs(Q, eqn, scheme, p):
+GHOST = 3  # cells beyond each x boundary that one stage's stencils read
+
+
+def rhs_bounded_x(Q, eqn, scheme, p, ghost):
+    """L(Q) on a domain that is not periodic in x (Sec. 5.1, Sec. 5.3: the
+    boundary values come from the exact solution), periodic in y.  ghost =
+    (left, right): per field the cell averages of the GHOST cells beyond x = 0
+    (cells -3..-1) and beyond x = lx (cells nx..nx+2), each GHOST x ny.  The
+    fields are extended by these rows; the x faces are the nx + 1 faces
+    x_{-1/2} .. x_{nx-1/2} between real or ghost cells, the y faces those of
+    the nx real rows (their Step 2 in x reads the ghost rows)."""
+    nx, ny = Q[0].shape
+    dx, dy = p["lx"] / nx, p["ly"] / ny
+    _, w = coeffs.gauss_legendre(nq_of(scheme))
+    gl, gr = ghost
+    E = [np.vstack([gl[c], Q[c], gr[c]]) for c in range(3)]
+    g0 = GHOST
+    out = [np.zeros_like(Q[0]) for _ in range(3)]
+    # x faces: extended face i sits between extended cells i-1 and i; the
+    # faces of the domain are i = GHOST .. GHOST + nx (no stencil there reads
+    # a wrapped row)
+    faces = [face_states(e, "x", scheme, dx, dy) for e in E]
+    Qm = [f[0][:, g0:g0 + nx + 1] for f in faces]
+    Qp = [f[1][:, g0:g0 + nx + 1] for f in faces]
+    Fh = llf(Qm, Qp, "x", eqn, p)
+    for c in range(3):
+        Fq = np.tensordot(w, Fh[c], axes=(0, 0))  # (nx + 1) x ny
+        out[c] -= (Fq[1:] - Fq[:-1]) / dx
+    # y faces of the real rows
+    faces = [face_states(e, "y", scheme, dx, dy) for e in E]
+    Qm = [f[0][:, g0:g0 + nx] for f in faces]
+    Qp = [f[1][:, g0:g0 + nx] for f in faces]
+    Fh = llf(Qm, Qp, "y", eqn, p)
+    for c in range(3):
+        Fq = np.tensordot(w, Fh[c], axes=(0, 0))
+        out[c] -= (np.roll(Fq, -1, axis=1) - Fq) / dy
+    f = p["f"]
+    out[1] += f * Q[2]
+    out[2] -= f * Q[1]
+    return out
+
+
+def rhs(Q, eqn, scheme, p, ghost=None):
     """Semi-discrete operator L(Q) of Eq. SWE-system-cell-avg:
-    -(F_{i+1/2}-F_{i-1/2})/dx - (G_{j+1/2}-G_{j-1/2})/dy + S."""
+    -(F_{i+1/2}-F_{i-1/2})/dx - (G_{j+1/2}-G_{j-1/2})/dy + S (doubly periodic;
+    with `ghost`, bounded in x: rhs_bounded_x)."""
+    if ghost is not None:
+        return rhs_bounded_x(Q, eqn, scheme, p, ghost)
     nx, ny = Q[0].shape
     dx, dy = p["lx"] / nx, p["ly"] / ny
     _, w = coeffs.gauss_legendre(nq_of(scheme))
@@ -190,24 +235,27 @@ def rhs(Q, eqn, scheme, p):
     return out
 
 
-def euler(Q, eqn, scheme, p, dt, src=None):
+def euler(Q, eqn, scheme, p, dt, src=None, ghost=None):
     """Q + dt (L(Q) + src), src the cell averages of an external source at the
-    stage's time (or None)."""
-    L = rhs(Q, eqn, scheme, p)
+    stage's time (or None); ghost the x-boundary cells at that time (or None:
+    periodic)."""
+    L = rhs(Q, eqn, scheme, p, ghost)
     if src is None:
         return [Q[c] + dt * L[c] for c in range(3)]
     return [Q[c] + dt * (L[c] + src[c]) for c in range(3)]
 
 
-def ssprk3_step(Q, eqn, scheme, p, dt, source=None, t=0.0):
+def ssprk3_step(Q, eqn, scheme, p, dt, source=None, t=0.0, bc=None):
     """One SSP-RK3 step (Sec. 4.4, Eq. tt-ssprk3 without rounding) from time t;
     source(time) -> cell averages of an external source (a manufactured
-    solution's forcing), evaluated at the stages' times t, t + dt, t + dt/2."""
+    solution's forcing) and bc(time) -> the x-boundary ghost cells (an exact
+    solution's), each evaluated at the stages' times t, t + dt, t + dt/2."""
     S = (lambda s: None) if source is None else source  # noqa: E731
-    u1 = euler(Q, eqn, scheme, p, dt, S(t))
-    f1 = euler(u1, eqn, scheme, p, dt, S(t + dt))
+    B = (lambda s: None) if bc is None else bc  # noqa: E731
+    u1 = euler(Q, eqn, scheme, p, dt, S(t), B(t))
+    f1 = euler(u1, eqn, scheme, p, dt, S(t + dt), B(t + dt))
     u2 = [0.75 * Q[c] + 0.25 * f1[c] for c in range(3)]
-    f2 = euler(u2, eqn, scheme, p, dt, S(t + 0.5 * dt))
+    f2 = euler(u2, eqn, scheme, p, dt, S(t + 0.5 * dt), B(t + 0.5 * dt))
     return [Q[c] / 3.0 + 2.0 / 3.0 * f2[c] for c in range(3)]
 
 

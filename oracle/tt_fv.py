@@ -74,6 +74,68 @@ def recon_linear(X, direction, scheme):
     return (As, Bm), (As.copy(), Bp)
 
 
+GHOST = FA.GHOST
+
+
+def _window_stencil(C, stencil, first, count):
+    """sum_s c_s C[i+s, :] for i = first .. first+count-1 (no wrap: the rows
+    read must exist)."""
+    out = np.zeros((count, C.shape[1]))
+    for s, c in stencil.items():
+        out += float(c) * C[first + s:first + s + count]
+    return out
+
+
+def extend_x(X, ghost):
+    """The TT of X with GHOST rows of an exact solution above and below in x:
+    ghost = (Al, Ar, Be) with the exact solution's first-core rows of the
+    cells -3..-1 (Al) and nx..nx+2 (Ar) and its second core Be; the cores are
+    concatenated (rank r + r_E), X's columns zero on the ghost rows and the
+    exact solution's zero on the real rows."""
+    A, B = X
+    Al, Ar, Be = ghost
+    r, re = A.shape[1], Al.shape[1]
+    top = np.hstack([np.zeros((GHOST, r)), Al])
+    mid = np.hstack([A, np.zeros((A.shape[0], re))])
+    bot = np.hstack([np.zeros((GHOST, r)), Ar])
+    return (np.vstack([top, mid, bot]), np.hstack([B, Be]))
+
+
+def recon_linear_bounded(X, ghost, direction, scheme):
+    """Face TTs (Qm, Qp) of X for Upwind3/Upwind5 on a domain bounded in x
+    with exact-solution ghost cells (periodic in y): x faces are the nx + 1
+    faces x_{-1/2} .. x_{nx-1/2} (Qm: the right-face value of the cell
+    below, Qp: the left-face value of the cell above, ghost or real); y faces
+    are those of the nx real rows, their Step 2 in x reading the ghost rows."""
+    order = 3 if scheme == "up3" else 5
+    right = coeffs.step1_linear(order, "-")
+    left = coeffs.step1_linear(order, "+")
+    Ae, Be = extend_x(X, ghost)
+    nx = X[0].shape[0]
+    if direction == "x":
+        Am = _window_stencil(Ae, right, GHOST - 1, nx + 1)  # cells -1 .. nx-1
+        Ap = _window_stencil(Ae, left, GHOST, nx + 1)       # cells 0 .. nx
+        Bs = _step2_core(Be, scheme)
+        return (Am, Bs), (Ap, Bs.copy())
+    Bm = np.roll(T.core_stencil(Be, right), 1, axis=0)
+    Bp = T.core_stencil(Be, left)
+    nq = FA.nq_of(scheme)
+    k = nq - 1
+    Cs = coeffs.step2_C(nq)
+    gam = coeffs.step2_gamma(nq)
+    blocks = []
+    for m in range(nq):
+        cand = [sum(Cs[m][r, l] * Ae[GHOST - r + l:GHOST - r + l + nx] for l in range(k + 1))
+                for r in range(k + 1)]
+        if gam[m] is not None:
+            blocks.append(sum(gam[m][r] * cand[r] for r in range(k + 1)))
+        else:
+            gp, gm, sp, sm = coeffs.step2_split()
+            blocks.append(sp * sum(gp[r] * cand[r] for r in range(3)) - sm * sum(gm[r] * cand[r] for r in range(3)))
+    As = np.vstack(blocks)
+    return (As, Bm), (As.copy(), Bp)
+
+
 # ---------------------------------------------------------------------------
 # WENO5 reconstruction by cross (Algorithms 2 and 3)
 # ---------------------------------------------------------------------------
@@ -267,28 +329,56 @@ def flux_cross(Qm, Qp, direction, p, w, seed=0):
     return [(A[c * n1:(c + 1) * n1].copy(), B) for c in range(3)]
 
 
-def quad_and_difference(Fh, direction, nq, n, d):
+def quad_and_difference(Fh, direction, nq, n, d, bounded=False):
     """Face average sum_m w_m over the stacked index, then (T - 1)/d on the
-    core normal to the face: returns the TT of (F_{i+1/2} - F_{i-1/2})/d."""
+    core normal to the face: returns the TT of (F_{i+1/2} - F_{i-1/2})/d
+    (bounded: the x faces are nx + 1 rows and the difference does not wrap)."""
     _, wts = coeffs.gauss_legendre(nq)
     A, B = Fh
     if direction == "x":
         Bq = sum(wts[m] * B[m * n:(m + 1) * n] for m in range(nq))
-        Ad = (np.roll(A, -1, axis=0) - A) / d
+        Ad = (A[1:] - A[:-1]) / d if bounded else (np.roll(A, -1, axis=0) - A) / d
         return (Ad, Bq)
     Aq = sum(wts[m] * A[m * n:(m + 1) * n] for m in range(nq))
     Bd = (np.roll(B, -1, axis=0) - B) / d
     return (Aq, Bd)
 
 
-def rhs_terms(Q, w, p, stats=None, seed=0):
-    """TT terms of L(Q) for each component: list of lists of (coef, TT)."""
+def ghost_tt(waves, field, n1, n2, t, lx, ly):
+    """(Al, Ar, Be) of the exact solution `waves` for field at time t: its
+    first-core rows of the GHOST cells beyond each x boundary and its second
+    core (waves_tt on those rows)."""
+    rows = np.concatenate([np.arange(-GHOST, 0), np.arange(n1, n1 + GHOST)])
+    E = waves_tt(waves, field, n1, n2, t, lx, ly, rows=rows)
+    if E is None:
+        return (np.zeros((GHOST, 1)), np.zeros((GHOST, 1)), np.zeros((n2, 1)))
+    return (E[0][:GHOST], E[0][GHOST:], E[1])
+
+
+def rhs_terms(Q, w, p, stats=None, seed=0, t=0.0):
+    """TT terms of L(Q) for each component: list of lists of (coef, TT).
+    With w["bc_x"] == "exact" (linear SWE, Upwind3/Upwind5) the domain is
+    bounded in x and the ghost cells hold the exact solution w["boundary"]
+    (plane waves) at time t."""
     n1, n2 = Q[0][0].shape[0], Q[0][1].shape[0]
     dx, dy = p["lx"] / n1, p["ly"] / n2
     scheme, eqn = w["scheme"], w["eqn"]
     nq = FA.nq_of(scheme)
+    bounded = w.get("bc_x", "periodic") == "exact"
     terms = [[], [], []]
+    if bounded:
+        if eqn != "linear" or scheme == "weno5":
+            raise ValueError("the bounded-x form is built for the linear SWE with Upwind3/Upwind5")
+        gh = [ghost_tt(w["boundary"], c, n1, n2, t, p["lx"], p["ly"]) for c in range(3)]
     for di, (direction, n, d) in enumerate((("x", n2, dx), ("y", n1, dy))):
+        if bounded:
+            faces = [recon_linear_bounded(q, gh[c], direction, scheme) for c, q in enumerate(Q)]
+            Qm = [f[0] for f in faces]
+            Qp = [f[1] for f in faces]
+            Fh = flux_linear(Qm, Qp, direction, p)
+            for c in range(3):
+                terms[c].append((-1.0, quad_and_difference(Fh[c], direction, nq, n, d, bounded=True)))
+            continue
         if scheme == "weno5":
             faces = [recon_weno(q, direction, w, dx, dy, seed_base=seed + 64 * di + 8 * c,
                                 stats=stats) for c, q in enumerate(Q)]
@@ -317,13 +407,14 @@ def _tol_u(w, c):
     return w["tol_u"][c] if "tol_u" in w else w["tol"]
 
 
-def waves_tt(waves, field, n1, n2, t, lx, ly):
+def waves_tt(waves, field, n1, n2, t, lx, ly, rows=None):
     """Cell averages of sum amp cos(kx x + ky y - omega t + phase) over the
-    waves of `field` as TT cores: a plane wave averaged over a cell is its
-    centre value times sinc(kx dx/2) sinc(ky dy/2), and cos(a + b) =
-    cos a cos b - sin a sin b is rank 2."""
+    waves of `field` as TT cores (first core on the x cells `rows`, by
+    default 0..n1-1): a plane wave averaged over a cell is its centre value
+    times sinc(kx dx/2) sinc(ky dy/2), and cos(a + b) = cos a cos b -
+    sin a sin b is rank 2."""
     dx, dy = lx / n1, ly / n2
-    xc = (np.arange(n1) + 0.5) * dx
+    xc = ((np.arange(n1) if rows is None else np.asarray(rows)) + 0.5) * dx
     yc = (np.arange(n2) + 0.5) * dy
     A, B = [], []
     for c, amp, kx, ky, om, ph in waves:
@@ -344,7 +435,7 @@ def forward_euler(Q, w, p, dt, stats=None, seed=0, t=0.0):
     """F(u) = round(u + dt (L(u) + S_m(t)), eps^u) per component (Eq.
     tt-forward-euler), S_m the external source w["forcing"] (plane waves) at
     time t when present."""
-    terms = rhs_terms(Q, w, p, stats, seed)
+    terms = rhs_terms(Q, w, p, stats, seed, t)
     n1, n2 = Q[0][0].shape[0], Q[0][1].shape[0]
     out = []
     for c in range(3):

@@ -9,9 +9,7 @@ differentiated symbolically (sympy) from the continuous equations and
 rewritten as a sum of plane waves amp cos(m kx x + m ky y - m omega t + phase)
 (every term is a product of sines and cosines of theta, so m <= 3).
 
-A plane wave's cell average over a dx x dy cell centred at (xc, yc) is its
-value there times sinc(kx dx / 2) sinc(ky dy / 2), and it is a rank-2 TT:
-cos(a + b) = cos a cos b - sin a sin b.
+Cell averages and TT cores of plane waves: synth/waves.py.
 
 The paper's amplitudes (eta_hat = 1e-2 m on H = 1000 m, u_hat = 1e-2 m/s on
 c = 100 m/s) are 1e-5 H and 1e-4 c, so its case is nearly linear; the
@@ -21,7 +19,7 @@ weight.
 import math
 from functools import lru_cache
 
-import numpy as np
+from .waves import waves_cellavg, waves_tt  # noqa: F401  (re-exported)
 
 MMS_DEFAULT = dict(g=9.81, H=1.0, f=1.0, eta_hat=0.1, u_hat=0.1, kx=2 * math.pi, ky=2 * math.pi)
 
@@ -85,38 +83,3 @@ def exact_waves(**prm):
             (1, P["H"] * P["u_hat"], kx, ky, om, 0.0),
             (1, 0.5 * P["eta_hat"] * P["u_hat"], 2 * kx, 2 * ky, 2 * om, -math.pi / 2)]
 
-
-def _sinc(z):
-    return 1.0 if z == 0.0 else math.sin(z) / z
-
-
-def waves_cellavg(waves, field, n, t, length=1.0):
-    """Exact cell averages (n x n) of the waves of `field` at time t."""
-    dx = length / n
-    xc = (np.arange(n) + 0.5) * dx
-    out = np.zeros((n, n))
-    for c, amp, kx, ky, om, ph in waves:
-        if c != field:
-            continue
-        s = _sinc(kx * dx / 2) * _sinc(ky * dx / 2)
-        out += amp * s * np.cos(kx * xc[:, None] + ky * xc[None, :] - om * t + ph)
-    return out
-
-
-def waves_tt(waves, field, n, t, length=1.0):
-    """The same cell averages as TT cores (A, B), rank 2 per wave (a zero
-    rank-1 TT when the field has no wave)."""
-    dx = length / n
-    xc = (np.arange(n) + 0.5) * dx
-    A, B = [], []
-    for c, amp, kx, ky, om, ph in waves:
-        if c != field:
-            continue
-        sx, sy = _sinc(kx * dx / 2), _sinc(ky * dx / 2)
-        a = kx * xc
-        b = ky * xc - om * t + ph
-        A += [sx * np.cos(a), -sx * np.sin(a)]
-        B += [amp * sy * np.cos(b), amp * sy * np.sin(b)]
-    if not A:
-        return np.zeros((n, 1)), np.zeros((n, 1))
-    return np.stack(A, axis=1), np.stack(B, axis=1)
