@@ -75,6 +75,7 @@ enum {
                             components stacked along the first mode (the LF-cross of Sec. 4.2) */
 };
 enum { TT_FLUX_PRODUCTS = 0, TT_FLUX_CROSS = 1 }; /* nonlinear LLF flux in TT (Sec. 4.2) */
+enum { TT_BC_PERIODIC = 0, TT_BC_EXACT = 1 };     /* x boundary (Sec. 5.1, 5.3) */
 
 typedef struct {
   int32_t eqn;        /* TT_LINEAR | TT_NONLINEAR */
@@ -106,6 +107,11 @@ typedef struct {
                          flux vector (TT_FN_LLF_FLUX), the LF-cross the paper compares against */
   int32_t forcing_waves; /* the most source waves of one field tt_fv_set_forcing may set, 0..TT_MAX_WAVES
                             (0: no source); the workspace is sized for it */
+  int32_t bc_x;       /* TT_BC_PERIODIC (0), or TT_BC_EXACT: the domain is bounded in x and the three
+                         cells beyond each x boundary hold the exact solution set by tt_fv_set_boundary
+                         (the linear SWE with TT_UP3 / TT_UP5 only); y stays periodic */
+  int32_t boundary_waves; /* under TT_BC_EXACT: the most plane waves of one field of that exact
+                             solution, 1..TT_MAX_WAVES; the workspace is sized for it */
 } tt_fv_params;
 
 /* One plane wave of an external source: amp cos(kx x + ky y - omega t + phase)
@@ -206,6 +212,20 @@ tt_status tt_fv_set(tt_fv_ctx* ctx, const tt2 q[3]);
  * u + dt L(u) before the forward-Euler round.  t0 is the time of the current
  * state; each step advances it by dt.  nwaves = 0 removes the source. */
 tt_status tt_fv_set_forcing(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwaves, double t0);
+
+/* Sets the exact solution that supplies the x-boundary values of a solver with
+ * bc_x = TT_BC_EXACT (the exact-solution boundary of Sec. 5.1 and Sec. 5.3):
+ * `nwaves` plane waves (host array, copied; at most params.boundary_waves per
+ * field, else TT_ERR_ARG).  At each stage's time (t, t + dt, t + dt/2) the
+ * three cells beyond x = 0 and beyond x = lx take the waves' exact cell
+ * averages: every field's TT is extended by those ghost rows (its first core
+ * by rank-2-per-wave columns that are zero on the real rows, its second core
+ * by the waves' y factors), Step 1 and Step 2 in x run without wrapping, the
+ * x faces are the nx + 1 faces x_{-1/2} .. x_{nx-1/2}, and the flux difference
+ * in x does not wrap.  t0 is the time of the current state (shared with the
+ * source of tt_fv_set_forcing).  A solver with TT_BC_EXACT refuses to step
+ * (TT_ERR_ARG) until its boundary is set. */
+tt_status tt_fv_set_boundary(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwaves, double t0);
 
 tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* out);
 void tt_fv_destroy(tt_fv_ctx* ctx);

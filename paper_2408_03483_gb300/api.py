@@ -171,12 +171,14 @@ class Solver:
 
     def __init__(self, q0, eqn, scheme, n, dt, tol, rank_cap, g=9.81, H=1.0, f=0.0, lx=1.0, ly=1.0,
                  kick=4, max_sweeps=10, max_iter=50, seed=0, precision="fp64", pivots="maxvol", stream=None,
-                 eps_rule="fixed", c_eps=1.0, flux="products", forcing_waves=0):
+                 eps_rule="fixed", c_eps=1.0, flux="products", forcing_waves=0, bc_x="periodic",
+                 boundary_waves=0):
         _require_cuda()
         self.lib = C.load()
         self.p = C.tt_fv_params(C.EQNS[eqn], C.SCHEMES[scheme], n, n, lx, ly, g, H, f, dt, tol, rank_cap,
                                 C.PRECISIONS[precision], C.PIVOTS[pivots], kick, max_sweeps, max_iter, seed,
-                                C.EPS_RULES[eps_rule], c_eps, C.FLUXES[flux], forcing_waves)
+                                C.EPS_RULES[eps_rule], c_eps, C.FLUXES[flux], forcing_waves, C.BCS[bc_x],
+                                boundary_waves)
         nbytes = self.lib.tt_fv_workspace_size(ctypes.byref(self.p))
         if nbytes == 0:
             raise C.TTError("tt_fv_workspace_size", C.TT_ERR_ARG)
@@ -211,6 +213,12 @@ class Solver:
         """waves: (field, amp, kx, ky, omega, phase) plane waves of the source."""
         arr = (C.tt_wave * max(1, len(waves)))(*[C.tt_wave(int(f), *map(float, rest)) for f, *rest in waves])
         C.check("tt_fv_set_forcing", self.lib.tt_fv_set_forcing(self.h, arr, len(waves), float(t0)))
+
+    def set_boundary(self, waves, t0=0.0):
+        """waves: (field, amp, kx, ky, omega, phase) plane waves of the exact
+        solution whose cell averages fill the x-boundary ghost cells."""
+        arr = (C.tt_wave * max(1, len(waves)))(*[C.tt_wave(int(f), *map(float, rest)) for f, *rest in waves])
+        C.check("tt_fv_set_boundary", self.lib.tt_fv_set_boundary(self.h, arr, len(waves), float(t0)))
 
     def stats(self):
         st = C.tt_fv_stats()

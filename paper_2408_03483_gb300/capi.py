@@ -27,6 +27,7 @@ PRECISIONS = {"fp64": TT_FP64, "fp32": TT_FP32, "tf32": TT_TF32, "bf16": TT_BF16
 PIVOTS = {"maxvol": 0, "learned": 1}
 EPS_RULES = {"fixed": 0, "adaptive": 1}
 FLUXES = {"products": 0, "cross": 1}
+BCS = {"periodic": 0, "exact": 1}
 
 
 class TTError(RuntimeError):
@@ -48,7 +49,7 @@ class tt_fv_params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("pivots", ctypes.c_int32), ("kick", ctypes.c_int32),
                 ("max_sweeps", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("seed", ctypes.c_uint32),
                 ("eps_rule", ctypes.c_int32), ("c_eps", ctypes.c_double), ("flux", ctypes.c_int32),
-                ("forcing_waves", ctypes.c_int32)]
+                ("forcing_waves", ctypes.c_int32), ("bc_x", ctypes.c_int32), ("boundary_waves", ctypes.c_int32)]
 
 
 class tt_wave(ctypes.Structure):
@@ -98,6 +99,7 @@ SIGNATURES = {
     "tt_fv_get": (ctypes.c_int, [_vp, _P(tt2)]),
     "tt_fv_set": (ctypes.c_int, [_vp, _P(tt2)]),
     "tt_fv_set_forcing": (ctypes.c_int, [_vp, _P(tt_wave), _i32, _d]),
+    "tt_fv_set_boundary": (ctypes.c_int, [_vp, _P(tt_wave), _i32, _d]),
     "tt_fv_stats_get": (ctypes.c_int, [_vp, _P(tt_fv_stats)]),
     "tt_fv_destroy": (None, [_vp]),
     "tt_fv_profile": (ctypes.c_int, [_vp, _i32]),

@@ -173,6 +173,19 @@ int reciprocal(Exec& ex, const TT& x, double tol, int cap, int max_iter, TT& y, 
 }
 
 // ============================================================== linear recon
+// Non-periodic window: tap t reads input row i + base0 + t (no wrap; the
+// caller guarantees the rows exist)
+static void add_taps_window(StencilOut& o, const double* coef, int ntap, int base0) {
+  for (int t = 0; t < ntap; ++t) {
+    if (coef[t] == 0.0) continue;
+    TT_REQUIRE(o.ntaps < kMaxTaps, TT_ERR_ARG);
+    o.shift[o.ntaps] = 0;
+    o.base[o.ntaps] = base0 + t;
+    o.coef[o.ntaps] = coef[t];
+    o.ntaps++;
+  }
+}
+
 static void add_taps(StencilOut& o, const double* coef, int ntap, int shift0, int base) {
   for (int t = 0; t < ntap; ++t) {
     if (coef[t] == 0.0) continue;
@@ -263,6 +276,9 @@ struct Solver {
   // current state and the time the current stage evaluates L at
   std::vector<tt_wave> waves;
   double time = 0.0, stage_time = 0.0;
+  // exact solution on the x-boundary ghost cells (bc_x = TT_BC_EXACT)
+  std::vector<tt_wave> bwaves;
+  bool boundary_set = false;
   ~Solver();
 };
 
@@ -386,6 +402,152 @@ static void faces_linear(Solver& S, Exec& ex, const TT& q, int d, TT& qm, TT& qp
     qm.a = ex.ar->get<double>((size_t)f1 * q.r);
   }
   recon_linear(ex, q, d, S.p.recon, qm, qp);
+}
+
+// ---------------------------------------------------------------- bounded x
+constexpr int kGhost = 3;  // cells beyond each x boundary that one stage's stencils read
+
+// The TT of a field with kGhost ghost rows beyond each x boundary holding the
+// exact solution's cell averages at time t (Sec. 5.1 / 5.3 boundary values):
+// first core Ae ((nx + 2 kGhost) x (r + 2 n)): the field's columns on the real
+// rows and zero on the ghost rows, then the waves' rank-2 columns on the ghost
+// rows and zero on the real rows; second core Be (ny x (r + 2 n)): the
+// field's second core, then the waves' y factors (as in k_wave_cores).
+__global__ void k_extend_x(const double* __restrict__ A, const double* __restrict__ B, int nx, int ny, int r,
+                           WaveSet w, double t, double dx, double dy, double* __restrict__ Ae,
+                           double* __restrict__ Be) {
+  const int ne = nx + 2 * kGhost, R = r + 2 * w.n;
+  const long na = (long)ne * R, total = na + (long)ny * R;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
+    if (q < na) {
+      const int i = int(q % ne), col = int(q / ne);
+      const bool ghost = i < kGhost || i >= kGhost + nx;
+      double v = 0.0;
+      if (col < r) {
+        if (!ghost) v = A[(i - kGhost) + (size_t)col * nx];
+      } else if (ghost) {
+        const int wc = col - r, wv = wc >> 1;
+        const double a = w.kx[wv] * (i - kGhost + 0.5) * dx, sx = sinc_dev(0.5 * w.kx[wv] * dx);
+        v = (wc & 1) ? -sx * sin(a) : sx * cos(a);
+      }
+      Ae[q] = v;
+    } else {
+      const long rr = q - na;
+      const int j = int(rr % ny), col = int(rr / ny);
+      double v;
+      if (col < r) {
+        v = B[j + (size_t)col * ny];
+      } else {
+        const int wc = col - r, wv = wc >> 1;
+        const double b = w.ky[wv] * (j + 0.5) * dy - w.om[wv] * t + w.ph[wv];
+        const double sy = w.amp[wv] * sinc_dev(0.5 * w.ky[wv] * dy);
+        v = (wc & 1) ? sy * sin(b) : sy * cos(b);
+      }
+      Be[rr] = v;
+    }
+  }
+}
+
+// Field c's TT extended by the boundary ghost rows at the current stage's time
+static TT extend_x(Solver& S, Exec& ex, const TT& q, int c) {
+  int nw = 0;
+  WaveSet ws{};
+  if (ex.dry) {
+    nw = S.p.boundary_waves;
+  } else {
+    for (const tt_wave& w : S.bwaves)
+      if (w.field == c) {
+        ws.amp[ws.n] = w.amp;
+        ws.kx[ws.n] = w.kx;
+        ws.ky[ws.n] = w.ky;
+        ws.om[ws.n] = w.omega;
+        ws.ph[ws.n] = w.phase;
+        ws.n++;
+      }
+    nw = ws.n;
+  }
+  const int nx = S.p.nx, ny = S.p.ny, ne = nx + 2 * kGhost, R = q.r + 2 * nw;
+  TT e = alloc_tt(*ex.ar, ne, ny, R);
+  e.r = R;
+  if (ex.dry) return e;
+  const long total = (long)(ne + ny) * R;
+  const int blocks = std::max(1, std::min(ceil_div(total, 256), 1184));
+  TT_KERNEL(ex, K_OTHER, 20.0 * (ne + ny) * 2.0 * nw, 8.0 * (double)total + 8.0 * (nx + ny) * (double)q.r,
+            k_extend_x<<<blocks, 256, 0, ex.s>>>(q.a, q.b, nx, ny, q.r, ws, S.stage_time, S.p.lx / nx,
+                                                 S.p.ly / ny, e.a, e.b));
+  return e;
+}
+
+// Linear faces (Upwind3 / Upwind5) of a field from its extended TT e on the
+// domain bounded in x: x faces are the nx + 1 faces x_{-1/2} .. x_{nx-1/2}
+// (Qm: the right-face value of the cell below, ghost or real, Qp: the
+// left-face value of the cell above), y faces those of the nx real rows
+// with Step 2 in x reading the ghost rows; y stays periodic.
+static void faces_linear_bounded(Solver& S, Exec& ex, const TT& e, int d, TT& qm, TT& qp) {
+  const ReconCoeffs& Rc = recon_coeffs();
+  const int nx = S.p.nx, ny = S.p.ny, nq = S.nq, ne = e.n1, R = e.r;
+  const double* right = S.p.recon == TT_UP3 ? Rc.up3_minus : Rc.up5_minus;
+  const double* left = S.p.recon == TT_UP3 ? Rc.up3_plus : Rc.up5_plus;
+  const int f1 = d == 0 ? nx + 1 : nq * nx, f2 = d == 0 ? nq * ny : ny;
+  qm.n1 = qp.n1 = f1;
+  qm.n2 = qp.n2 = f2;
+  qm.cap = qp.cap = R;
+  if (d == 0) {
+    qm.a = ex.ar->get<double>((size_t)f1 * R);
+    qp.a = ex.ar->get<double>((size_t)f1 * R);
+    qm.b = ex.ar->get<double>((size_t)f2 * R);
+    qp.b = qm.b;
+    // Step 1 in x without wrap: face k reads ghost-extended rows k .. k + 4
+    // (Qm, cell k - 1) and k + 1 .. k + 5 (Qp, cell k)
+    StencilSet s1;
+    s1.nout = 2;
+    s1.out[0].dst = qm.a;
+    s1.out[0].ld = f1;
+    add_taps_window(s1.out[0], right, 5, 0);
+    s1.out[1].dst = qp.a;
+    s1.out[1].ld = f1;
+    add_taps_window(s1.out[1], left, 5, 1);
+    stencil(ex, s1, e.a, ne, f1, R);
+    StencilSet s2;  // Step 2 in y (periodic)
+    s2.nout = nq;
+    for (int m = 0; m < nq; ++m) {
+      s2.out[m].dst = qm.b;
+      s2.out[m].ld = (long)nq * ny;
+      s2.out[m].row0 = m * ny;
+      if (nq == 2)
+        add_taps(s2.out[m], Rc.lin2[m], 3, -1, 0);
+      else
+        add_taps(s2.out[m], Rc.lin3[m], 5, -2, 0);
+    }
+    stencil(ex, s2, e.b, ny, ny, R);
+  } else {
+    qm.b = ex.ar->get<double>((size_t)ny * R);
+    qp.b = ex.ar->get<double>((size_t)ny * R);
+    qm.a = ex.ar->get<double>((size_t)f1 * R);
+    qp.a = qm.a;
+    StencilSet s1;  // Step 1 in y (periodic)
+    s1.nout = 2;
+    s1.out[0].dst = qm.b;
+    s1.out[0].ld = ny;
+    add_taps(s1.out[0], right, 5, -2 - 1, 0);
+    s1.out[1].dst = qp.b;
+    s1.out[1].ld = ny;
+    add_taps(s1.out[1], left, 5, -2, 0);
+    stencil(ex, s1, e.b, ny, ny, R);
+    StencilSet s2;  // Step 2 in x at the Gauss points, real rows, no wrap
+    s2.nout = nq;
+    for (int m = 0; m < nq; ++m) {
+      s2.out[m].dst = qm.a;
+      s2.out[m].ld = (long)nq * nx;
+      s2.out[m].row0 = m * nx;
+      if (nq == 2)
+        add_taps_window(s2.out[m], Rc.lin2[m], 3, kGhost - 1);
+      else
+        add_taps_window(s2.out[m], Rc.lin3[m], 5, kGhost - 2);
+    }
+    stencil(ex, s2, e.a, ne, nx, R);
+  }
+  qm.r = qp.r = R;
 }
 
 // One side of the WENO5 faces of one field (Algorithms 2 and 3): Step 1 by
@@ -564,6 +726,13 @@ static void quad_and_difference(Solver& S, Exec& ex, const TT& Fh, int d, TT& ou
   sd.out[0].dst = d == 0 ? out.a : out.b;
   sd.out[0].ld = nn;
   const double cd[2] = {-1.0 / h, 1.0 / h};
+  if (d == 0 && S.p.bc_x == TT_BC_EXACT) {
+    // nx + 1 faces, difference without wrap
+    TT_REQUIRE(Fh.n1 == nn + 1, TT_ERR_ARG);
+    add_taps_window(sd.out[0], cd, 2, 0);
+    stencil(ex, sd, Fh.a, nn + 1, nn, Fh.r);
+    return;
+  }
   add_taps(sd.out[0], cd, 2, 0, 0);
   stencil(ex, sd, d == 0 ? Fh.a : Fh.b, nn, nn, Fh.r);
 }
@@ -599,13 +768,19 @@ static void forward_euler_linear(Solver& S, Exec& ex, const TT Q[3], unsigned se
   for (int c = 0; c < 3; ++c) terms[c].push_back(Term{1.0, Q[c]});
   TT qm[2][3], qp[2][3];
   int f1[2], f2[2];
+  const bool bounded = p.bc_x == TT_BC_EXACT;
   for (int d = 0; d < 2; ++d) {
-    f1[d] = d == 0 ? p.nx : S.nq * p.nx;
+    f1[d] = d == 0 ? p.nx + (bounded ? 1 : 0) : S.nq * p.nx;
     f2[d] = d == 0 ? S.nq * p.ny : p.ny;
   }
   {
     SectionTimer st0(S.section_ms[0]);
-    if (p.recon == TT_WENO5) {
+    if (bounded) {
+      for (int c = 0; c < 3; ++c) {
+        const TT e = extend_x(S, ex, Q[c], c);
+        for (int d = 0; d < 2; ++d) faces_linear_bounded(S, ex, e, d, qm[d][c], qp[d][c]);
+      }
+    } else if (p.recon == TT_WENO5) {
       for (int d = 0; d < 2; ++d)
         for (int c = 0; c < 3; ++c) {
           qm[d][c] = alloc_tt(*ex.ar, f1[d], f2[d], cap);
@@ -896,6 +1071,7 @@ static void step_tolerances(Solver& S, Exec& ex) {
 
 static void run_stage(Solver& S, Exec& ex, int stage) {
   TT_REQUIRE(stage == S.next_stage, TT_ERR_ARG);
+  TT_REQUIRE(S.p.bc_x != TT_BC_EXACT || S.boundary_set || ex.dry, TT_ERR_ARG);
   if (stage == 0) {
     step_tolerances(S, ex);
     // the lambda guesses and sketch widths carried between stages are
@@ -957,6 +1133,10 @@ static bool valid_params(const tt_fv_params* p) {
   if (p->eps_rule == TT_EPS_ADAPTIVE && !(p->c_eps > 0.0)) return false;
   if (p->flux != TT_FLUX_PRODUCTS && p->flux != TT_FLUX_CROSS) return false;
   if (p->forcing_waves < 0 || p->forcing_waves > TT_MAX_WAVES) return false;
+  if (p->bc_x != TT_BC_PERIODIC && p->bc_x != TT_BC_EXACT) return false;
+  if (p->bc_x == TT_BC_EXACT &&
+      (p->eqn != TT_LINEAR || p->recon == TT_WENO5 || p->boundary_waves < 1 || p->boundary_waves > TT_MAX_WAVES))
+    return false;
   return true;
 }
 
@@ -1189,6 +1369,24 @@ tt_status tt_fv_set_forcing(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwaves
     if (++per[w.field] > S.p.forcing_waves) return TT_ERR_ARG;
   }
   S.waves.assign(waves, waves + nwaves);
+  S.time = t0;
+  return TT_OK;
+}
+
+tt_status tt_fv_set_boundary(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwaves, double t0) {
+  if (!ctx || nwaves < 0 || (nwaves > 0 && !waves) || !std::isfinite(t0)) return TT_ERR_ARG;
+  Solver& S = ctx->S;
+  if (S.p.bc_x != TT_BC_EXACT) return TT_ERR_ARG;
+  int per[3] = {0, 0, 0};
+  for (int i = 0; i < nwaves; ++i) {
+    const tt_wave& w = waves[i];
+    if (w.field < 0 || w.field > 2 || !std::isfinite(w.amp) || !std::isfinite(w.kx) || !std::isfinite(w.ky) ||
+        !std::isfinite(w.omega) || !std::isfinite(w.phase))
+      return TT_ERR_ARG;
+    if (++per[w.field] > S.p.boundary_waves) return TT_ERR_ARG;
+  }
+  S.bwaves.assign(waves, waves + nwaves);
+  S.boundary_set = true;
   S.time = t0;
   return TT_OK;
 }
