@@ -381,8 +381,24 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(LeafJob<Real> j0, Leaf
 // (p x p each) by Householder reflectors that touch row j of T and rows 0..j
 // of each B_b only.  Reflectors are kept unnormalised: v = [alpha - beta at T
 // row j; B_b(0..j, j)], tau = -1 / (beta (alpha - beta)), so no scaling pass
-// is needed.  Columns are spread over lanes (lane = column within a group of
-// 32), the bottom blocks over warps; a node with one input passes it through.
+// is needed.  A node with one input passes it through.
+//
+// Work layout (GB300 FP64: an SM sub-partition issues one FP64 warp
+// instruction per ~64 cycles whatever the number of active lanes, so the
+// kernel packs lanes and counts instructions):
+// - the stacked blocks sit row-major in shared memory, row q = b p + i, with a
+//   padded row length ld = p (mod 16 rule below), so lanes on consecutive
+//   columns read consecutive words;
+// - a lane owns column c = w C + (lane mod C) of its warp w and the row class
+//   i = r (mod K), r = lane / C, of every bottom block (C K = 32), so one
+//   column's K row classes live in one warp and its dot product is finished
+//   by log2 K shuffle steps, with no shared-memory partials;
+// - the last warp is the scalar warp: while the others form the dot products
+//   of column j with the trailing columns, its lane 0 forms reflector j from
+//   the norm that the owners of column j left at the end of the previous
+//   column.  Two block barriers per column.
+// ld = p rounded up to C (mod 16) when C < 16: lanes of a half warp then hold
+// K/2 consecutive rows of C consecutive columns, i.e. 16 distinct banks.
 template <typename Real>
 struct MergeJob {
   const Real* Rin;
@@ -394,26 +410,46 @@ struct MergeJob {
   Real* taum;
 };
 
+// lanes per column (K) and columns per warp (C) of the merge and apply-merge
+// kernels for a triangle of order p, the merge's work warps and its padded
+// shared-memory row length
+struct MergeShape {
+  int K, C, nwork, ld;
+};
+constexpr int AM_WARPS = 4;  // warps per CTA of the apply-merge kernel
+__host__ __device__ inline int pow2_ceil(int x) {
+  int v = 1;
+  while (v < x) v <<= 1;
+  return v;
+}
+inline MergeShape merge_shape(int p) {
+  int C = pow2_ceil((p + 14) / 15);  // at most 15 work warps
+  int K = 32 / C;
+  if (K > pow2_ceil(p)) {
+    K = pow2_ceil(p);
+    C = 32 / K;
+  }
+  int ld = p;
+  if (C < 16)
+    while ((ld & 15) != C) ++ld;
+  return MergeShape{K, C, (p + C - 1) / C, ld};
+}
+
 template <typename Real>
-__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, MergeJob<Real> j1, int p, int g) {
+__global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, MergeJob<Real> j1, int p, int g, int K,
+                                                         int ld) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  Real* sm = reinterpret_cast<Real*>(smraw);
+  Real* X = reinterpret_cast<Real*>(smraw);  // ng p rows x ld, row q = b p + i
+  __shared__ Real s_tau, s_vj, s_nrm;
   const bool second = (int)blockIdx.x >= j0.nodes;
   const MergeJob<Real> jb = second ? j1 : j0;
-  const Real* __restrict__ Rin = jb.Rin;
-  const int nin = jb.nin;
-  Real* Rout = jb.Rout;
-  Real* Vm = jb.Vm;
-  Real* vtop = jb.vtop;
-  Real* taum = jb.taum;
   const int node = second ? (int)blockIdx.x - j0.nodes : (int)blockIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int first = node * g, ng = min(g, nin - first);
-  Real* Ro = Rout + (size_t)node * p * p;
-  Real* Vo = Vm + (size_t)node * g * p * p;  // bottom blocks 1..ng-1 at Vo + b*p*p
-  Real* vt = vtop + (size_t)node * p;
-  Real* to = taum + (size_t)node * p;
-  const Real* Ri = Rin + (size_t)first * p * p;
+  const int first = node * g, ng = min(g, jb.nin - first);
+  Real* Ro = jb.Rout + (size_t)node * p * p;
+  Real* Vo = jb.Vm + (size_t)node * g * p * p;  // bottom blocks 1..ng-1 at Vo + b p p
+  Real* vt = jb.vtop + (size_t)node * p;
+  Real* to = jb.taum + (size_t)node * p;
+  const Real* __restrict__ Ri = jb.Rin + (size_t)first * p * p;
   if (ng == 1) {
     for (int t = threadIdx.x; t < p * p; t += blockDim.x) Ro[t] = Ri[t];
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
@@ -422,29 +458,37 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, Merg
     }
     return;
   }
-  Real* T = sm;                       // block 0 (p x p)
-  Real* part = sm + (size_t)ng * p * p;  // [slice][column] partial sums
-  __shared__ Real s_tau, s_vj;
-  __shared__ Real s_nrm[QR_THREADS / 32];  // per-slice partial norms of the next column
-  for (int t = threadIdx.x; t < ng * p * p; t += blockDim.x) T[t] = Ri[t];
-  const int G = (p + 31) / 32;
-  const int S = max(1, nw / G);
-  const int grp = w % G, sl = w / G;
-  const int c = grp * 32 + lane;  // this lane's column
-  const bool active = (sl < S) && (c < p);
-  // norm below the diagonal of column 0: B_b[0,0]^2 over this slice's bottoms
+  const int pp = p * p;
+  for (int t = threadIdx.x; t < ng * pp; t += blockDim.x) {
+    const int b = t / pp, rem = t - b * pp, i = rem % p, c = rem / p;
+    X[(size_t)(b * p + i) * ld + c] = Ri[t];
+  }
+  const int C = 32 / K, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nwork = (int)(blockDim.x >> 5) - 1;
+  const bool scalar = w == nwork;
+  const int r = lane / C, c = w * C + lane % C;
+  const int wlast = w * C + C - 1;  // the warp's last column
   __syncthreads();
-  if (active && c == 0) {
+  if (scalar && lane == 0) {
     Real sg = Real(0);
-    for (int b = 1 + sl; b < ng; b += S) sg = fma(T[(size_t)b * p * p], T[(size_t)b * p * p], sg);
-    s_nrm[sl] = sg;
+    for (int b = 1; b < ng; ++b) sg = fma(X[(size_t)b * p * ld], X[(size_t)b * p * ld], sg);
+    s_nrm = sg;
   }
   __syncthreads();
   for (int j = 0; j < p; ++j) {
-    if (threadIdx.x == 0) {
-      Real sg = Real(0);
-      for (int q = 0; q < S; ++q) sg += s_nrm[q];
-      const Real alpha = T[j + (size_t)j * p];
+    const bool busy = !scalar && wlast > j;  // warp-uniform
+    const bool live = busy && c > j && c < p;
+    Real d = Real(0);
+    if (busy) {
+      if (live)
+        for (int b = 1; b < ng; ++b) {
+          const Real* Xb = X + (size_t)b * p * ld;
+          for (int i = r; i <= j; i += K) d = fma(Xb[(size_t)i * ld + j], Xb[(size_t)i * ld + c], d);
+        }
+      for (int o = C; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    } else if (scalar && lane == 0) {
+      const Real sg = s_nrm;
+      const Real alpha = X[(size_t)j * ld + j];
       Real tau = Real(0), vj = Real(0), beta = alpha;
       if (sg > Real(0) && fma(alpha, alpha, sg) >= hh_safe_norm<Real>() * hh_safe_norm<Real>()) {
         const Real nrm = sqrt(fma(alpha, alpha, sg));
@@ -456,63 +500,64 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, Merg
       s_vj = vj;
       to[j] = tau;
       vt[j] = vj;
-      T[j + (size_t)j * p] = beta;
+      X[(size_t)j * ld + j] = beta;
     }
     __syncthreads();
-    const Real tau = s_tau, vj = s_vj;
-    if (tau != Real(0)) {
-      // partial dots of column c with v over this slice's bottom blocks
-      if (active && c > j) {
-        Real d = Real(0);
-        for (int b = 1 + sl; b < ng; b += S) {
-          const Real* Bb = T + (size_t)b * p * p;
-          for (int i = 0; i <= j; ++i) d = fma(Bb[i + (size_t)j * p], Bb[i + (size_t)c * p], d);
+    if (busy) {
+      const Real tau = s_tau, vj = s_vj;
+      // the warp holding column j + 1 also sums the squares of what it
+      // writes (warp-uniform; the other warps skip that FMA)
+      const bool next = j + 1 < p && j + 1 >= w * C && j + 1 <= wlast;
+      Real sq = Real(0);
+      if (live) {
+        Real* Tj = X + (size_t)j * ld + c;
+        const Real f = tau * fma(vj, *Tj, d);
+        for (int b = 1; b < ng; ++b) {
+          Real* Xb = X + (size_t)b * p * ld;
+          if (next) {
+            for (int i = r; i <= j; i += K) {
+              const Real x = fma(-f, Xb[(size_t)i * ld + j], Xb[(size_t)i * ld + c]);
+              Xb[(size_t)i * ld + c] = x;
+              sq = fma(x, x, sq);
+            }
+          } else {
+            for (int i = r; i <= j; i += K)
+              Xb[(size_t)i * ld + c] = fma(-f, Xb[(size_t)i * ld + j], Xb[(size_t)i * ld + c]);
+          }
         }
-        part[(size_t)sl * p + c] = d;
+        if (r == 0) *Tj = fma(-f, vj, *Tj);
       }
-      __syncthreads();
-      if (active && sl == 0 && c > j) {
-        Real d = vj * T[j + (size_t)c * p];
-        for (int q = 0; q < S; ++q) d += part[(size_t)q * p + c];
-        part[c] = tau * d;  // f_c (slice 0 row of the partial table)
-      }
-      __syncthreads();
-      if (active && c > j) {
-        const Real f = part[c];
-        if (sl == 0) T[j + (size_t)c * p] -= f * vj;
-        for (int b = 1 + sl; b < ng; b += S) {
-          Real* Bb = T + (size_t)b * p * p;
-          for (int i = 0; i <= j; ++i) Bb[i + (size_t)c * p] = fma(-f, Bb[i + (size_t)j * p], Bb[i + (size_t)c * p]);
+      // the owners of column j + 1 leave its norm below the diagonal (rows
+      // 0..j just updated, row j + 1 untouched by reflector j) for the
+      // scalar warp
+      if (next) {
+        for (int o = C; o < 32; o <<= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (c == j + 1 && r == 0) {
+          for (int b = 1; b < ng; ++b) {
+            const Real x = X[(size_t)(b * p + j + 1) * ld + j + 1];
+            sq = fma(x, x, sq);
+          }
+          s_nrm = sq;
         }
       }
-    }
-    // the thread of column j+1 in each slice continues with that column's
-    // norm below its diagonal (bottoms' rows 0..j+1) over its own bottoms;
-    // thread 0 adds the slices' partials at the start of the next column
-    if (active && c == j + 1) {
-      Real sg = Real(0);
-      for (int b = 1 + sl; b < ng; b += S) {
-        const Real* Bb = T + (size_t)b * p * p;
-        for (int i = 0; i <= j + 1; ++i) sg = fma(Bb[i + (size_t)c * p], Bb[i + (size_t)c * p], sg);
-      }
-      s_nrm[sl] = sg;
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+  for (int t = threadIdx.x; t < pp; t += blockDim.x) {
     const int i = t % p, jj = t / p;
-    Ro[t] = (i <= jj) ? T[t] : Real(0);
+    Ro[t] = (i <= jj) ? X[(size_t)i * ld + jj] : Real(0);
   }
-  for (int t = threadIdx.x; t < (ng - 1) * p * p; t += blockDim.x) {
-    const int i = t % p, jj = (t / p) % p;
-    Vo[(size_t)p * p + t] = (i <= jj) ? T[(size_t)p * p + t] : Real(0);
+  for (int t = threadIdx.x; t < (ng - 1) * pp; t += blockDim.x) {
+    const int b = 1 + t / pp, rem = t % pp, i = rem % p, jj = rem / p;
+    Vo[(size_t)pp + t] = (i <= jj) ? X[(size_t)(b * p + i) * ld + jj] : Real(0);
   }
 }
 
-// fan-in of a merge node: as many triangles as fit in shared memory, but at
-// most 4 from p = 32 up, where a merge is FP64-bound on its SM: a level of
-// 4-triangle nodes on separate SMs, then a short second level, beats one SM
-// eliminating 11 triangles in turn (442 us at p = 40)
+// fan-in of a merge node: as many triangles as the merge's and the
+// apply-merge's shared memory hold, but at most 4 from p = 32 up and 16
+// below: a lane's dot product runs over every bottom block of its column, so
+// a level of small nodes on separate SMs beats one SM eliminating many
+// triangles in turn
 // TT_QR_FANIN (environment, read once): the largest merge fan-in from p = 32
 // up (default 4), for tuning.
 static int qr_fanin_cap() {
@@ -523,10 +568,13 @@ static int qr_fanin_cap() {
   }();
   return v;
 }
+static int apply_merge_lanes(int p) { return std::min(32, pow2_ceil(p)); }
 static int qr_merge_fanin(int p, size_t elem) {
-  const size_t per = ((size_t)p * p + (size_t)16 * p) * elem;
-  const int g = std::max(2, int(QR_SMEM_MAX / per));
-  return p >= 32 ? std::min(g, qr_fanin_cap()) : g;
+  const MergeShape ms = merge_shape(p);
+  const size_t per = (size_t)p * ms.ld * elem;
+  const size_t per_apply = (size_t)AM_WARPS * p * (32 / apply_merge_lanes(p)) * elem;
+  const int g = int(std::min(QR_SMEM_MAX / per, QR_SMEM_MAX / per_apply));
+  return std::max(2, std::min(g, p >= 32 ? qr_fanin_cap() : 16));
 }
 
 static int qr_leaf_rows(int p, size_t elem) {
@@ -597,9 +645,10 @@ static void tsqr_run(Exec& ex, int nj, const void* const* X, const int* x64, con
     if (nodes_total == 0) break;
     if (!ex.dry) {
       smem_attr_once(k_qr_merge<Real>);
-      const size_t smem = ((size_t)maxin * p * p + (size_t)16 * p) * sizeof(Real);
+      const MergeShape ms = merge_shape(p);
+      const size_t smem = (size_t)maxin * p * ms.ld * sizeof(Real);
       TT_KERNEL(ex, K_QR_MERGE, mfl, mby,
-                k_qr_merge<Real><<<nodes_total, QR_THREADS, smem, ex.s>>>(mj[0], mj[1], p, g));
+                k_qr_merge<Real><<<nodes_total, 32 * (ms.nwork + 1), smem, ex.s>>>(mj[0], mj[1], p, g, ms.K, ms.ld));
     }
   }
   for (int q = 0; q < nj; ++q) t[q]->R = R[q];
@@ -689,6 +738,17 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(ALeafJob<Real> j
 
 // Reverse of a merge node: [top; B_1; ...] = Q_node [Z; 0; ...]; the top goes
 // to input node*g, block b to input node*g + b (each p x k, ld p).
+//
+// The k columns of Z are independent under Q_node, so each warp takes C of
+// them through all p reflectors on its own: lane (r, cc) = (lane / C,
+// lane mod C) owns rows i = r (mod K) of every block of column cc (C K = 32,
+// K the power of two >= p capped at 32), keeps them in its warp's slice of
+// shared memory (row-major, C words per row, so a warp's 32 lanes touch 32
+// consecutive words), and a dot product over the stacked rows is finished by
+// log2 K shuffle steps.  No block barrier inside the sweep.  A node's column
+// groups are spread over `cpn` CTAs of up to four warps (one per SM
+// sub-partition), so the p-reflector chains of a level's nodes run on many
+// SMs at once.
 template <typename Real>
 struct AMergeJob {
   const Real* Vm;
@@ -703,73 +763,60 @@ struct AMergeJob {
 };
 
 template <typename Real>
-__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_merge(AMergeJob<Real> j0, AMergeJob<Real> j1, int p, int g,
-                                                               int k) {
+__global__ void __launch_bounds__(AM_WARPS * 32) k_qr_apply_merge(AMergeJob<Real> j0, AMergeJob<Real> j1, int p,
+                                                                  int g, int k, int K, int cpn) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  Real* sm = reinterpret_cast<Real*>(smraw);
-  const bool second = (int)blockIdx.x >= j0.nodes;
+  const int nodeg = (int)blockIdx.x / cpn, part = (int)blockIdx.x - nodeg * cpn;
+  const bool second = nodeg >= j0.nodes;
   const AMergeJob<Real> jb = second ? j1 : j0;
-  const Real* __restrict__ Vm = jb.Vm;
-  const Real* __restrict__ vtop = jb.vtop;
-  const Real* __restrict__ taum = jb.taum;
-  const int nin = jb.nin;
-  const int node = second ? (int)blockIdx.x - j0.nodes : (int)blockIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int first = node * g, ng = min(g, nin - first);
+  const int node = second ? nodeg - j0.nodes : nodeg;
+  const int first = node * g, ng = min(g, jb.nin - first);
   const size_t zoff = (size_t)node * jb.zstride;
   const long zld = jb.zld;
   Real* out = jb.zout + (size_t)first * p * k;
+  const int C = 32 / K, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = lane / C, cc = lane % C;
+  const int c = (part * AM_WARPS + w) * C + cc;  // this lane's column of Z
+  if ((part * AM_WARPS + w) * C >= k) return;    // warp-uniform: no column here
+  const bool col = c < k;
   if (ng == 1) {
-    for (int t = threadIdx.x; t < p * k; t += blockDim.x)
-      out[t] = ld_any<Real>(jb.zin, zoff + (t % p) + (size_t)(t / p) * zld, jb.z64);
+    if (col)
+      for (int i = r; i < p; i += K) out[i + (size_t)c * p] = ld_any<Real>(jb.zin, zoff + i + (size_t)c * zld, jb.z64);
     return;
   }
-  Real* Z = sm;                          // ng blocks of p x k
-  Real* part = sm + (size_t)ng * p * k;  // [slice][column]
-  for (int t = threadIdx.x; t < p * k; t += blockDim.x)
-    Z[t] = ld_any<Real>(jb.zin, zoff + (t % p) + (size_t)(t / p) * zld, jb.z64);
-  for (int t = threadIdx.x; t < (ng - 1) * p * k; t += blockDim.x) Z[(size_t)p * k + t] = Real(0);
-  const Real* V = Vm + (size_t)node * g * p * p;
-  const Real* vt = vtop + (size_t)node * p;
-  const Real* tv = taum + (size_t)node * p;
-  const int G = (k + 31) / 32;
-  const int S = max(1, nw / G);
-  const int grp = w % G, sl = w / G;
-  const int c = grp * 32 + lane;
-  const bool active = (sl < S) && (c < k);
-  __syncthreads();
+  Real* Z = reinterpret_cast<Real*>(smraw) + (size_t)w * ng * p * C;  // row q = b p + i, C words per row
+  for (int q = r; q < ng * p; q += K)
+    Z[(size_t)q * C + cc] = (col && q < p) ? ld_any<Real>(jb.zin, zoff + q + (size_t)c * zld, jb.z64) : Real(0);
+  __syncwarp();
+  const Real* __restrict__ V = jb.Vm + (size_t)node * g * p * p;
+  const Real* __restrict__ vt = jb.vtop + (size_t)node * p;
+  const Real* __restrict__ tv = jb.taum + (size_t)node * p;
   for (int j = p - 1; j >= 0; --j) {
     const Real tj = tv[j];
-    if (tj == Real(0)) continue;  // uniform across the block
+    if (tj == Real(0)) continue;  // uniform across the warp
     const Real vj = vt[j];
-    if (active) {
-      Real d = Real(0);
-      for (int b = 1 + sl; b < ng; b += S) {
-        const Real* Vb = V + (size_t)b * p * p + (size_t)j * p;
-        const Real* Zb = Z + (size_t)b * p * k + (size_t)c * p;
-        for (int i = 0; i <= j; ++i) d = fma(Vb[i], Zb[i], d);
-      }
-      part[(size_t)sl * k + c] = d;
+    const bool top = r == (j & (K - 1));  // owner of top row j
+    Real d = top ? vj * Z[(size_t)j * C + cc] : Real(0);
+    for (int b = 1; b < ng; ++b) {
+      const Real* Vb = V + (size_t)b * p * p + (size_t)j * p;
+      const Real* Zb = Z + (size_t)b * p * C + cc;
+      for (int i = r; i <= j; i += K) d = fma(__ldg(Vb + i), Zb[(size_t)i * C], d);
     }
-    __syncthreads();
-    if (active && sl == 0) {
-      Real d = vj * Z[j + (size_t)c * p];
-      for (int q = 0; q < S; ++q) d += part[(size_t)q * k + c];
-      part[c] = tj * d;
+    for (int o = C; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    const Real f = tj * d;
+    if (top) Z[(size_t)j * C + cc] = fma(-f, vj, Z[(size_t)j * C + cc]);
+    for (int b = 1; b < ng; ++b) {
+      const Real* Vb = V + (size_t)b * p * p + (size_t)j * p;
+      Real* Zb = Z + (size_t)b * p * C + cc;
+      for (int i = r; i <= j; i += K) Zb[(size_t)i * C] = fma(-f, __ldg(Vb + i), Zb[(size_t)i * C]);
     }
-    __syncthreads();
-    if (active) {
-      const Real f = part[c];
-      if (sl == 0) Z[j + (size_t)c * p] -= f * vj;
-      for (int b = 1 + sl; b < ng; b += S) {
-        const Real* Vb = V + (size_t)b * p * p + (size_t)j * p;
-        Real* Zb = Z + (size_t)b * p * k + (size_t)c * p;
-        for (int i = 0; i <= j; ++i) Zb[i] = fma(-f, Vb[i], Zb[i]);
-      }
-    }
-    __syncthreads();
   }
-  for (int t = threadIdx.x; t < ng * p * k; t += blockDim.x) out[t] = Z[t];
+  __syncwarp();
+  if (col)
+    for (int q = r; q < ng * p; q += K) {
+      const int b = q / p, i = q - b * p;
+      out[(size_t)b * p * k + i + (size_t)c * p] = Z[(size_t)q * C + cc];
+    }
 }
 
 // Out_q (m_q x k) = Q_q [C_q; 0] for nj (1 or 2) trees with the same p:
@@ -810,9 +857,12 @@ static void tsqr_apply_run(Exec& ex, int nj, const QRTreeT<Real>* const* t, cons
     }
     if (!ex.dry && nodes_total > 0) {
       smem_attr_once(k_qr_apply_merge<Real>);
-      const size_t smem = ((size_t)maxin * p * k + (size_t)16 * k) * sizeof(Real);
+      const int K = apply_merge_lanes(p), C = 32 / K;
+      const int cpn = ceil_div(ceil_div(k, C), AM_WARPS);
+      const size_t smem = (size_t)AM_WARPS * maxin * p * C * sizeof(Real);
       TT_KERNEL(ex, K_QR_APPLY_MERGE, fl, by,
-                k_qr_apply_merge<Real><<<nodes_total, QR_THREADS, smem, ex.s>>>(aj[0], aj[1], p, g, k));
+                k_qr_apply_merge<Real><<<nodes_total * cpn, AM_WARPS * 32, smem, ex.s>>>(aj[0], aj[1], p, g, k, K,
+                                                                                            cpn));
     }
   }
   ALeafJob<Real> lj[2] = {};
