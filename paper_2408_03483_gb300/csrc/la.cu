@@ -266,59 +266,36 @@ void fdot(Exec& ex, const double* X, const double* Y, long n, double* out) {
 }
 
 // ============================================================== TSQR
-// Householder QR of row blocks held in shared memory (LAPACK sign convention:
-// beta = -sign(alpha) ||x||, v(0) = 1, tau = (beta - alpha) / beta).
+// Tall-skinny QR: Householder QR of row blocks (leaves) held in shared
+// memory, then trees of merges of their triangular factors; the reflectors
+// are kept unnormalised (beta = -sign(alpha) ||x||, v = x - beta e_j,
+// tau = 2 / v^T v = -1 / (beta (alpha - beta))).
 constexpr int QR_THREADS = 512;
 constexpr size_t QR_SMEM_MAX = 200 * 1024;
 
-// Two barriers per column: warp 0 forms the reflector of column j (its norm
-// below the diagonal was computed by warp 0 while updating that column in
-// the previous step), then all warps update the trailing columns.
-template <typename Real>
-__device__ void cta_householder_qr(Real* A, int mb, int p, Real* tau_out) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ Real s_tau;
-  Real next_sigma = Real(0);  // warp 0: sum of squares of column j below row j
-  if (w == 0) {
-    Real s = Real(0);
-    for (int i = 1 + lane; i < mb; i += 32) s = fma(A[i], A[i], s);
-    next_sigma = warp_sum(s);
+// lanes per column (K) and columns per warp (C) of the merge and apply-merge
+// kernels for a triangle of order p, the merge's work warps and its padded
+// shared-memory row length
+struct MergeShape {
+  int K, C, nwork, ld;
+};
+constexpr int AM_WARPS = 4;  // warps per CTA of the apply-merge kernel
+__host__ __device__ inline int pow2_ceil(int x) {
+  int v = 1;
+  while (v < x) v <<= 1;
+  return v;
+}
+inline MergeShape merge_shape(int p) {
+  int C = pow2_ceil((p + 14) / 15);  // at most 15 work warps
+  int K = 32 / C;
+  if (K > pow2_ceil(p)) {
+    K = pow2_ceil(p);
+    C = 32 / K;
   }
-  for (int j = 0; j < p; ++j) {
-    Real* col = A + (size_t)j * mb;
-    if (w == 0) {
-      const Real sigma = next_sigma, alpha = col[j];
-      Real tau, beta, scale;
-      householder_params(alpha, sigma, beta, tau, scale);
-      if (sigma > Real(0))
-        for (int i = j + 1 + lane; i < mb; i += 32) col[i] *= scale;
-      if (lane == 0) {
-        col[j] = beta;
-        s_tau = tau;
-        tau_out[j] = tau;
-      }
-    }
-    __syncthreads();
-    const Real tau = s_tau;
-    for (int c = j + 1 + w; c < p; c += nw) {
-      Real* cc = A + (size_t)c * mb;
-      if (tau != Real(0)) {
-        Real d = Real(0);
-        for (int i = j + 1 + lane; i < mb; i += 32) d = fma(col[i], cc[i], d);
-        d = warp_sum(d) + cc[j];
-        const Real f = tau * d;
-        if (lane == 0) cc[j] -= f;
-        for (int i = j + 1 + lane; i < mb; i += 32) cc[i] = fma(-f, col[i], cc[i]);
-      }
-      if (c == j + 1) {  // warp 0: norm of the next column below its diagonal
-        __syncwarp();
-        Real s = Real(0);
-        for (int i = j + 2 + lane; i < mb; i += 32) s = fma(cc[i], cc[i], s);
-        next_sigma = warp_sum(s);
-      }
-    }
-    __syncthreads();
-  }
+  int ld = p;
+  if (C < 16)
+    while ((ld & 15) != C) ++ld;
+  return MergeShape{K, C, (p + C - 1) / C, ld};
 }
 
 // Element i of an array that is FP64 (f64 != 0) or of the working type
@@ -350,30 +327,102 @@ struct LeafJob {
   int nb;
 };
 
+// Householder QR of an mb x p row block (rows past m are zero) in shared
+// memory, with the merge kernel's lane layout: the block row-major with the
+// padded row length ld, lane (r, cc) of warp w owning column w C + cc and
+// rows i = r (mod K), the reflector of column j formed by the scalar warp
+// while the work warps form the dot products with the trailing columns.
+// Reflectors are unnormalised, v = [alpha - beta at row j; A(j+1.., j)],
+// tau = -1 / (beta (alpha - beta)); V keeps v below the diagonal and its top
+// entry alpha - beta on the diagonal, R the upper triangle.
 template <typename Real>
-__global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(LeafJob<Real> j0, LeafJob<Real> j1, int p, int mb) {
+__global__ void __launch_bounds__(QR_THREADS) k_qr_blocks(LeafJob<Real> j0, LeafJob<Real> j1, int p, int mb, int K,
+                                                          int ld) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  Real* sm = reinterpret_cast<Real*>(smraw);
+  Real* A = reinterpret_cast<Real*>(smraw);  // mb rows x ld
+  __shared__ Real s_tau, s_vj, s_nrm;
+  __shared__ Real s_vt[128];
   const bool second = (int)blockIdx.x >= j0.nb;
   const LeafJob<Real> jb = second ? j1 : j0;
   const int b = second ? (int)blockIdx.x - j0.nb : (int)blockIdx.x, r0 = b * mb;
   const int m = jb.m;
-  Real* V = jb.V;
-  Real* tau = jb.tau;
-  Real* Rout = jb.R;
-  Real* A = sm;
   for (int t = threadIdx.x; t < mb * p; t += blockDim.x) {
-    const int i = t % mb, j = t / mb;
-    A[t] = (r0 + i < m) ? ld_any<Real>(jb.X, (size_t)(r0 + i) + (size_t)j * jb.ldx, jb.x64) : Real(0);
+    const int i = t % mb, c = t / mb;
+    A[(size_t)i * ld + c] = (r0 + i < m) ? ld_any<Real>(jb.X, (size_t)(r0 + i) + (size_t)c * jb.ldx, jb.x64) : Real(0);
+  }
+  const int C = 32 / K, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nwork = (int)(blockDim.x >> 5) - 1;
+  const bool scalar = w == nwork;
+  const int r = lane / C, c = w * C + lane % C;
+  const int wlast = w * C + C - 1;
+  __syncthreads();
+  if (scalar && lane == 0) {
+    Real sg = Real(0);
+    for (int i = 1; i < mb; ++i) sg = fma(A[(size_t)i * ld], A[(size_t)i * ld], sg);
+    s_nrm = sg;
   }
   __syncthreads();
-  cta_householder_qr<Real>(A, mb, p, tau + (size_t)b * p);
-  Real* Vb = V + (size_t)b * mb * p;
-  for (int t = threadIdx.x; t < mb * p; t += blockDim.x) Vb[t] = A[t];
-  Real* Rb = Rout + (size_t)b * p * p;
+  Real* tau_out = jb.tau + (size_t)b * p;
+  for (int j = 0; j < p; ++j) {
+    const bool busy = !scalar && wlast > j;  // warp-uniform
+    const bool live = busy && c > j && c < p;
+    const int i0 = j + 1 + ((r - j - 1) & (K - 1));  // first row > j of this lane's class
+    Real d = Real(0);
+    if (busy) {
+      if (live)
+        for (int i = i0; i < mb; i += K) d = fma(A[(size_t)i * ld + j], A[(size_t)i * ld + c], d);
+      for (int o = C; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    } else if (scalar && lane == 0) {
+      const Real sg = s_nrm;
+      const Real alpha = A[(size_t)j * ld + j];
+      Real tau = Real(0), vj = Real(0), beta = alpha;
+      if (sg > Real(0) && fma(alpha, alpha, sg) >= hh_safe_norm<Real>() * hh_safe_norm<Real>()) {
+        const Real nrm = sqrt(fma(alpha, alpha, sg));
+        beta = alpha >= Real(0) ? -nrm : nrm;
+        vj = alpha - beta;
+        tau = Real(-1) / (beta * vj);
+      }
+      s_tau = tau;
+      s_vj = vj;
+      s_vt[j] = vj;
+      tau_out[j] = tau;
+      A[(size_t)j * ld + j] = beta;
+    }
+    __syncthreads();
+    if (busy) {
+      const Real tau = s_tau, vj = s_vj;
+      const bool next = j + 1 < p && j + 1 >= w * C && j + 1 <= wlast;
+      Real sq = Real(0);
+      if (live) {
+        Real* Aj = A + (size_t)j * ld + c;
+        const Real f = tau * fma(vj, *Aj, d);
+        if (next) {
+          for (int i = i0; i < mb; i += K) {
+            const Real x = fma(-f, A[(size_t)i * ld + j], A[(size_t)i * ld + c]);
+            A[(size_t)i * ld + c] = x;
+            if (i > j + 1) sq = fma(x, x, sq);
+          }
+        } else {
+          for (int i = i0; i < mb; i += K) A[(size_t)i * ld + c] = fma(-f, A[(size_t)i * ld + j], A[(size_t)i * ld + c]);
+        }
+        if (r == 0) *Aj = fma(-f, vj, *Aj);
+      }
+      if (next) {
+        for (int o = C; o < 32; o <<= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (c == j + 1 && r == 0) s_nrm = sq;
+      }
+    }
+    __syncthreads();
+  }
+  Real* Vb = jb.V + (size_t)b * mb * p;
+  for (int t = threadIdx.x; t < mb * p; t += blockDim.x) {
+    const int i = t % mb, jj = t / mb;
+    Vb[t] = (i > jj) ? A[(size_t)i * ld + jj] : (i == jj ? s_vt[jj] : Real(0));
+  }
+  Real* Rb = jb.R + (size_t)b * p * p;
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-    const int i = t % p, j = t / p;
-    Rb[t] = (i <= j) ? A[i + (size_t)j * mb] : Real(0);
+    const int i = t % p, jj = t / p;
+    Rb[t] = (i <= jj) ? A[(size_t)i * ld + jj] : Real(0);
   }
 }
 
@@ -409,31 +458,6 @@ struct MergeJob {
   Real* vtop;
   Real* taum;
 };
-
-// lanes per column (K) and columns per warp (C) of the merge and apply-merge
-// kernels for a triangle of order p, the merge's work warps and its padded
-// shared-memory row length
-struct MergeShape {
-  int K, C, nwork, ld;
-};
-constexpr int AM_WARPS = 4;  // warps per CTA of the apply-merge kernel
-__host__ __device__ inline int pow2_ceil(int x) {
-  int v = 1;
-  while (v < x) v <<= 1;
-  return v;
-}
-inline MergeShape merge_shape(int p) {
-  int C = pow2_ceil((p + 14) / 15);  // at most 15 work warps
-  int K = 32 / C;
-  if (K > pow2_ceil(p)) {
-    K = pow2_ceil(p);
-    C = 32 / K;
-  }
-  int ld = p;
-  if (C < 16)
-    while ((ld & 15) != C) ++ld;
-  return MergeShape{K, C, (p + C - 1) / C, ld};
-}
 
 template <typename Real>
 __global__ void __launch_bounds__(QR_THREADS) k_qr_merge(MergeJob<Real> j0, MergeJob<Real> j1, int p, int g, int K,
@@ -572,14 +596,17 @@ static int apply_merge_lanes(int p) { return std::min(32, pow2_ceil(p)); }
 static int qr_merge_fanin(int p, size_t elem) {
   const MergeShape ms = merge_shape(p);
   const size_t per = (size_t)p * ms.ld * elem;
-  const size_t per_apply = (size_t)AM_WARPS * p * (32 / apply_merge_lanes(p)) * elem;
+  const size_t per_apply = ((size_t)p * p + (size_t)AM_WARPS * p * (32 / apply_merge_lanes(p))) * elem;
   const int g = int(std::min(QR_SMEM_MAX / per, QR_SMEM_MAX / per_apply));
   return std::max(2, std::min(g, p >= 32 ? qr_fanin_cap() : 16));
 }
 
+// rows of a leaf: the leaf QR holds mb x ld entries, the leaf application mb x
+// (p + 2 AM_WARPS) (its reflectors and four warps' two columns)
 static int qr_leaf_rows(int p, size_t elem) {
   int mb = std::max(((p + 31) / 32) * 32, 64);
-  const int lim = int(QR_SMEM_MAX / (elem * (size_t)p));
+  const size_t row = std::max<size_t>(merge_shape(p).ld, (size_t)p + 2 * AM_WARPS) * elem;
+  const int lim = int((QR_SMEM_MAX - (size_t)p * elem) / row);
   return std::max(std::min(mb, lim), p);
 }
 
@@ -615,8 +642,10 @@ static void tsqr_run(Exec& ex, int nj, const void* const* X, const int* x64, con
   }
   if (!ex.dry) {
     smem_attr_once(k_qr_blocks<Real>);
-    const size_t smem = (size_t)mb * p * sizeof(Real);
-    TT_KERNEL(ex, K_QR, fl, by, k_qr_blocks<Real><<<nbt, QR_THREADS, smem, ex.s>>>(lj[0], lj[1], p, mb));
+    const MergeShape ms = merge_shape(p);
+    const size_t smem = (size_t)mb * ms.ld * sizeof(Real);
+    TT_KERNEL(ex, K_QR, fl, by,
+              k_qr_blocks<Real><<<nbt, 32 * (ms.nwork + 1), smem, ex.s>>>(lj[0], lj[1], p, mb, ms.K, ms.ld));
   }
   for (;;) {
     MergeJob<Real> mj[2] = {};
@@ -677,7 +706,11 @@ void tsqr2(Exec& ex, const Src* X1, int m1, long ldx1, const Src* X2, int m2, lo
 }
 
 // Apply the level-0 reflectors of each block (in reverse order) to
-// [Zin_block; 0], Zin_block = Zin + b*zstride (p x k, ld zld).
+// [Zin_block; 0], Zin_block = Zin + b*zstride (p x k, ld zld).  As in the
+// apply-merge kernel, each warp takes C columns of Z through all p
+// reflectors on its own (lane (r, cc) owning rows i = r (mod K) of column
+// cc, K = 16), the leaf's reflectors staged in shared memory once per CTA,
+// and a leaf's column groups spread over `cpn` CTAs.
 template <typename Real>
 struct ALeafJob {
   const Real* V;
@@ -692,47 +725,53 @@ struct ALeafJob {
   long ldo;
 };
 
+constexpr int AL_LANES = 16;  // lanes per column of the leaf application
+
 template <typename Real>
-__global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(ALeafJob<Real> j0, ALeafJob<Real> j1, int mb, int p,
-                                                                int k) {
+__global__ void __launch_bounds__(AM_WARPS * 32) k_qr_apply_blocks(ALeafJob<Real> j0, ALeafJob<Real> j1, int mb, int p,
+                                                                  int k, int cpn) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  Real* sm = reinterpret_cast<Real*>(smraw);
-  const bool second = (int)blockIdx.x >= j0.nb;
+  constexpr int K = AL_LANES, C = 32 / AL_LANES;
+  const int leafg = (int)blockIdx.x / cpn, part = (int)blockIdx.x - leafg * cpn;
+  const bool second = leafg >= j0.nb;
   const ALeafJob<Real> jb = second ? j1 : j0;
-  const Real* __restrict__ V = jb.V;
-  const Real* __restrict__ tau = jb.tau;
-  const int rows = jb.rows;
-  const int b = second ? (int)blockIdx.x - j0.nb : (int)blockIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  Real* Z = sm;  // mb x k
-  const size_t zoff = (size_t)b * jb.zstride;
-  for (int t = threadIdx.x; t < mb * k; t += blockDim.x) {
-    const int i = t % mb, j = t / mb;
-    Z[t] = (i < p) ? ld_any<Real>(jb.zin, zoff + i + (size_t)j * jb.zld, jb.z64) : Real(0);
+  const int b = second ? leafg - j0.nb : leafg;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = lane / C, cc = lane % C;
+  const int c = (part * AM_WARPS + w) * C + cc;  // this lane's column of Z
+  const bool col = c < k;
+  Real* V = reinterpret_cast<Real*>(smraw);  // mb x p, column-major, top entries on the diagonal
+  Real* tv = V + (size_t)mb * p;
+  {
+    const Real* __restrict__ Vg = jb.V + (size_t)b * mb * p;
+    for (int t = threadIdx.x; t < mb * p; t += blockDim.x) V[t] = Vg[t];
+    for (int t = threadIdx.x; t < p; t += blockDim.x) tv[t] = jb.tau[(size_t)b * p + t];
   }
   __syncthreads();
-  const Real* Vb = V + (size_t)b * mb * p;
-  const Real* tb = tau + (size_t)b * p;
-  for (int jr = p - 1; jr >= 0; --jr) {
-    const Real tj = tb[jr];
-    if (tj != Real(0)) {
-      const Real* v = Vb + (size_t)jr * mb;
-      for (int c = w; c < k; c += nw) {
-        Real* zc = Z + (size_t)c * mb;
-        Real d = Real(0);
-        for (int i = jr + 1 + lane; i < mb; i += 32) d = fma(v[i], zc[i], d);
-        d = warp_sum(d) + zc[jr];
-        const Real f = tj * d;
-        if (lane == 0) zc[jr] -= f;
-        for (int i = jr + 1 + lane; i < mb; i += 32) zc[i] = fma(-f, v[i], zc[i]);
-      }
-    }
-    __syncthreads();
+  if ((part * AM_WARPS + w) * C >= k) return;  // warp-uniform: no column here
+  Real* Z = tv + p + (size_t)w * mb * C;  // row i, C words per row
+  const size_t zoff = (size_t)b * jb.zstride;
+  for (int i = r; i < mb; i += K)
+    Z[(size_t)i * C + cc] = (col && i < p) ? ld_any<Real>(jb.zin, zoff + i + (size_t)c * jb.zld, jb.z64) : Real(0);
+  __syncwarp();
+  for (int j = p - 1; j >= 0; --j) {
+    const Real tj = tv[j];
+    if (tj == Real(0)) continue;  // uniform across the warp
+    const Real* v = V + (size_t)j * mb;
+    const bool top = r == (j & (K - 1));  // owner of row j
+    const int i0 = j + 1 + ((r - j - 1) & (K - 1));
+    Real d = top ? v[j] * Z[(size_t)j * C + cc] : Real(0);
+    for (int i = i0; i < mb; i += K) d = fma(v[i], Z[(size_t)i * C + cc], d);
+    for (int o = C; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    const Real f = tj * d;
+    if (top) Z[(size_t)j * C + cc] = fma(-f, v[j], Z[(size_t)j * C + cc]);
+    for (int i = i0; i < mb; i += K) Z[(size_t)i * C + cc] = fma(-f, v[i], Z[(size_t)i * C + cc]);
   }
-  const int r0 = b * mb;
-  for (int t = threadIdx.x; t < mb * k; t += blockDim.x) {
-    const int i = t % mb, j = t / mb;
-    if (r0 + i < rows) st_any<Real>(jb.out, (size_t)(r0 + i) + (size_t)j * jb.ldo, jb.o64, Z[t]);
+  __syncwarp();
+  if (col) {
+    const int r0 = b * mb;
+    for (int i = r; i < mb; i += K)
+      if (r0 + i < jb.rows) st_any<Real>(jb.out, (size_t)(r0 + i) + (size_t)c * jb.ldo, jb.o64, Z[(size_t)i * C + cc]);
   }
 }
 
@@ -745,7 +784,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_apply_blocks(ALeafJob<Real> j
 // K the power of two >= p capped at 32), keeps them in its warp's slice of
 // shared memory (row-major, C words per row, so a warp's 32 lanes touch 32
 // consecutive words), and a dot product over the stacked rows is finished by
-// log2 K shuffle steps.  No block barrier inside the sweep.  A node's column
+// log2 K shuffle steps.  The node's reflectors are copied to shared memory
+// once per CTA; no block barrier inside the sweep.  A node's column
 // groups are spread over `cpn` CTAs of up to four warps (one per SM
 // sub-partition), so the p-reflector chains of a level's nodes run on many
 // SMs at once.
@@ -777,20 +817,32 @@ __global__ void __launch_bounds__(AM_WARPS * 32) k_qr_apply_merge(AMergeJob<Real
   const int C = 32 / K, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int r = lane / C, cc = lane % C;
   const int c = (part * AM_WARPS + w) * C + cc;  // this lane's column of Z
-  if ((part * AM_WARPS + w) * C >= k) return;    // warp-uniform: no column here
   const bool col = c < k;
   if (ng == 1) {
-    if (col)
+    if ((part * AM_WARPS + w) * C < k && col)
       for (int i = r; i < p; i += K) out[i + (size_t)c * p] = ld_any<Real>(jb.zin, zoff + i + (size_t)c * zld, jb.z64);
     return;
   }
-  Real* Z = reinterpret_cast<Real*>(smraw) + (size_t)w * ng * p * C;  // row q = b p + i, C words per row
+  // the node's reflectors (bottom blocks 1..ng-1, column-major p x p) and
+  // their top entries and factors, staged once for all of the CTA's warps
+  const int nv = (ng - 1) * p * p;
+  Real* V = reinterpret_cast<Real*>(smraw);
+  Real* vt = V + nv;
+  Real* tv = vt + p;
+  {
+    const Real* __restrict__ Vg = jb.Vm + (size_t)node * g * p * p + (size_t)p * p;
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) V[t] = Vg[t];
+    for (int t = threadIdx.x; t < p; t += blockDim.x) {
+      vt[t] = jb.vtop[(size_t)node * p + t];
+      tv[t] = jb.taum[(size_t)node * p + t];
+    }
+  }
+  __syncthreads();
+  if ((part * AM_WARPS + w) * C >= k) return;  // warp-uniform: no column here
+  Real* Z = tv + p + (size_t)w * ng * p * C;  // row q = b p + i, C words per row
   for (int q = r; q < ng * p; q += K)
     Z[(size_t)q * C + cc] = (col && q < p) ? ld_any<Real>(jb.zin, zoff + q + (size_t)c * zld, jb.z64) : Real(0);
   __syncwarp();
-  const Real* __restrict__ V = jb.Vm + (size_t)node * g * p * p;
-  const Real* __restrict__ vt = jb.vtop + (size_t)node * p;
-  const Real* __restrict__ tv = jb.taum + (size_t)node * p;
   for (int j = p - 1; j >= 0; --j) {
     const Real tj = tv[j];
     if (tj == Real(0)) continue;  // uniform across the warp
@@ -798,17 +850,17 @@ __global__ void __launch_bounds__(AM_WARPS * 32) k_qr_apply_merge(AMergeJob<Real
     const bool top = r == (j & (K - 1));  // owner of top row j
     Real d = top ? vj * Z[(size_t)j * C + cc] : Real(0);
     for (int b = 1; b < ng; ++b) {
-      const Real* Vb = V + (size_t)b * p * p + (size_t)j * p;
+      const Real* Vb = V + (size_t)(b - 1) * p * p + (size_t)j * p;
       const Real* Zb = Z + (size_t)b * p * C + cc;
-      for (int i = r; i <= j; i += K) d = fma(__ldg(Vb + i), Zb[(size_t)i * C], d);
+      for (int i = r; i <= j; i += K) d = fma(Vb[i], Zb[(size_t)i * C], d);
     }
     for (int o = C; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     const Real f = tj * d;
     if (top) Z[(size_t)j * C + cc] = fma(-f, vj, Z[(size_t)j * C + cc]);
     for (int b = 1; b < ng; ++b) {
-      const Real* Vb = V + (size_t)b * p * p + (size_t)j * p;
+      const Real* Vb = V + (size_t)(b - 1) * p * p + (size_t)j * p;
       Real* Zb = Z + (size_t)b * p * C + cc;
-      for (int i = r; i <= j; i += K) Zb[(size_t)i * C] = fma(-f, __ldg(Vb + i), Zb[(size_t)i * C]);
+      for (int i = r; i <= j; i += K) Zb[(size_t)i * C] = fma(-f, Vb[i], Zb[(size_t)i * C]);
     }
   }
   __syncwarp();
@@ -859,7 +911,7 @@ static void tsqr_apply_run(Exec& ex, int nj, const QRTreeT<Real>* const* t, cons
       smem_attr_once(k_qr_apply_merge<Real>);
       const int K = apply_merge_lanes(p), C = 32 / K;
       const int cpn = ceil_div(ceil_div(k, C), AM_WARPS);
-      const size_t smem = (size_t)AM_WARPS * maxin * p * C * sizeof(Real);
+      const size_t smem = ((size_t)(maxin - 1) * p * p + 2 * (size_t)p + (size_t)AM_WARPS * maxin * p * C) * sizeof(Real);
       TT_KERNEL(ex, K_QR_APPLY_MERGE, fl, by,
                 k_qr_apply_merge<Real><<<nodes_total * cpn, AM_WARPS * 32, smem, ex.s>>>(aj[0], aj[1], p, g, k, K,
                                                                                             cpn));
@@ -878,10 +930,11 @@ static void tsqr_apply_run(Exec& ex, int nj, const QRTreeT<Real>* const* t, cons
   if (!ex.dry) {
     const int mb = t[0]->mb0;
     smem_attr_once(k_qr_apply_blocks<Real>);
-    const size_t smem = (size_t)mb * k * sizeof(Real);
+    const int cpn = ceil_div(ceil_div(k, 32 / AL_LANES), AM_WARPS);
+    const size_t smem = ((size_t)mb * p + p + (size_t)AM_WARPS * mb * (32 / AL_LANES)) * sizeof(Real);
     TT_REQUIRE(smem <= QR_SMEM_MAX + 16 * 1024, TT_ERR_ARG);
     TT_KERNEL(ex, K_QR_APPLY, fl, by,
-              k_qr_apply_blocks<Real><<<nbt, QR_THREADS, smem, ex.s>>>(lj[0], lj[1], mb, p, k));
+              k_qr_apply_blocks<Real><<<nbt * cpn, AM_WARPS * 32, smem, ex.s>>>(lj[0], lj[1], mb, p, k, cpn));
   }
 }
 

@@ -266,7 +266,7 @@ void fdot(Exec& ex, const double* X, const double* Y, long n, double* out);
 template <typename Real>
 struct QRTreeT {
   int m = 0, p = 0, mb0 = 0, nb0 = 0;
-  Real* V0 = nullptr;        // leaf reflectors: nb0 blocks of mb0 x p (unit diagonal implicit)
+  Real* V0 = nullptr;        // leaf reflectors: nb0 blocks of mb0 x p (top entries on the diagonal)
   Real* tau0 = nullptr;      // nb0 x p
   int g = 2;                 // fan-in of a merge node
   std::vector<int> nin;      // inputs of each merge level (bottom-up)
