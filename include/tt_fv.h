@@ -411,6 +411,18 @@ tt_status tt_cross(int32_t fn, const tt2* inputs, int32_t ninputs, const tt2* x0
                    int32_t max_sweeps, uint32_t seed, tt2* y, int32_t* sweeps_out, void* ws,
                    size_t ws_bytes, void* stream);
 
+/* Maximum-volume rows (Sec. 3.3, the pivot choice of every cross sweep): r
+ * row indices I of the n x r FP64 matrix U (device, column-major, ld n) such
+ * that every entry of U U[I, :]^{-1} has magnitude at most 1 + delta.  Rows
+ * are first chosen by partial pivoting, then swapped one at a time (the
+ * largest entry above 1 + delta, ties to the smallest row-major index) until
+ * none exceeds it or max_iter swaps were made (the bound may then not hold;
+ * no error).  The choice compares magnitudes only and is made in FP32.
+ * I: device int32[r], written.  Requires 1 <= r <= 128, n >= r. */
+size_t tt_maxvol_workspace_size(int32_t n, int32_t r);
+tt_status tt_maxvol(const double* U, int32_t n, int32_t r, double delta, int32_t max_iter, int32_t* I,
+                    void* ws, size_t ws_bytes, void* stream);
+
 /* Taylor-series TT reciprocal, Algorithm 1: y ~ 1/x with x_avg = sum(x)/N,
  * x~ = round(1 - x/x_avg), dy <- round(dy o x~), y <- round(y + dy) until
  * ||dy||_F / sqrt(N) <= tol.  TT_ERR_NOCONV after max_iter iterations. */

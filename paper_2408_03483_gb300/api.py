@@ -111,6 +111,21 @@ def tt_cross(fn, inputs, x0, fparams, tol, rank_cap, n1, n2, kick=4, max_sweeps=
     return y, sw.value
 
 
+def tt_maxvol(U, delta=1e-2, max_iter=200, stream=None):
+    """Maximum-volume rows of the n x r FP64 CUDA tensor U: an int32 CUDA
+    tensor of r row indices (tt_maxvol)."""
+    _require_cuda()
+    lib = C.load()
+    n, r = U.shape
+    Uc = U.t().contiguous()  # column-major n x r
+    idx = torch.empty(r, dtype=torch.int32, device=U.device)
+    ws = _ws(lib.tt_maxvol_workspace_size(n, r))
+    C.check("tt_maxvol", lib.tt_maxvol(ctypes.c_void_p(Uc.data_ptr()), n, r, delta, max_iter,
+                                       ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       _stream_ptr(stream)))
+    return idx
+
+
 def tt_reciprocal(x, tol, rank_cap, max_iter=50, y=None, stream=None):
     _require_cuda()
     lib = C.load()

@@ -134,6 +134,8 @@ SIGNATURES = {
     "tt_cross_workspace_size": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "tt_cross": (ctypes.c_int, [_i32, _P(tt2), _i32, _P(tt2), _P(_d), _d, _i32, _i32, _i32, ctypes.c_uint32,
                                 _P(tt2), _P(_i32), _vp, _sz, _vp]),
+    "tt_maxvol_workspace_size": (_sz, [_i32, _i32]),
+    "tt_maxvol": (ctypes.c_int, [_vp, _i32, _i32, _d, _i32, _vp, _vp, _sz, _vp]),
     "tt_reciprocal_workspace_size": (_sz, [_i32, _i32, _i32, _i32]),
     "tt_reciprocal": (ctypes.c_int, [_P(tt2), _d, _i32, _i32, _P(tt2), _P(_i32), _vp, _sz, _vp]),
     "tt_recon_linear": (ctypes.c_int, [_P(tt2), _i32, _i32, _P(tt2), _P(tt2), _vp]),

@@ -1777,6 +1777,20 @@ tt_status tt_cross(int32_t fn, const tt2* inputs, int32_t ninputs, const tt2* x0
   });
 }
 
+size_t tt_maxvol_workspace_size(int32_t n, int32_t r) {
+  if (r < 1 || r > 128 || n < r) return 0;
+  return dry_bytes([&](Exec& ex) { maxvol(ex, nullptr, n, r, 1e-2, 1, nullptr); });
+}
+
+tt_status tt_maxvol(const double* U, int32_t n, int32_t r, double delta, int32_t max_iter, int32_t* I, void* ws,
+                    size_t ws_bytes, void* stream) {
+  if (!U || !I || r < 1 || r > 128 || n < r || !(delta >= 0.0) || max_iter < 0) return TT_ERR_ARG;
+  return run_call(ws, ws_bytes, stream, [&](Exec& ex) {
+    maxvol(ex, U, n, r, delta, max_iter, I);
+    return TT_OK;
+  });
+}
+
 size_t tt_reciprocal_workspace_size(int32_t n1, int32_t n2, int32_t rank_in, int32_t rank_cap) {
   if (n1 < 1 || n2 < 1 || rank_in < 1 || rank_cap < 1) return 0;
   return dry_bytes([&](Exec& ex) {

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <algorithm>
 #include <type_traits>
+#include <cooperative_groups.h>
 
 #include "tt_common.cuh"
 
@@ -139,7 +140,24 @@ void gemm(Exec& ex, int M, int N, int K, Real alpha, const Real* A, long ars, lo
           Real beta, Real* C, long ldc) {
   if (M <= 0 || N <= 0) return;
   const int tiles = ceil_div(M, GB) * ceil_div(N, GB);
-  int nsplit = std::max(1, std::min(ceil_div(2 * sm_count(), tiles), ceil_div(std::max(K, 1), 64)));
+  // K split: the CTA count tiles * nsplit is balanced over the SMs (FP64
+  // work per SM ~ the CTAs it holds, and one CTA already keeps an SM's FP64
+  // pipes busy), so nsplit maximises tiles * nsplit / (SMs * ceil(tiles *
+  // nsplit / SMs)) among the splits with K chunks of at least 64, at least
+  // two CTAs per SM where K allows (latency of the tile loads), fewer
+  // splits on ties
+  const int sms = sm_count(), kmax = std::max(1, K / 64);
+  int nsplit = 1;
+  double best = -1.0;
+  for (int ns = 1; ns <= std::min(kmax, 64); ++ns) {
+    const long ctas = (long)tiles * ns;
+    const double util = (double)ctas / ((double)sms * (double)((ctas + sms - 1) / sms));
+    const double score = util * std::min(1.0, (double)ctas / (2.0 * sms));
+    if (score > best + 1e-9) {
+      best = score;
+      nsplit = ns;
+    }
+  }
   int kchunk = ceil_div(ceil_div(std::max(K, 1), nsplit), GK) * GK;
   nsplit = ceil_div(std::max(K, 1), kchunk);
   Scope sc(*ex.ar);
@@ -1689,6 +1707,272 @@ __global__ void __launch_bounds__(MV_THREADS) k_maxvol(const double* __restrict_
   if (threadIdx.x == 0 && it >= max_iter) atomicOr(status, DEV_MAXVOL_NOCONV);
 }
 
+// ---------------------------------------------------------------- maxvol over a cluster
+// The same three phases as k_maxvol with the n rows split over the CTAs of a
+// thread-block cluster, each CTA keeping its rows of the working matrix (FP32,
+// row-major) in its own shared memory: the single-CTA kernel streams the whole
+// n x r matrix through one SM's L2 path on every pivot step, the cluster
+// scans shared memory on up to 8 SMs.  Per pivot step each CTA publishes its
+// best local candidate and a copy of that row in a double-buffered slot, one
+// cluster barrier makes the slots visible, and every CTA reads all slots
+// through distributed shared memory and takes the same (largest value,
+// smallest index) decision, so all CTAs run the same number of steps and
+// barriers.  The r x r inverse is formed redundantly (identically) by every
+// CTA.  Row choices and tie rules are those of k_maxvol.
+constexpr int MVC_THREADS = 512;
+constexpr int MVC_MAX_CLUSTER = 8;
+
+struct MvcLayout {
+  int nc;  // rows per CTA
+  size_t off_flag, off_col, off_prow, off_P, off_slot, bytes;
+  int slot_floats;  // per slot: value, index (as bits), row of r values
+};
+__host__ __device__ inline MvcLayout mvc_layout(int n, int r, int cl) {
+  MvcLayout L;
+  L.nc = (n + cl - 1) / cl;
+  size_t o = (size_t)L.nc * r * 4;  // rows
+  L.off_col = o;
+  o += (size_t)L.nc * 4;  // saved pivot column (phase 3)
+  L.off_prow = o;
+  o += (size_t)r * 4;  // pivot row
+  L.off_P = o;
+  o += (size_t)2 * r * r * 4;  // [P | I] for Gauss-Jordan
+  L.off_slot = o;
+  L.slot_floats = 2 + r;
+  o += (size_t)2 * L.slot_floats * 4;  // two candidate slots
+  L.off_flag = o;
+  o += (size_t)L.nc;  // free-row flags
+  L.bytes = (o + 15) & ~(size_t)15;
+  return L;
+}
+
+__device__ __forceinline__ bool mv_better(float v, long idx, float bv, long bidx) {
+  return v > bv || (v == bv && idx < bidx);
+}
+
+__global__ void __launch_bounds__(MVC_THREADS) k_maxvol_cluster(const double* __restrict__ U, int n, int r,
+                                                                double delta, int max_iter, int* I,
+                                                                unsigned* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cl = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const MvcLayout L = mvc_layout(n, r, cl);
+  float* W = reinterpret_cast<float*>(smraw);  // nc x r, row-major
+  float* col = reinterpret_cast<float*>(smraw + L.off_col);
+  float* prow = reinterpret_cast<float*>(smraw + L.off_prow);
+  float* P = reinterpret_cast<float*>(smraw + L.off_P);  // r x 2r, column-major
+  float* slot = reinterpret_cast<float*>(smraw + L.off_slot);
+  unsigned char* freeflag = smraw + L.off_flag;
+  __shared__ double rv[33];
+  __shared__ long ri[33];
+  __shared__ int piv[128];
+  __shared__ int s_win, s_gp;
+  __shared__ float s_inv;
+  const int row0 = me * L.nc, nloc = max(0, min(L.nc, n - row0));
+  for (int t = threadIdx.x; t < nloc * r; t += blockDim.x) {
+    const int i = t / r, j = t - i * r;
+    W[t] = (float)U[(size_t)(row0 + i) + (size_t)j * n];
+  }
+  for (int i = threadIdx.x; i < L.nc; i += blockDim.x) freeflag[i] = 1;
+  __syncthreads();
+  // publish this CTA's candidate (value, global index, a copy of local row
+  // li) in slot buffer b; li < 0: no candidate
+  auto publish = [&](int b, float v, long gidx, int li) {
+    float* s = slot + (size_t)b * L.slot_floats;
+    if (threadIdx.x == 0) {
+      s[0] = v;
+      reinterpret_cast<int*>(s)[1] = (int)gidx;
+    }
+    if (li >= 0)
+      for (int j = threadIdx.x; j < r; j += blockDim.x) s[2 + j] = W[(size_t)li * r + j];
+  };
+  // after the cluster barrier: the winning slot's CTA (s_win) and index (s_gp)
+  auto decide = [&](int b) {
+    if (threadIdx.x == 0) {
+      float bv = -2.0f;
+      long bi = 0x7fffffffffffffffL;
+      int win = 0;
+      for (int q = 0; q < cl; ++q) {
+        const float* rs = cluster.map_shared_rank(slot + (size_t)b * L.slot_floats, q);
+        const float v = rs[0];
+        const long idx = reinterpret_cast<const int*>(rs)[1];
+        if (mv_better(v, idx, bv, bi)) {
+          bv = v;
+          bi = idx;
+          win = q;
+        }
+      }
+      s_win = win;
+      s_gp = (int)bi;
+    }
+    __syncthreads();
+  };
+  // 1. partial-pivoting row choice
+  for (int k = 0; k < r; ++k) {
+    ArgMax best{-1.0, 0x7fffffffffffffffL};
+    for (int i = threadIdx.x; i < nloc; i += blockDim.x)
+      if (freeflag[i]) {
+        double v = fabs((double)W[(size_t)i * r + k]);
+        if (!(v >= 0.0)) {
+          v = 0.0;
+          atomicOr(status, DEV_NONFINITE);
+        }
+        best = amax_better(best, ArgMax{v, (long)i});
+      }
+    best = block_argmax(best, rv, ri);
+    const int li = best.v >= 0.0 ? (int)best.idx : -1;
+    const int sb = k & 1;  // slot of publication number k
+    publish(sb, li >= 0 ? (float)best.v : -1.0f, li >= 0 ? (long)(row0 + li) : 0x7fffffffL, li);
+    cluster.sync();
+    decide(sb);
+    const int win = s_win, pr = s_gp;
+    {
+      const float* rs = cluster.map_shared_rank(slot + (size_t)sb * L.slot_floats, win);
+      for (int j = threadIdx.x; j < r; j += blockDim.x) prow[j] = rs[2 + j];
+    }
+    if (threadIdx.x == 0) {
+      piv[k] = pr;
+      if (win == me) freeflag[pr - row0] = 0;
+    }
+    __syncthreads();
+    const float pv = prow[k];
+    if (pv != 0.0f && k + 1 < r) {
+      const float ipv = (float)(1.0 / (double)pv);
+      const int w = r - k - 1;
+      for (int t = threadIdx.x; t < nloc * w; t += blockDim.x) {
+        const int i = t / w, c = k + 1 + (t - i * w);
+        if (freeflag[i]) {
+          const float f = W[(size_t)i * r + k] * ipv;
+          W[(size_t)i * r + c] = fmaf(-f, prow[c], W[(size_t)i * r + c]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // 2. B = U P^{-1}, P = U[piv, :]: Gauss-Jordan on [P | I] (every CTA)
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int i = t % r, j = t / r;
+    P[i + (size_t)j * r] = (float)U[piv[i] + (size_t)j * n];
+    P[i + (size_t)(j + r) * r] = (i == j) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) {
+      int bsel = k;
+      double bv = fabs((double)P[k + (size_t)k * r]);
+      for (int i = k + 1; i < r; ++i) {
+        const double v = fabs((double)P[i + (size_t)k * r]);
+        if (v > bv) {
+          bv = v;
+          bsel = i;
+        }
+      }
+      s_gp = bsel;
+    }
+    __syncthreads();
+    const int pr = s_gp;
+    if (pr != k)
+      for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) {
+        const float a = P[k + (size_t)c * r];
+        P[k + (size_t)c * r] = P[pr + (size_t)c * r];
+        P[pr + (size_t)c * r] = a;
+      }
+    __syncthreads();
+    const float d = P[k + (size_t)k * r];
+    if (threadIdx.x == 0) s_inv = d != 0.0f ? (float)(1.0 / (double)d) : 0.0f;
+    __syncthreads();
+    if (d != 0.0f)
+      for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) P[k + (size_t)c * r] *= s_inv;
+    __syncthreads();
+    for (int t = threadIdx.x; t < r * 2 * r; t += blockDim.x) {
+      const int i = t % r, c = t / r;
+      if (i != k && c != k)
+        P[i + (size_t)c * r] = fmaf(-P[i + (size_t)k * r], P[k + (size_t)c * r], P[i + (size_t)c * r]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x)
+      if (i != k) P[i + (size_t)k * r] = 0.0f;
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nloc * r; t += blockDim.x) {
+    const int i = t / r, j = t - i * r;
+    float s = 0.0f;
+    for (int l = 0; l < r; ++l) s = fmaf((float)U[(size_t)(row0 + i) + (size_t)l * n], P[l + (size_t)(j + r) * r], s);
+    W[t] = s;
+  }
+  __syncthreads();
+  // 3. swap rows while some |B_ij| > 1 + delta (ties: smallest i r + j)
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    ArgMax best{-1.0, 0x7fffffffffffffffL};
+    for (int t = threadIdx.x; t < nloc * r; t += blockDim.x) {
+      const int i = t / r, j = t - i * r;
+      best = amax_better(best, ArgMax{fabs((double)W[t]), (long)(row0 + i) * r + j});
+    }
+    best = block_argmax(best, rv, ri);
+    const int li = best.v >= 0.0 ? (int)(best.idx / r) - row0 : -1;
+    // publications continue the numbering of phase 1 (r of them), so two
+    // uses of one slot are always a cluster barrier apart
+    const int sb = (r + it) & 1;
+    publish(sb, li >= 0 ? (float)best.v : -1.0f, li >= 0 ? best.idx : 0x7fffffffL, li);
+    cluster.sync();
+    decide(sb);
+    const int win = s_win, gidx = s_gp;
+    {
+      const float* rs = cluster.map_shared_rank(slot + (size_t)sb * L.slot_floats, win);
+      if (threadIdx.x == 0) s_inv = rs[0];
+      for (int j = threadIdx.x; j < r; j += blockDim.x) prow[j] = rs[2 + j];
+    }
+    __syncthreads();
+    if ((double)s_inv <= 1.0 + delta) break;  // the same decision in every CTA
+    const int bi = gidx / r, bj = gidx - bi * r;
+    for (int i = threadIdx.x; i < nloc; i += blockDim.x) col[i] = W[(size_t)i * r + bj];
+    __syncthreads();
+    const float ipiv = (float)(1.0 / (double)prow[bj]);
+    for (int t = threadIdx.x; t < nloc * r; t += blockDim.x) {
+      const int i = t / r, j = t - i * r;
+      const float rj = prow[j] - (j == bj ? 1.0f : 0.0f);
+      W[t] = fmaf(-col[i] * ipiv, rj, W[t]);
+    }
+    if (threadIdx.x == 0) piv[bj] = bi;
+    __syncthreads();
+  }
+  if (me == 0) {
+    for (int k = threadIdx.x; k < r; k += blockDim.x) I[k] = piv[k];
+    if (threadIdx.x == 0 && it >= max_iter) atomicOr(status, DEV_MAXVOL_NOCONV);
+  }
+  // no CTA leaves while another may still read its slots
+  cluster.sync();
+}
+
+// whether an 8-CTA cluster of k_maxvol_cluster with the shared-memory budget
+// can be resident on this device (checked once per process)
+static bool maxvol_cluster_ok() {
+  static const bool ok = [] {
+    if (smem_attr_once_impl(reinterpret_cast<const void*>(k_maxvol_cluster)) != cudaSuccess) return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(MVC_MAX_CLUSTER);
+    cfg.blockDim = dim3(MVC_THREADS);
+    cfg.dynamicSmemBytes = QR_SMEM_MAX;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = MVC_MAX_CLUSTER;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, k_maxvol_cluster, &cfg);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    return nc > 0;
+  }();
+  return ok;
+}
+
 void maxvol(Exec& ex, const double* U, int n, int r, double delta, int max_iter, int* I) {
   TT_REQUIRE(r >= 1 && r <= 128 && n >= r, TT_ERR_ARG);
   using T = float;
@@ -1697,6 +1981,35 @@ void maxvol(Exec& ex, const double* U, int n, int r, double delta, int max_iter,
   T* B = ex.ar->get<T>((size_t)n * r);
   T* P = ex.ar->get<T>((size_t)2 * r * r);
   if (ex.dry) return;
+  // cluster form: the smallest power-of-two cluster (at most 8 CTAs) that
+  // leaves each CTA at most 8192 entries, when it fits shared memory;
+  // TT_MAXVOL_CLUSTER=0 (environment, read once) keeps the single-CTA
+  // kernel, which makes the same choices (tests compare the two)
+  static const bool allow = [] {
+    const char* e = std::getenv("TT_MAXVOL_CLUSTER");
+    return !(e && std::atoi(e) == 0);
+  }();
+  int cl = 1;
+  while (cl < MVC_MAX_CLUSTER && (long)ceil_div(n, cl) * r > 8192) cl *= 2;
+  const MvcLayout L = mvc_layout(n, r, cl);
+  if (allow && r <= 128 && L.bytes <= QR_SMEM_MAX && maxvol_cluster_ok()) {
+    smem_attr_once(k_maxvol_cluster);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(MVC_THREADS);
+    cfg.dynamicSmemBytes = L.bytes;
+    cfg.stream = ex.s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    TT_KERNEL(ex, K_MAXVOL, 3.0 * n * (double)r * r, (8.0 + 2.0 * sizeof(T)) * n * (double)r,
+              TT_CUDA(cudaLaunchKernelEx(&cfg, k_maxvol_cluster, U, n, r, delta, max_iter, I, ex.dev_status)));
+    return;
+  }
   const size_t smem = (size_t)n;
   TT_REQUIRE(smem <= 200 * 1024, TT_ERR_ARG);
   smem_attr_once(k_maxvol<T>);

@@ -477,6 +477,7 @@ double effective_tol(const Exec& ex, double tol) {
 
 static void finish_counts(Exec& ex, int k, int cap, int rin) {
   ex.rounds++;
+  ex.last_rank = k;
   if (k == cap && rin > cap) ex.cap_hits++;
 }
 

@@ -265,6 +265,7 @@ struct TraceRec {
   // the node's own work: host syncs, range-finder attempts, small SVDs and
   // the sum of their sizes, cross sweeps, kernel launches
   long long syncs, qb, svd, svd_p, sweeps, launches;
+  int rank;  // kept rank of the worker's latest rounding
 };
 
 struct Tally {
@@ -331,7 +332,7 @@ struct TaskGraph::Impl {
       trace.push_back(TraceRec{n.name, worker, t0, now_us(), after.syncs - before.syncs,
                                after.qb_attempts - before.qb, after.svd_calls - before.svd,
                                after.svd_p - before.svd_p, after.cross_sweeps - before.sweeps,
-                               after.launches - before.launches});
+                               after.launches - before.launches, after.last_rank});
     cv.notify_all();
   }
   void write_trace() {
@@ -345,8 +346,8 @@ struct TaskGraph::Impl {
       std::fprintf(f,
                    "{\"graph\": %lld, \"name\": \"%s\", \"worker\": %d, \"t0_us\": %.1f, \"t1_us\": %.1f, "
                    "\"syncs\": %lld, \"qb\": %lld, \"svd\": %lld, \"svd_p\": %lld, \"sweeps\": %lld, "
-                   "\"launches\": %lld}\n",
-                   g, r.name, r.worker, r.t0, r.t1, r.syncs, r.qb, r.svd, r.svd_p, r.sweeps, r.launches);
+                   "\"launches\": %lld, \"rank\": %d}\n",
+                   g, r.name, r.worker, r.t0, r.t1, r.syncs, r.qb, r.svd, r.svd_p, r.sweeps, r.launches, r.rank);
     std::fclose(f);
   }
   void run_serial();

@@ -144,6 +144,7 @@ struct Exec {
   long long rounds = 0, qb_attempts = 0, qb_uncertified = 0, syncs = 0;
   long long jacobi_sweeps = 0, cross_calls = 0, cross_sweeps = 0;
   long long taylor_iters = 0, cap_hits = 0;
+  int last_rank = 0;  // kept rank of the latest rounding (node trace)
   long long svd_calls = 0, svd_p = 0, svd_pd = 0, svd_sweeps = 0;
   long long learned_calls = 0, learned_accepted = 0;
   long long launches = 0;           // kernels this context launched

@@ -58,6 +58,8 @@ def test_workspace_queries_without_gpu(lib):
         for split in (0, 1):
             assert lib.tt_contract_workspace_size(prec, split, 1024, 112, 3072) > 0
     assert lib.tt_contract_workspace_size(9, 1, 1024, 112, 3072) == 0
+    assert lib.tt_maxvol_workspace_size(12288, 13) > 0
+    assert lib.tt_maxvol_workspace_size(8, 13) == 0 and lib.tt_maxvol_workspace_size(512, 129) == 0
     assert lib.tt_contract_workspace_size(capi.TT_TF32, 1, 0, 112, 3072) == 0
 
 
