@@ -1088,31 +1088,53 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     return;
   }
   const double thr = defl * defl * fro2;
-  // ---- 1. QR with column pivoting of M^T, deflated
+  // ---- 1. QR with column pivoting of M^T, deflated.  The pivot search
+  // runs on FP32 copies of the squared column norms scaled by 1/||M||_F^2
+  // (it only picks a column); the stop test sums the FP64 norms whenever the
+  // FP32 sum of the trailing norms is within a factor of 4 of the threshold.
+  // The trailing columns are updated by warps that each own Cp columns and,
+  // per column, the rows i = rp (mod Kp) below the pivot row, inner products
+  // finished by shuffles.
+  const double ifro2 = fro2 > 0.0 ? 1.0 / fro2 : 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) cnf[j] = (float)(cn[j] * ifro2);
+  __syncthreads();
+  const float thrf = (float)(thr * ifro2);
+  // lane (rp, cp) = (lane mod Kp, lane / Kp): a half warp holds two columns'
+  // eight consecutive row classes, so it touches at most two banks' worth of
+  // columns whatever p
+  constexpr int Kp = 8, Cp = 32 / Kp;
+  const int rp = lane % Kp, cp = lane / Kp;
   int pd = p;
   for (int k = 0; k < p; ++k) {
     if (w == 0) {
-      double best = -1.0, trail = 0.0;
+      float best = -1.0f, tf = 0.0f;
       int bj = k;
       for (int j = k + lane; j < p; j += 32) {
-        trail += cn[j];
-        if (cn[j] > best) {
-          best = cn[j];
+        tf += cnf[j];
+        if (cnf[j] > best) {
+          best = cnf[j];
           bj = j;
         }
       }
-      trail = warp_sum(trail);
+      tf = warp_sum(tf);
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
         if (ob > best || (ob == best && oj < bj)) {
           best = ob;
           bj = oj;
         }
       }
+      int stop = 0;
+      double trail = 0.0;
+      if (!(tf > 4.0f * thrf)) {  // near the threshold: decide in FP64
+        for (int j = k + lane; j < p; j += 32) trail += cn[j];
+        trail = warp_sum(trail);
+        stop = trail <= thr ? 1 : 0;
+      }
       if (lane == 0) {
         s_jmax = bj;
-        s_stop = (trail <= thr) ? 1 : 0;
+        s_stop = stop;
         s_trail = trail;
       }
     }
@@ -1138,6 +1160,9 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
         const double c0 = cn0[k];
         cn0[k] = cn0[jm];
         cn0[jm] = c0;
+        const float cf = cnf[k];
+        cnf[k] = cnf[jm];
+        cnf[jm] = cf;
       }
     }
     __syncthreads();
@@ -1159,37 +1184,49 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     }
     __syncthreads();
     const double tau = s_tau;
-    for (int c = k + 1 + w; c < p; c += nw) {
-      double* cc = A + (size_t)c * p;
+    const int nact = p - k - 1;
+    const int i0 = k + 1 + ((rp - k - 1) & (Kp - 1));  // first row > k of this lane's class
+    for (int base = w * Cp; base < nact; base += nw * Cp) {  // warp-uniform
+      const int c = k + 1 + base + cp;
+      const bool colv = base + cp < nact;
+      double* ccol = A + (size_t)(colv ? c : k) * p;
       if (tau != 0.0) {
         double d = 0.0;
-        for (int i = k + 1 + lane; i < p; i += 32) d = fma(col[i], cc[i], d);
-        d = warp_sum(d) + cc[k];
-        const double f = tau * d;
-        if (lane == 0) cc[k] -= f;
-        for (int i = k + 1 + lane; i < p; i += 32) cc[i] = fma(-f, col[i], cc[i]);
+        if (colv)
+          for (int i = i0; i < p; i += Kp) d = fma(col[i], ccol[i], d);
+        for (int o = 1; o < Kp; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        const double f = colv ? tau * (d + ccol[k]) : 0.0;
+        __syncwarp();  // the column's lanes have read ccol[k]
+        if (colv) {
+          if (rp == 0) ccol[k] -= f;
+          for (int i = i0; i < p; i += Kp) ccol[i] = fma(-f, col[i], ccol[i]);
+        }
+        __syncwarp();
       }
-      __syncwarp();
-      // trailing norm below row k: downdate by the new row-k entry (one lane),
-      // recompute exactly only after heavy cancellation (as pivoted Householder
-      // QR codes do)
+      // trailing norm below row k: downdate by the new row-k entry (one lane
+      // per column), recompute exactly only after heavy cancellation (as
+      // pivoted Householder QR codes do)
       double s2 = 0.0;
       int redo = 0;
-      if (lane == 0) {
-        s2 = fma(-cc[k], cc[k], cn[c]);
+      if (colv && rp == 0) {
+        s2 = fma(-ccol[k], ccol[k], cn[c]);
         redo = (s2 <= 1e-6 * cn0[c]) ? 1 : 0;
       }
-      redo = __shfl_sync(0xffffffffu, redo, 0);
-      if (redo) {
+      redo = __shfl_sync(0xffffffffu, redo, cp * Kp);
+      if (__any_sync(0xffffffffu, redo)) {
         double e = 0.0;
-        for (int i = k + 1 + lane; i < p; i += 32) e = fma(cc[i], cc[i], e);
-        e = warp_sum(e);
-        if (lane == 0) {
+        if (colv && redo)
+          for (int i = i0; i < p; i += Kp) e = fma(ccol[i], ccol[i], e);
+        for (int o = 1; o < Kp; o <<= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (colv && redo && rp == 0) {
           s2 = e;
           cn0[c] = e;
         }
       }
-      if (lane == 0) cn[c] = s2 > 0.0 ? s2 : 0.0;
+      if (colv && rp == 0) {
+        cn[c] = s2 > 0.0 ? s2 : 0.0;
+        cnf[c] = (float)(cn[c] * ifro2);
+      }
     }
     __syncthreads();
   }
@@ -1468,9 +1505,12 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     const int r = t % p, c = t / p;
     US[piv[r] + (size_t)c * p] = c < pd ? A[r + (size_t)order[c] * p] : 0.0;
   }
-  // Vout = Q [V; 0]: one thread per column (a warp instruction then serves
-  // 32 columns), reflectors applied last-to-first to Z in shared memory,
-  // row-major with an odd stride so that the columns' threads hit distinct banks
+  // Vout = Q [V; 0]: reflectors applied last-to-first to Z (p x k in
+  // shared memory, row-major with an odd row length).  Each warp owns Cq
+  // columns of Z and, per column, the rows i = rq (mod Kq) (lane (rq, cq) =
+  // (lane / Cq, lane mod Cq)); a reflector's inner products are finished by
+  // shuffles and no block barrier is needed, the reflectors and their
+  // factors being first copied into shared memory.
   __syncthreads();  // A (L V) has been read into US: reuse it for Z
   const int kz = (k < p) ? (k | 1) : k;  // Z must fit in A's p x p doubles
   double* Z = A;                          // p x kz
@@ -1478,24 +1518,48 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     const int r = t / k, c = t % k;
     Z[(size_t)r * kz + c] = (c < pd && r < pd) ? J[r + (size_t)order[c] * pd] : ((c >= pd && r == c) ? 1.0 : 0.0);
   }
+  __syncthreads();  // J (V) has been read into Z: reuse it for the reflectors
+  double* hvs = J;  // p x pd, column kk holds reflector kk below row kk
+  for (int t = threadIdx.x; t < p * pd; t += blockDim.x) hvs[t] = HV[t];
+  for (int t = threadIdx.x; t < pd; t += blockDim.x) cn0[t] = htau[t];
   __syncthreads();
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    for (int kk = pd - 1; kk >= 0; --kk) {
-      const double tk = htau[kk];
-      if (tk == 0.0) continue;
-      const double* hv = HV + (size_t)kk * p;
-      double d0 = Z[(size_t)kk * kz + c], d1 = 0.0, d2 = 0.0, d3 = 0.0;
-      int r = kk + 1;
-      for (; r + 3 < p; r += 4) {
-        d0 = fma(hv[r], Z[(size_t)r * kz + c], d0);
-        d1 = fma(hv[r + 1], Z[(size_t)(r + 1) * kz + c], d1);
-        d2 = fma(hv[r + 2], Z[(size_t)(r + 2) * kz + c], d2);
-        d3 = fma(hv[r + 3], Z[(size_t)(r + 3) * kz + c], d3);
+  {
+    // lanes per column: the fewest FP64 instructions on the busiest SM
+    // sub-partition over the pd reflectors (rows kk..p-1, p/2 on average)
+    int Kq = 32;
+    long bestq = 0x7fffffffffffffffL;
+    for (int kq = 2; kq <= 32; kq <<= 1) {
+      const int cpw = 32 / kq, warps = (k + cpw - 1) / cpw;
+      if (warps > nw) continue;
+      int lg = 0;
+      while ((1 << lg) < kq) ++lg;
+      const long cost = (long)((warps + 3) / 4) * (2L * ((p / 2 + kq - 1) / kq) + lg + 3);
+      if (cost < bestq) {
+        bestq = cost;
+        Kq = kq;
       }
-      for (; r < p; ++r) d0 = fma(hv[r], Z[(size_t)r * kz + c], d0);
-      const double d = ((d0 + d1) + (d2 + d3)) * tk;
-      Z[(size_t)kk * kz + c] -= d;
-      for (r = kk + 1; r < p; ++r) Z[(size_t)r * kz + c] = fma(-d, hv[r], Z[(size_t)r * kz + c]);
+    }
+    const int Cq = 32 / Kq, rq = lane / Cq, cq = lane % Cq, c = w * Cq + cq;
+    if (w * Cq < k) {  // warp-uniform
+      const bool colv = c < k;
+      for (int kk = pd - 1; kk >= 0; --kk) {
+        const double tk = cn0[kk];
+        if (tk == 0.0) continue;
+        const double* hv = hvs + (size_t)kk * p;
+        const bool top = rq == (kk & (Kq - 1));
+        const int i0 = kk + 1 + ((rq - kk - 1) & (Kq - 1));
+        double d = 0.0;
+        if (colv) {
+          if (top) d = Z[(size_t)kk * kz + c];
+          for (int i = i0; i < p; i += Kq) d = fma(hv[i], Z[(size_t)i * kz + c], d);
+        }
+        for (int o = Cq; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        d *= tk;
+        if (colv) {
+          if (top) Z[(size_t)kk * kz + c] -= d;
+          for (int i = i0; i < p; i += Kq) Z[(size_t)i * kz + c] = fma(-d, hv[i], Z[(size_t)i * kz + c]);
+        }
+      }
     }
   }
   __syncthreads();
