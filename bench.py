@@ -61,6 +61,8 @@ def parse():
                     help="a second workload timed in the same run, reported under 'secondary' ('' for none)")
     ap.add_argument("--tol", type=float, default=None,
                     help="truncation tolerance instead of the workload's (same-error comparisons of the forms)")
+    ap.add_argument("--tile-shape", type=int, default=0,
+                    help="TSQR tile shape of the roundings (an index of api.tile_shapes(); 0 the default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     return ap.parse_args()
@@ -304,6 +306,8 @@ def measure(args, wname, world, local, with_cpu, with_l2):
                        flux=args.flux)
         if args.pivots == "learned":
             s.set_pivot_net(net)
+        if args.tile_shape:
+            s.set_tile_shape(args.tile_shape)
         return s
 
     # ---- device-timed region
@@ -371,6 +375,7 @@ def measure(args, wname, world, local, with_cpu, with_l2):
                   "roundings": st_all["rounds"], "range_finder_attempts": st_all["qb_attempts"],
                   "range_finder_uncertified": st_all["qb_uncertified"], "svd_calls": st_all["svd_calls"],
                   "svd_mean_p": st_all["svd_p_sum"] / max(st_all["svd_calls"], 1),
+                  "svd_mean_deflated_p": st_all["svd_pd_sum"] / max(st_all["svd_calls"], 1),
                   "svd_mean_sweeps": st_all["svd_sweeps_sum"] / max(st_all["svd_calls"], 1),
                   "window": "all steps of the timed solver (warm-up, timed, profile)"}
     total_ms = sum(step_ms)
@@ -432,7 +437,7 @@ def measure(args, wname, world, local, with_cpu, with_l2):
     res = {"value": value, "ms_per_step": total_ms / args.steps,
            "config": {"workload": wname, "n": n, "scheme": w["scheme"], "eqn": w["eqn"],
                       "precision": args.precision, "pivots": args.pivots, "flux": args.flux, "rank_cap": cap,
-                      "tol": w["tol"],
+                      "tol": w["tol"], "tile_shape": args.tile_shape,
                       "steps_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
                       "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
            "step_ms": [round(x, 2) for x in step_ms],
@@ -555,6 +560,10 @@ def run_ensemble(args):
     # candidate; workers = 1 with inner tasks is the plain one-instance path
     cands = (1, 8, 16)
     (bw, bi), rates = b.tune(workers=cands, steps_per_trial=1, with_rates=True)
+    # then each member's TSQR tile shape (leaf rows, merge fan-in), one step
+    # per shape with the chosen concurrency
+    tile_of, tile_rates = b.tune_tiles(steps_per_trial=1, rounds=1)
+    shapes = api.tile_shapes()
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -588,7 +597,7 @@ def run_ensemble(args):
             insts2.append((q0, dict(eqn=w["eqn"], scheme=w["scheme"], n=w["n"], dt=p["dt"], tol=w["tol"],
                                     rank_cap=w["cap"], g=p["g"], H=p["H"], f=p["f"], seed=0)))
         b2 = api.Batch(insts2, precision=prec, workers=1, inner_tasks=True)
-        b2.step(2 * len(cands))
+        b2.step(2 * len(cands) + len(shapes))
         torch.cuda.synchronize()
         e0.record(stream)
         b2.step(args.steps)
@@ -602,7 +611,7 @@ def run_ensemble(args):
     # rank's time: the job's throughput, counting every member once
     value = cells * args.steps / (total_ms / 1e3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": 2 * len(cands), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": 2 * len(cands) + len(shapes), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
             "config": {"workload": args.workload, "instances": count, "cells": cells, "precision": prec,
                        "schemes": {s: sum(w["scheme"] == s for w in ws_all) for s in ("up3", "up5", "weno5")},
@@ -612,7 +621,10 @@ def run_ensemble(args):
                        "parallelism": f"ensemble sharded over {world} GPU(s) (LPT on N cap^2), no exchange",
                        "rank0_members": len(ws)},
             "tuned": {"workers": bw, "inner_tasks": bi,
-                      "trial_rates": {f"w{w}_{'inner' if i else 'flat'}": r for (w, i), r in rates.items()}},
+                      "trial_rates": {f"w{w}_{'inner' if i else 'flat'}": r for (w, i), r in rates.items()},
+                      "tile_shapes": {f"leaf{lm}_fanin{fi or 'default'}": {"members": tile_of.count(k),
+                                                                            "trial_rate": tile_rates[k]}
+                                      for k, (lm, fi) in enumerate(shapes)}},
             "plain_same_steps": ({"ms_per_step": plain_ms / args.steps, "speedup": plain_ms / total_ms,
                                   "what": "workers=1 with stage tasks (the single-instance path), same steps"}
                                  if plain_ms else None),

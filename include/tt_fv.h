@@ -230,6 +230,17 @@ tt_status tt_fv_set_boundary(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwave
 tt_status tt_fv_stats_get(tt_fv_ctx* ctx, tt_fv_stats* out);
 void tt_fv_destroy(tt_fv_ctx* ctx);
 
+/* TSQR tile shapes of the rounding (Sec. 3.2's QR of the cores, done as a
+ * tree of leaf QRs and merges): shape s is (leaf_mult[s], fanin[s]), the leaf
+ * rows as a multiple of max(64, rank rounded up to 32) and the largest merge
+ * fan-in (0: the default 4), both capped by shared memory.  tt_tile_shapes
+ * writes up to `max` shapes (either array may be NULL) and returns their
+ * number; shape 0, (2, 0), is the default of every entry point.  tt_fv_workspace_size covers every shape.
+ * tt_fv_set_tile_shape switches a solver's roundings to shape `shape`
+ * (results change at round-off level only); TT_ERR_ARG for an unknown shape. */
+int32_t tt_tile_shapes(int32_t* leaf_mult, int32_t* fanin, int32_t max);
+tt_status tt_fv_set_tile_shape(tt_fv_ctx* ctx, int32_t shape);
+
 /* Enable (1) or disable (0) CUDA-event timing of every kernel launch of the
  * context, accumulated per kernel class.  While enabled, the stage's
  * independent tasks run one after another on the context stream (so a
@@ -328,6 +339,13 @@ tt_status tt_fv_pivot_take(tt_fv_ctx* ctx, float* X, float* y, int64_t rows);
  *   reports it (the trial steps advance the ensemble); rates (may be NULL,
  *   2*ncand doubles) receives each trial's cell updates per second, index
  *   2*c + inner.
+ * tt_fv_batch_tune_tiles times every TSQR tile shape of tt_tile_shapes
+ *   (rounds x steps_per_trial real batch steps per shape, the shapes
+ *   interleaved round by round, all instances on the same shape in a trial)
+ *   and gives each instance the shape of its own least step time; shape_out
+ *   (may be NULL, count int32) receives each instance's shape, rates (may be
+ *   NULL, one double per shape) the batch's cell updates per second under
+ *   each shape.  The trial steps advance the ensemble.
  * tt_fv_batch_get / tt_fv_batch_stats_get: as tt_fv_get / tt_fv_stats_get for
  *   instance i.  Errors: TT_ERR_ARG, TT_ERR_OOM (workspace too small), or the
  *   first error an instance returned. */
@@ -339,6 +357,8 @@ tt_status tt_fv_batch_configure(tt_fv_batch* b, int32_t workers, int32_t inner_t
 tt_status tt_fv_batch_step(tt_fv_batch* b, int32_t nsteps);
 tt_status tt_fv_batch_tune(tt_fv_batch* b, const int32_t* workers, int32_t ncand, int32_t steps_per_trial,
                            int32_t* best_workers, int32_t* best_inner, double* rates);
+tt_status tt_fv_batch_tune_tiles(tt_fv_batch* b, int32_t steps_per_trial, int32_t rounds, int32_t* shape_out,
+                                 double* rates);
 tt_status tt_fv_batch_get(tt_fv_batch* b, int32_t i, tt2 q_out[3]);
 tt_status tt_fv_batch_stats_get(tt_fv_batch* b, int32_t i, tt_fv_stats* out);
 void tt_fv_batch_destroy(tt_fv_batch* b);

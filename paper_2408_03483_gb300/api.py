@@ -181,6 +181,16 @@ def launch_count():
     return int(C.load().tt_launch_count())
 
 
+def tile_shapes():
+    """The TSQR tile shapes (leaf-row multiple, largest merge fan-in; 0 is the
+    default fan-in) a solver can be switched to; shape 0 is the default."""
+    lib = C.load()
+    K = lib.tt_tile_shapes(None, None, 0)
+    lm, fi = (ctypes.c_int32 * K)(), (ctypes.c_int32 * K)()
+    lib.tt_tile_shapes(lm, fi, K)
+    return [(lm[k], fi[k]) for k in range(K)]
+
+
 class Solver:
     """tt_fv_init / tt_fv_stage / tt_fv_step / tt_fv_get over a torch workspace."""
 
@@ -243,6 +253,10 @@ class Solver:
 
     def profile(self, enable=True):
         C.check("tt_fv_profile", self.lib.tt_fv_profile(self.h, 1 if enable else 0))
+
+    def set_tile_shape(self, shape):
+        """Use TSQR tile shape `shape` (an index into tile_shapes())."""
+        C.check("tt_fv_set_tile_shape", self.lib.tt_fv_set_tile_shape(self.h, shape))
 
     def kernel_profile(self, reset=False):
         arr = (C.tt_kernel_prof * len(C.TT_K_NAMES))()
@@ -331,6 +345,18 @@ class Batch:
             tab = {(w, bool(i)): rates[2 * c + i] for c, w in enumerate(workers) for i in (0, 1)}
             return (bw.value, bool(bi.value)), tab
         return bw.value, bool(bi.value)
+
+    def tune_tiles(self, steps_per_trial=1, rounds=1):
+        """Autotune each instance's TSQR tile shape on real steps (every shape
+        of tile_shapes() timed rounds x steps_per_trial steps); returns the
+        per-instance shape indices and {shape: batch cell updates/s}."""
+        K = self.lib.tt_tile_shapes(None, None, 0)
+        n = len(self.shapes)
+        out = (ctypes.c_int32 * n)()
+        rates = (ctypes.c_double * K)()
+        C.check("tt_fv_batch_tune_tiles",
+                self.lib.tt_fv_batch_tune_tiles(self.h, steps_per_trial, rounds, out, rates))
+        return list(out), {k: rates[k] for k in range(K)}
 
     def get(self, i):
         n, cap = self.shapes[i]

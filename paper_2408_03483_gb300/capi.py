@@ -102,6 +102,8 @@ SIGNATURES = {
     "tt_fv_set_boundary": (ctypes.c_int, [_vp, _P(tt_wave), _i32, _d]),
     "tt_fv_stats_get": (ctypes.c_int, [_vp, _P(tt_fv_stats)]),
     "tt_fv_destroy": (None, [_vp]),
+    "tt_tile_shapes": (_i32, [_P(_i32), _P(_i32), _i32]),
+    "tt_fv_set_tile_shape": (ctypes.c_int, [_vp, _i32]),
     "tt_fv_profile": (ctypes.c_int, [_vp, _i32]),
     "tt_fv_kernel_profile": (ctypes.c_int, [_vp, _P(tt_kernel_prof), _i32]),
     "tt_launch_count": (ctypes.c_uint64, []),
@@ -122,6 +124,7 @@ SIGNATURES = {
     "tt_fv_batch_configure": (ctypes.c_int, [_vp, _i32, _i32]),
     "tt_fv_batch_step": (ctypes.c_int, [_vp, _i32]),
     "tt_fv_batch_tune": (ctypes.c_int, [_vp, _P(_i32), _i32, _i32, _P(_i32), _P(_i32), _P(_d)]),
+    "tt_fv_batch_tune_tiles": (ctypes.c_int, [_vp, _i32, _i32, _P(_i32), _P(_d)]),
     "tt_fv_batch_get": (ctypes.c_int, [_vp, _i32, _P(tt2)]),
     "tt_fv_batch_stats_get": (ctypes.c_int, [_vp, _i32, _P(tt_fv_stats)]),
     "tt_fv_batch_destroy": (None, [_vp]),

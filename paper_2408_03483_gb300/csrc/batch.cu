@@ -8,8 +8,9 @@
 // kernels of `workers` instances at once -- the single-instance path leaves
 // most SMs idle between its rank-dependent launches.  The worker count and
 // whether each instance also runs its own independent stage tasks
-// concurrently are the tunables; tt_fv_batch_tune times candidates on real
-// steps and keeps the fastest.
+// concurrently are tunables; tt_fv_batch_tune times candidates on real
+// steps and keeps the fastest.  tt_fv_batch_tune_tiles picks each instance's
+// TSQR tile shape (leaf rows, merge fan-in) from the same kind of trials.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -199,6 +200,42 @@ tt_status tt_fv_batch_tune(tt_fv_batch* b, const int32_t* workers, int32_t ncand
   if (best_workers) *best_workers = bw;
   if (best_inner) *best_inner = bi ? 1 : 0;
   return r;
+}
+
+tt_status tt_fv_batch_tune_tiles(tt_fv_batch* b, int32_t steps_per_trial, int32_t rounds, int32_t* shape_out,
+                                 double* rates) {
+  if (!b || steps_per_trial < 1 || rounds < 1) return TT_ERR_ARG;
+  const int K = tt_tile_shapes(nullptr, nullptr, 0), n = (int)b->inst.size();
+  const double cells = (double)std::accumulate(b->cells.begin(), b->cells.end(), 0LL);
+  // the rounds interleave the shapes, so that the ranks' growth over the
+  // trial steps does not favour the shapes timed first
+  std::vector<double> cost((size_t)n * K, 0.0), sec(K, 0.0);
+  for (int r = 0; r < rounds; ++r)
+    for (int k = 0; k < K; ++k) {
+      for (tt_fv_ctx* c : b->inst) {
+        const tt_status e = tt_fv_set_tile_shape(c, k);
+        if (e != TT_OK) return e;
+      }
+      const auto t0 = std::chrono::steady_clock::now();
+      for (int st = 0; st < steps_per_trial; ++st) {
+        const tt_status e = batch_step(b);
+        if (e != TT_OK) return e;
+        for (int i = 0; i < n; ++i) cost[(size_t)i * K + k] += b->cost[i];
+      }
+      if (cudaStreamSynchronize(b->user) != cudaSuccess) return TT_ERR_CUDA;
+      sec[k] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+  if (rates)
+    for (int k = 0; k < K; ++k) rates[k] = cells * steps_per_trial * rounds / std::max(sec[k], 1e-9);
+  for (int i = 0; i < n; ++i) {
+    int best = 0;
+    for (int k = 1; k < K; ++k)
+      if (cost[(size_t)i * K + k] < cost[(size_t)i * K + best]) best = k;
+    const tt_status e = tt_fv_set_tile_shape(b->inst[i], best);
+    if (e != TT_OK) return e;
+    if (shape_out) shape_out[i] = best;
+  }
+  return TT_OK;
 }
 
 tt_status tt_fv_batch_get(tt_fv_batch* b, int32_t i, tt2 q_out[3]) {

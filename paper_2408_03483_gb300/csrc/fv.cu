@@ -64,6 +64,7 @@ struct Reciprocal {
   TT* y = nullptr;
   double tol = 0.0, x_avg = 1.0, err = 1.0;
   int cap = 0, max_iter = 0, prio = 0, it = 0;
+  bool urgent = false;  // the chain is on the stage's critical path
   TT xt, dy[2];
   int reader[2] = {-1, -1};  // the y update that reads dy[b]
   int last_y = -1;
@@ -77,7 +78,7 @@ static void taylor_y(Reciprocal& R, int b, int dy_node) {
   const int yk = R.G->add(
       "taylor_y", R.prio,
       [&R, b](Exec& cx) { round_sum(cx, {Term{1.0, *R.y}, Term{1.0, R.dy[b]}}, R.tol, R.cap, *R.y); },
-      {dy_node, R.last_y});
+      {dy_node, R.last_y}, false, R.urgent);
   R.reader[b] = yk;
   R.last_y = yk;
 }
@@ -108,7 +109,7 @@ static void taylor_dy(Reciprocal& R, int k, int prev) {
           R.G->release(R.done);
         }
       },
-      {prev, R.reader[b]});
+      {prev, R.reader[b]}, false, R.urgent);
 }
 
 // Adds the nodes of y = 1/x (x and y preallocated; x's cores are read when
@@ -116,7 +117,7 @@ static void taylor_dy(Reciprocal& R, int k, int prev) {
 // the result; R must outlive G.run(), after which R.noconv and R.it hold the
 // stop-test outcome and the iteration count.
 static int reciprocal_nodes(TaskGraph& G, Exec& ex, const TT& x, double tol, int cap, int max_iter, TT& y,
-                            int after, int prio, Reciprocal& R) {
+                            int after, int prio, Reciprocal& R, bool urgent = false) {
   const int n1 = x.n1, n2 = x.n2;
   TT_REQUIRE(y.cap >= cap && y.n1 == n1 && y.n2 == n2, TT_ERR_ARG);
   R.G = &G;
@@ -126,6 +127,7 @@ static int reciprocal_nodes(TaskGraph& G, Exec& ex, const TT& x, double tol, int
   R.cap = cap;
   R.max_iter = max_iter;
   R.prio = prio;
+  R.urgent = urgent;
   R.xt = alloc_tt(*ex.ar, n1, n2, cap);
   R.dy[0] = alloc_tt(*ex.ar, n1, n2, cap);
   R.dy[1] = alloc_tt(*ex.ar, n1, n2, cap);
@@ -136,7 +138,7 @@ static int reciprocal_nodes(TaskGraph& G, Exec& ex, const TT& x, double tol, int
         scaled_copy(cx, R.y->a, R.y->a, (long)R.y->n1 * R.y->r, 1.0 / R.x_avg);
         R.noconv = R.err > R.tol;
       },
-      {}, true);
+      {}, true, urgent);
   G.add(
       "taylor_init", prio,
       [&R](Exec& cx) {
@@ -158,7 +160,7 @@ static int reciprocal_nodes(TaskGraph& G, Exec& ex, const TT& x, double tol, int
           R.G->release(R.done);
         }
       },
-      {after});
+      {after}, false, urgent);
   return R.done;
 }
 
@@ -871,7 +873,7 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
           face[d][c][k] = G.add("weno_face", c == 0 ? 100 : 90, [&, d, c, k](Exec& cx) {
             weno_side(S, cx, Q[c], d, c, k, seed, k == 0 ? qm[d][c] : qp[d][c]);
             mark(0);
-          });
+          }, {}, false, c == 0);
   } else {
     for (int d = 0; d < 2; ++d)
       for (int c = 0; c < 3; ++c) faces_linear(S, ex, Q[c], d, qm[d][c], qp[d][c]);
@@ -895,12 +897,12 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
       const int fx = G.add("llf_flux_cross", 85, [&, d](Exec& cx) {
         flux_by_cross(S, cx, qm[d], qp[d], d, seed + 64u * d + 44u, Fh[d]);
         mark(2);
-      }, deps);
+      }, deps, false, true);
       for (int c = 0; c < 3; ++c)
         qd_node[d][c] = G.add("quad_difference", 40, [&, d, c](Exec& cx) {
           quad_and_difference(S, cx, Fh[d][c], d, D[d][c]);
           mark(3);
-        }, {fx});
+        }, {fx}, false, true);
     }
   } else {
   for (int d = 0; d < 2; ++d) {
@@ -925,7 +927,7 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
     const int k = d == 0 ? 1 : 2;  // the normal momentum hu (x) or hv (y)
     for (int sd = 0; sd < 2; ++sd) {
       const int rdone = reciprocal_nodes(G, ex, side(d, sd)[0], tol, cap, mi, rh[d][sd], face[d][0][sd], 80,
-                                         R[d][sd]);
+                                         R[d][sd], true);
       hh_node[d][sd] = G.add("h_o_h", 60, [&, d, sd](Exec& cx) {
         round_hadamard(cx, side(d, sd)[0], side(d, sd)[0], tol, cap, hh[d][sd]);
         mark(1);
@@ -934,7 +936,7 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
         vel_node[d][sd][comp] = G.add("velocity", 75, [&, d, sd, comp](Exec& cx) {
           round_hadamard(cx, side(d, sd)[1 + comp], rh[d][sd], tol, cap, comp == 0 ? uu[d][sd] : vv[d][sd]);
           mark(1);
-        }, {rdone, face[d][1 + comp][sd]});
+        }, {rdone, face[d][1 + comp][sd]}, false, true);
       flux_node[d][sd][0] = -1;
       for (int comp = 1; comp < 3; ++comp)
         flux_node[d][sd][comp] = G.add("flux", 70, [&, d, sd, comp, k](Exec& cx) {
@@ -949,7 +951,7 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
             round_hadamard(cx, qn, vel, tol, cap, F[d][sd][comp]);
           }
           mark(1);
-        }, {vel_node[d][sd][comp - 1], face[d][k][sd], comp == k ? hh_node[d][sd] : -1});
+        }, {vel_node[d][sd][comp - 1], face[d][k][sd], comp == k ? hh_node[d][sd] : -1}, false, true);
     }
     lam_node[d] = G.add("llf_lambda", 85, [&, d](Exec& cx) {
       // lambda moves little from one stage to the next: the previous
@@ -1000,11 +1002,11 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
       const int llf = G.add("llf_combine", 40, [&, d, c, k](Exec& cx) {
         llf_combine(S, cx, c == 0 ? qm[d][k] : F[d][0][c], c == 0 ? qp[d][k] : F[d][1][c], ld[d][c], Fh[d][c]);
         mark(2);
-      }, deps);
+      }, deps, false, true);
       qd_node[d][c] = G.add("quad_difference", 40, [&, d, c](Exec& cx) {
         quad_and_difference(S, cx, Fh[d][c], d, D[d][c]);
         mark(3);
-      }, {llf});
+      }, {llf}, false, true);
     }
   }
   }  // products form
@@ -1018,7 +1020,7 @@ static void forward_euler_graph(Solver& S, Exec& ex, const TT Q[3], unsigned see
       if (source_tt(S, cx, c, src)) terms.push_back(Term{p.dt, src});
       round_sum(cx, terms, S.tol_u[c], cap, out[c]);
       mark(4);
-    }, {qd_node[0][c], qd_node[1][c]});
+    }, {qd_node[0][c], qd_node[1][c]}, false, true);
   G.run();
   for (int d = 0; d < 2; ++d)
     for (int sd = 0; sd < 2; ++sd) TT_REQUIRE(!R[d][sd].noconv, TT_ERR_NOCONV);
@@ -1229,7 +1231,13 @@ static void alloc_lambda_prev(Solver& S) {
   S.lam_prev[1] = alloc_tt(S.ar, S.nq * S.p.nx, S.p.ny, S.p.rank_cap);
 }
 
-static size_t solver_bytes(const tt_fv_params* p, bool with_state) {
+// TSQR tile shapes a solver may be switched to after its workspace is sized
+// (tt_fv_set_tile_shape): (leaf-row multiple, largest merge fan-in; 0 = the
+// default, 4 from p = 32 up).  Entry 0 is the default of every Exec.
+static const int kTiles[][2] = {{2, 0}, {1, 0}, {1, 2}, {2, 2}, {3, 0}, {4, 0}};
+constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
+
+static size_t solver_bytes_tiles(const tt_fv_params* p, int tile) {
   // dry run of one stage at the rank cap
   Solver S;
   S.p = *p;
@@ -1238,6 +1246,8 @@ static size_t solver_bytes(const tt_fv_params* p, bool with_state) {
   int hi[16];
   double hd[16];
   setup_exec(ex, S.ar, nullptr, 0, nullptr, hi, hd, true);
+  ex.qr_leaf_mult = kTiles[tile][0];
+  ex.qr_fanin = kTiles[tile][1];
   ex.precision = p->precision;
   MlpNet dry_net;  // sizing pass: the proposal's scratch is counted, no weight is read
   if (p->pivots == TT_PIVOT_LEARNED) ex.pivot_net = &dry_net;
@@ -1248,18 +1258,42 @@ static size_t solver_bytes(const tt_fv_params* p, bool with_state) {
       S.Qn[c].r = S.Qs[c].r = p->rank_cap;
     }
     alloc_lambda_prev(S);
-    (void)with_state;
     for (int st = 0; st < 3; ++st) run_stage(S, ex, st);
   } catch (const Error&) {
     return 0;
   }
-  const size_t peak = S.ar.peak;
+  return S.ar.peak;
+}
+
+// the largest footprint over the tile shapes, so that any of them fits
+static size_t solver_bytes(const tt_fv_params* p) {
+  size_t peak = 0;
+  for (int t = 0; t < kNumTiles; ++t) {
+    const size_t b = solver_bytes_tiles(p, t);
+    if (b == 0) return 0;
+    peak = std::max(peak, b);
+  }
   return peak + peak / 2 + (64u << 20);
 }
 
 size_t tt_fv_workspace_size(const tt_fv_params* p) {
   if (!valid_params(p)) return 0;
-  return solver_bytes(p, true);
+  return solver_bytes(p);
+}
+
+int32_t tt_tile_shapes(int32_t* leaf_mult, int32_t* fanin, int32_t max) {
+  for (int t = 0; t < kNumTiles && t < max; ++t) {
+    if (leaf_mult) leaf_mult[t] = kTiles[t][0];
+    if (fanin) fanin[t] = kTiles[t][1];
+  }
+  return kNumTiles;
+}
+
+tt_status tt_fv_set_tile_shape(tt_fv_ctx* ctx, int32_t shape) {
+  if (!ctx || shape < 0 || shape >= kNumTiles) return TT_ERR_ARG;
+  ctx->S.ex.qr_leaf_mult = kTiles[shape][0];
+  ctx->S.ex.qr_fanin = kTiles[shape][1];
+  return TT_OK;
 }
 
 tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws_bytes, void* stream,

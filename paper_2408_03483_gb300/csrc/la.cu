@@ -24,6 +24,14 @@ __device__ __forceinline__ Real warp_sum(Real v) {
   return v;
 }
 
+// Sum over aligned groups of H lanes (H a power of two <= 32); every lane of
+// the warp must take part.
+template <typename Real>
+__device__ __forceinline__ Real group_sum(Real v, int H) {
+  for (int o = H >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Block-wide sum (all threads get the result).  `red` holds >= 33 doubles.
 __device__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -611,18 +619,18 @@ static int qr_fanin_cap() {
   return v;
 }
 static int apply_merge_lanes(int p) { return std::min(32, pow2_ceil(p)); }
-static int qr_merge_fanin(int p, size_t elem) {
+static int qr_merge_fanin(int p, size_t elem, int cap) {
   const MergeShape ms = merge_shape(p);
   const size_t per = (size_t)p * ms.ld * elem;
   const size_t per_apply = ((size_t)p * p + (size_t)AM_WARPS * p * (32 / apply_merge_lanes(p))) * elem;
   const int g = int(std::min(QR_SMEM_MAX / per, QR_SMEM_MAX / per_apply));
-  return std::max(2, std::min(g, p >= 32 ? qr_fanin_cap() : 16));
+  return std::max(2, std::min(g, p >= 32 ? (cap >= 2 ? cap : qr_fanin_cap()) : 16));
 }
 
 // rows of a leaf: the leaf QR holds mb x ld entries, the leaf application mb x
 // (p + 2 AM_WARPS) (its reflectors and four warps' two columns)
-static int qr_leaf_rows(int p, size_t elem) {
-  int mb = std::max(((p + 31) / 32) * 32, 64);
+static int qr_leaf_rows(int p, size_t elem, int mult) {
+  int mb = std::max(((p + 31) / 32) * 32, 64) * std::max(1, std::min(mult, 8));
   const size_t row = std::max<size_t>(merge_shape(p).ld, (size_t)p + 2 * AM_WARPS) * elem;
   const int lim = int((QR_SMEM_MAX - (size_t)p * elem) / row);
   return std::max(std::min(mb, lim), p);
@@ -634,7 +642,7 @@ template <typename Real>
 static void tsqr_run(Exec& ex, int nj, const void* const* X, const int* x64, const int* m, const long* ldx, int p,
                      QRTreeT<Real>* const* t) {
   TT_REQUIRE(p >= 1 && p <= 112, TT_ERR_ARG);
-  const int mb = qr_leaf_rows(p, sizeof(Real)), g = qr_merge_fanin(p, sizeof(Real));
+  const int mb = qr_leaf_rows(p, sizeof(Real), ex.qr_leaf_mult), g = qr_merge_fanin(p, sizeof(Real), ex.qr_fanin);
   Real* R[2] = {nullptr, nullptr};
   int n[2] = {1, 1};
   LeafJob<Real> lj[2] = {};
@@ -1023,6 +1031,7 @@ constexpr int SVD_MAX_SWEEPS = 30;
 constexpr int SVD_MIXED_MIN = 8;      // FP32 pre-rotation from this deflated rank up
 constexpr int SVD_MIXED_SWEEPS = 6;   // cap of FP32 sweeps
 constexpr float SVD_MIXED_TOL = 1e-5f;  // FP32 phase: rotate while |g| > 1e-5 sqrt(a b)
+constexpr int SVD_CHOLQR_MIN = 60;      // deflated rank from which V0 is orthonormalised by Cholesky QR
 
 __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restrict__ Min, int p, double tol, int cap,
                                                           double defl, double* US, double* Vout, double* sig,
@@ -1036,7 +1045,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   __shared__ int piv[128];
   __shared__ int order[128];
   __shared__ double s_tau, s_fro2, s_trail;
-  __shared__ int s_jmax, s_stop, s_rot, s_k, s_tmax;
+  __shared__ int s_jmax, s_stop, s_rot, s_k, s_tmax, s_bad;
   __shared__ float cnf[128];
   __shared__ double gam[64], rc_c[64], rc_s[64];  // per pair of a round (q/2 <= 56)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1247,6 +1256,10 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) J[t] = ((t % pd) == (t / pd)) ? 1.0 : 0.0;
   __syncthreads();
   const int q = pd + (pd & 1);
+  // a round's q/2 pairs take one warp each up to one pair per warp, and half
+  // a warp each beyond (p > 64), so that a round is one pass of the warps
+  const int H = (q / 2 > nw) ? 16 : 32, PW = 32 / H;
+  const int sub = lane & (H - 1), lead = lane & ~(H - 1);
   // ---- 2a. FP32 pre-rotation.  One-sided Jacobi sweeps on an FP32 copy of L
   // (FP32 instructions cost 1/64 of FP64 ones here) orthogonalise its columns
   // to FP32 level; the accumulated rotations V0 are re-orthonormalised in FP64
@@ -1273,19 +1286,27 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
       if (threadIdx.x == 0) s_rot = 0;
       __syncthreads();
       for (int step = 0; step < q - 1; ++step) {
-        for (int pr = w; pr < q / 2; pr += nw) {
-          const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
-          const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
-          if (i >= pd || j >= pd) continue;
-          float* ci = Af + (size_t)i * p;
-          float* cj = Af + (size_t)j * p;
+        // PW pairs per warp, H lanes each (the loop is warp-uniform: the
+        // halves of a warp finish their sums by shuffles together)
+        for (int base = w * PW; base < q / 2; base += nw * PW) {
+          const int pr = base + lane / H;
+          int i = 0, j = 0;
+          bool ok = pr < q / 2;
+          if (ok) {
+            i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
+            j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
+            ok = i < pd && j < pd;
+          }
+          float* ci = Af + (size_t)(ok ? i : 0) * p;
+          float* cj = Af + (size_t)(ok ? j : 0) * p;
           float ga = 0.0f;
-          for (int r = lane; r < p; r += 32) ga = fmaf(ci[r], cj[r], ga);
-          ga = warp_sum(ga);
-          const float al = cnf[i], be = cnf[j];
-          if (!(ga * ga > epsf * epsf * al * be)) continue;
+          if (ok)
+            for (int r = sub; r < p; r += H) ga = fmaf(ci[r], cj[r], ga);
+          ga = group_sum(ga, H);
+          const float al = ok ? cnf[i] : 0.0f, be = ok ? cnf[j] : 0.0f;
+          const bool rot = ok && (ga * ga > epsf * epsf * al * be);
           float c = 1.0f, sn = 0.0f;
-          if (lane == 0) {
+          if (rot && sub == 0) {
             const float dd = be - al;
             const float t = (dd >= 0.0f ? 2.0f * ga : -2.0f * ga) / (fabsf(dd) + sqrtf(fmaf(dd, dd, 4.0f * ga * ga)));
             c = rsqrtf(fmaf(t, t, 1.0f));
@@ -1293,50 +1314,125 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
             cnf[i] = fmaf(-t, ga, al);
             cnf[j] = fmaf(t, ga, be);
           }
-          c = __shfl_sync(0xffffffffu, c, 0);
-          sn = __shfl_sync(0xffffffffu, sn, 0);
-          for (int r = lane; r < p; r += 32) {
-            const float x = ci[r], y = cj[r];
-            ci[r] = c * x - sn * y;
-            cj[r] = sn * x + c * y;
+          c = __shfl_sync(0xffffffffu, c, lead);
+          sn = __shfl_sync(0xffffffffu, sn, lead);
+          if (rot) {
+            for (int r = sub; r < p; r += H) {
+              const float x = ci[r], y = cj[r];
+              ci[r] = c * x - sn * y;
+              cj[r] = sn * x + c * y;
+            }
+            float* vi = Jf + (size_t)i * pd;
+            float* vj = Jf + (size_t)j * pd;
+            for (int r = sub; r < pd; r += H) {
+              const float x = vi[r], y = vj[r];
+              vi[r] = c * x - sn * y;
+              vj[r] = sn * x + c * y;
+            }
+            if (sub == 0) s_rot = 1;
           }
-          float* vi = Jf + (size_t)i * pd;
-          float* vj = Jf + (size_t)j * pd;
-          for (int r = lane; r < pd; r += 32) {
-            const float x = vi[r], y = vj[r];
-            vi[r] = c * x - sn * y;
-            vj[r] = sn * x + c * y;
-          }
-          if (lane == 0) s_rot = 1;
         }
         __syncthreads();
       }
       if (s_rot == 0) break;
       __syncthreads();
     }
-    // V0 in FP64 (global scratch), two Newton-Schulz steps back into J
-    for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) Vg[t] = (double)Jf[t];
-    __syncthreads();
-    for (int it = 0; it < 2; ++it) {
-      const double* Vs = (it == 0) ? Vg : J;
-      double* Vd = (it == 0) ? J : Vg;
-      for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) {  // G = V^T V
-        const int a = t % pd, b = t / pd;
-        double g = 0.0;
-        for (int r = 0; r < pd; ++r) g = fma(Vs[r + (size_t)a * pd], Vs[r + (size_t)b * pd], g);
-        Gg[t] = g;
-      }
+    // V0 made orthonormal in FP64: by two Newton-Schulz steps
+    // V <- V (3 I - V^T V) / 2 up to pd = SVD_CHOLQR_MIN, above by a Cholesky QR
+    // (a quarter of the FP64 work, but 2 pd block barriers and a sequential
+    // substitution, which only pay off for large pd)
+    if (pd < SVD_CHOLQR_MIN) {
+      for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) Vg[t] = (double)Jf[t];
       __syncthreads();
-      for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) {  // Vd = 1.5 V - 0.5 V G
-        const int r = t % pd, b = t / pd;
-        double u = 0.0;
-        for (int a = 0; a < pd; ++a) u = fma(Vs[r + (size_t)a * pd], Gg[a + (size_t)b * pd], u);
-        Vd[t] = fma(-0.5, u, 1.5 * Vs[t]);
+      for (int it = 0; it < 2; ++it) {
+        const double* Vs = (it == 0) ? Vg : J;
+        double* Vd = (it == 0) ? J : Vg;
+        for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) {  // G = V^T V
+          const int a = t % pd, b = t / pd;
+          double g = 0.0;
+          for (int r = 0; r < pd; ++r) g = fma(Vs[r + (size_t)a * pd], Vs[r + (size_t)b * pd], g);
+          Gg[t] = g;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) {  // Vd = 1.5 V - 0.5 V G
+          const int r = t % pd, b = t / pd;
+          double u = 0.0;
+          for (int a = 0; a < pd; ++a) u = fma(Vs[r + (size_t)a * pd], Gg[a + (size_t)b * pd], u);
+          Vd[t] = fma(-0.5, u, 1.5 * Vs[t]);
+        }
+        __syncthreads();
       }
+      for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) J[t] = Vg[t];
+      __syncthreads();
+    } else {
+      // V0 in FP64, made orthonormal by a Cholesky QR: V0 is orthogonal to
+      // FP32 round-off, so G = V0^T V0 = I + O(1e-7) is perfectly conditioned
+      // and Q = V0 C^-T (G = C C^T, C lower) is orthonormal to FP64 round-off,
+      // for a quarter of the FP64 work of two Newton-Schulz steps.  V0 goes to
+      // global scratch twice: row-major in Vg (lanes along a row form G) and
+      // column-major in Tg (lanes along a column solve for Q in place).
+      for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) {
+        const int r = t % pd, a = t / pd;
+        const double v = (double)Jf[t];
+        Vg[a + (size_t)r * pd] = v;
+        Tg[t] = v;
+      }
+      if (threadIdx.x == 0) s_bad = 0;
+      __syncthreads();
+      // lower triangle of G into J: a warp per column b, lanes over rows a >= b
+      for (int b = w; b < pd; b += nw)
+        for (int a = b + lane; a < pd; a += 32) {
+          double g0 = 0.0, g1 = 0.0;
+          int r = 0;
+          for (; r + 1 < pd; r += 2) {
+            g0 = fma(Vg[a + (size_t)r * pd], Vg[b + (size_t)r * pd], g0);
+            g1 = fma(Vg[a + (size_t)(r + 1) * pd], Vg[b + (size_t)(r + 1) * pd], g1);
+          }
+          if (r < pd) g0 = fma(Vg[a + (size_t)r * pd], Vg[b + (size_t)r * pd], g0);
+          J[a + (size_t)b * pd] = g0 + g1;
+        }
+      __syncthreads();
+      // right-looking Cholesky over G's lower triangle: column k of C is
+      // column k of G over sqrt(G[k][k]); 1 / C[k][k] is kept in cn0[k] (J's
+      // diagonal is not read again)
+      for (int k = 0; k < pd; ++k) {
+        const double gkk = J[k + (size_t)k * pd];
+        const bool okk = gkk > 0.5;  // a diagonal far from 1: V0 is not near-orthogonal
+        const double ick = okk ? rsqrt(gkk) : 1.0;
+        for (int i = k + 1 + threadIdx.x; i < pd; i += blockDim.x) J[i + (size_t)k * pd] *= ick;
+        if (threadIdx.x == 0) {
+          cn0[k] = ick;
+          if (!okk) s_bad = 1;
+        }
+        __syncthreads();
+        for (int j = k + 1 + w; j < pd; j += nw) {
+          const double cj = J[j + (size_t)k * pd];
+          for (int i = j + lane; i < pd; i += 32) J[i + (size_t)j * pd] = fma(-J[i + (size_t)k * pd], cj, J[i + (size_t)j * pd]);
+        }
+        __syncthreads();
+      }
+      // Q C^T = V0 by forward substitution along each row, one thread per row
+      // (four partial sums shorten the FP64 dependency chain)
+      if (!s_bad)
+        for (int r = threadIdx.x; r < pd; r += blockDim.x)
+          for (int c = 0; c < pd; ++c) {
+            double s0 = Tg[r + (size_t)c * pd], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int j = 0;
+            for (; j + 3 < c; j += 4) {
+              s0 = fma(-Tg[r + (size_t)j * pd], J[c + (size_t)j * pd], s0);
+              s1 = fma(-Tg[r + (size_t)(j + 1) * pd], J[c + (size_t)(j + 1) * pd], s1);
+              s2 = fma(-Tg[r + (size_t)(j + 2) * pd], J[c + (size_t)(j + 2) * pd], s2);
+              s3 = fma(-Tg[r + (size_t)(j + 3) * pd], J[c + (size_t)(j + 3) * pd], s3);
+            }
+            for (; j < c; ++j) s0 = fma(-Tg[r + (size_t)j * pd], J[c + (size_t)j * pd], s0);
+            Tg[r + (size_t)c * pd] = ((s0 + s1) + (s2 + s3)) * cn0[c];
+          }
+      __syncthreads();
+      // no usable pre-rotation: V0 = I and L stays as it is
+      for (int t = threadIdx.x; t < pd * pd; t += blockDim.x)
+        J[t] = s_bad ? (((t % pd) == (t / pd)) ? 1.0 : 0.0) : Tg[t];
       __syncthreads();
     }
-    for (int t = threadIdx.x; t < pd * pd; t += blockDim.x) J[t] = Vg[t];
-    __syncthreads();
     for (int t = threadIdx.x; t < p * pd; t += blockDim.x) {  // T = L V0
       const int r = t % p, b = t / p;
       double u = 0.0;
@@ -1364,17 +1460,24 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     }
     __syncthreads();
     for (int step = 0; step < q - 1; ++step) {
-      // (a) one warp per pair: the off-diagonal g = <c_i, c_j>
-      for (int pr = w; pr < q / 2; pr += nw) {
-        const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
-        const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
-        if (i >= pd || j >= pd) continue;
-        const double* ci = A + (size_t)i * p;
-        const double* cj = A + (size_t)j * p;
+      // (a) H lanes per pair: the off-diagonal g = <c_i, c_j>
+      for (int base = w * PW; base < q / 2; base += nw * PW) {
+        const int pr = base + lane / H;
+        int i = 0, j = 0;
+        bool ok = pr < q / 2;
+        if (ok) {
+          i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
+          j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
+          ok = i < pd && j < pd;
+        }
         double ga = 0.0;
-        for (int r = lane; r < p; r += 32) ga = fma(ci[r], cj[r], ga);
-        ga = warp_sum(ga);
-        if (lane == 0) gam[pr] = ga;
+        if (ok) {
+          const double* ci = A + (size_t)i * p;
+          const double* cj = A + (size_t)j * p;
+          for (int r = sub; r < p; r += H) ga = fma(ci[r], cj[r], ga);
+        }
+        ga = group_sum(ga, H);
+        if (ok && sub == 0) gam[pr] = ga;
       }
       __syncthreads();
       // (b) warp 0, one lane per pair: the rotations of the whole round (an
@@ -1417,8 +1520,9 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
         }
       }
       __syncthreads();
-      // (c) one warp per pair: apply the rotation to L and V
-      for (int pr = w; pr < q / 2; pr += nw) {
+      // (c) H lanes per pair: apply the rotation to L and V (no shuffles:
+      // the lanes of a pair go their own way)
+      for (int pr = w * PW + lane / H; pr < q / 2; pr += nw * PW) {
         const double sn = rc_s[pr];
         if (sn == 0.0) continue;
         const double c = rc_c[pr];
@@ -1426,14 +1530,14 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
         const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
         double* ci = A + (size_t)i * p;
         double* cj = A + (size_t)j * p;
-        for (int r = lane; r < p; r += 32) {
+        for (int r = sub; r < p; r += H) {
           const double x = ci[r], y = cj[r];
           ci[r] = c * x - sn * y;
           cj[r] = sn * x + c * y;
         }
         double* vi = J + (size_t)i * pd;
         double* vj = J + (size_t)j * pd;
-        for (int r = lane; r < pd; r += 32) {
+        for (int r = sub; r < pd; r += H) {
           const double x = vi[r], y = vj[r];
           vi[r] = c * x - sn * y;
           vj[r] = sn * x + c * y;

@@ -66,6 +66,17 @@ cudaStream_t StreamPool::stream(size_t i) {
   return streams[i];
 }
 
+cudaStream_t StreamPool::stream_hi(size_t i) {
+  while (streams_hi.size() <= i) {
+    int least = 0, greatest = 0;
+    TT_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    cudaStream_t s;
+    TT_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
+    streams_hi.push_back(s);
+  }
+  return streams_hi[i];
+}
+
 cudaEvent_t StreamPool::event(size_t i) {
   while (events.size() <= i) {
     cudaEvent_t e;
@@ -93,6 +104,7 @@ void host_wait(Exec& ex) { TT_CUDA(cudaStreamSynchronize(ex.s)); }
 
 StreamPool::~StreamPool() {
   for (cudaStream_t s : streams) cudaStreamDestroy(s);
+  for (cudaStream_t s : streams_hi) cudaStreamDestroy(s);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
   if (pinned) cudaFreeHost(pinned);
 }
@@ -140,6 +152,8 @@ static void child_exec(const Exec& parent, Exec& c, Arena* a, cudaStream_t s, Pr
   c.ar = a;
   c.dev_status = parent.dev_status;
   c.precision = parent.precision;
+  c.qr_leaf_mult = parent.qr_leaf_mult;
+  c.qr_fanin = parent.qr_fanin;
   c.pivot_net = parent.pivot_net;
   c.pivot_rec = parent.pivot_rec;
   c.h_pinned = hi;
@@ -242,6 +256,7 @@ namespace {
 struct GNode {
   const char* name = "";
   int prio = 0;
+  bool urgent = false;  // GPU work on the worker's high-priority stream
   TaskGraph::Fn fn;
   std::vector<int> in;   // every dependency (the GPU-side waits)
   std::vector<int> out;  // dependents still counting on this node
@@ -276,8 +291,20 @@ struct Tally {
 };
 
 // Events of graph nodes are taken from the stream pool above those that
-// parallel_tasks uses (one per task plus the start event).
+// parallel_tasks uses (one per task plus the start event); a worker that
+// moves between its two streams orders them by event kSwitchEvent0 + worker.
+constexpr size_t kSwitchEvent0 = 32;
 constexpr size_t kGraphEvent0 = 64;
+
+// TT_STREAM_PRIORITY=0 (environment, read once) queues urgent nodes on the
+// ordinary streams too, for comparison.
+bool stream_priority_on() {
+  static const bool v = [] {
+    const char* e = std::getenv("TT_STREAM_PRIORITY");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
 
 thread_local int t_self = -1;
 
@@ -358,7 +385,7 @@ TaskGraph::TaskGraph(Exec& ex, int workers) : im(new Impl(ex, workers)) {}
 TaskGraph::~TaskGraph() { delete im; }
 int TaskGraph::self() { return t_self; }
 
-int TaskGraph::add(const char* name, int priority, Fn fn, const std::vector<int>& deps, bool hold) {
+int TaskGraph::add(const char* name, int priority, Fn fn, const std::vector<int>& deps, bool hold, bool urgent) {
   std::lock_guard<std::mutex> lk(im->mu);
   const int id = (int)im->nodes.size();
   for (int d : deps) TT_REQUIRE(d < id, TT_ERR_ARG);
@@ -366,6 +393,7 @@ int TaskGraph::add(const char* name, int priority, Fn fn, const std::vector<int>
   GNode& n = im->nodes.back();
   n.name = name;
   n.prio = priority;
+  n.urgent = urgent;
   n.fn = std::move(fn);
   n.pending = hold ? 1 : 0;
   for (int d : deps) {
@@ -464,14 +492,25 @@ void TaskGraph::Impl::run_parallel() {
     child_exec(ex, w.ex, &w.ar, ex.pool->stream((size_t)i), &w.prof, w.hi, w.hd, (size_t)i + 1);
     TT_CUDA(cudaStreamWaitEvent(w.ex.s, start, 0));
   }
+  const bool prio = stream_priority_on() && workers <= int(kGraphEvent0 - kSwitchEvent0);
+  // created here: the pool's vectors are not touched by the worker threads
+  std::vector<cudaStream_t> s_hi(workers, nullptr);
+  std::vector<cudaEvent_t> s_sw(workers, nullptr);
+  if (prio)
+    for (int i = 0; i < workers; ++i) {
+      s_hi[i] = ex.pool->stream_hi((size_t)i);
+      s_sw[i] = ex.pool->event(kSwitchEvent0 + (size_t)i);
+    }
   auto loop = [&](int wi) {
     GWorker& w = wk[wi];
+    cudaStream_t s_lo = w.ex.s;
     std::vector<cudaEvent_t> waits;
     for (;;) {
       int id;
       Fn fn;
       cudaEvent_t ev;
       double t0;
+      bool urg;
       {
         std::unique_lock<std::mutex> lk(mu);
         cv.wait(lk, [&] { return !ready.empty() || err != TT_OK || remaining == 0 || running == 0; });
@@ -487,6 +526,7 @@ void TaskGraph::Impl::run_parallel() {
         GNode& n = nodes[id];
         fn = std::move(n.fn);
         ev = n.ev;
+        urg = prio && n.urgent;
         waits.clear();
         for (int d : n.in) waits.push_back(nodes[d].ev);
         t0 = now_us();
@@ -494,6 +534,14 @@ void TaskGraph::Impl::run_parallel() {
       tt_status st = TT_OK;
       const Tally before(w.ex);
       try {
+        // the worker's two streams share its arena slice: the stream taken
+        // next waits for everything queued on the other one
+        const cudaStream_t want = urg ? s_hi[wi] : s_lo;
+        if (want != w.ex.s) {
+          TT_CUDA(cudaEventRecord(s_sw[wi], w.ex.s));
+          TT_CUDA(cudaStreamWaitEvent(want, s_sw[wi], 0));
+          w.ex.s = want;
+        }
         for (cudaEvent_t e : waits) TT_CUDA(cudaStreamWaitEvent(w.ex.s, e, 0));
         Scope sc(w.ar);
         SelfScope me(id);

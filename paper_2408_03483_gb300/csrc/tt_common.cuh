@@ -113,10 +113,12 @@ struct TT {
 struct StreamPool {
   static constexpr size_t kSlots = 64, kSlotBytes = 256;  // int[16] then double[16]
   std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> streams_hi;  // the device's greatest stream priority
   std::vector<cudaEvent_t> events;
   char* pinned = nullptr;
   bool pinned_failed = false;
   cudaStream_t stream(size_t i);
+  cudaStream_t stream_hi(size_t i);
   cudaEvent_t event(size_t i);
   // slot i (< kSlots), or null if page-locked memory is unavailable
   char* slot(size_t i);
@@ -155,6 +157,12 @@ struct Exec {
   // sketch's width when larger than the default, set to the certified width
   // (null: default first sketch)
   int* rf_hint = nullptr;
+  // TSQR tile shape (tunable): leaf rows as a multiple of max(64, p rounded
+  // up to 32), and the largest merge fan-in (0: default).  Two multiples by
+  // default: at 4096^2 the step measured 136 ms with single ones, 124 with
+  // two, 122 with three and 125 with four (fewer leaves and merge nodes
+  // competing for the SMs), the same at 256^2.
+  int qr_leaf_mult = 2, qr_fanin = 0;
 };
 
 // Wait on the host until ex.s has drained (the sync point of a read-back).
@@ -187,7 +195,11 @@ class TaskGraph {
   ~TaskGraph();
   TaskGraph(const TaskGraph&) = delete;
   TaskGraph& operator=(const TaskGraph&) = delete;
-  int add(const char* name, int priority, Fn fn, const std::vector<int>& deps = {}, bool hold = false);
+  // urgent: queue the node's GPU work on a stream of the device's greatest
+  // priority (nodes on the step's longest dependency chain), so that the
+  // block scheduler places its CTAs before those of other nodes as SMs free up
+  int add(const char* name, int priority, Fn fn, const std::vector<int>& deps = {}, bool hold = false,
+          bool urgent = false);
   void depend(int node, int dep);
   void release(int node);
   void run();

@@ -93,3 +93,18 @@ def test_argument_errors_return_codes(lib):
     h = ctypes.c_void_p()
     assert lib.tt_fv_init(None, None, None, 0, None, ctypes.byref(h)) == capi.TT_ERR_ARG
     assert lib.tt_fv_stage(None, 0) == capi.TT_ERR_ARG
+
+
+def test_tile_shapes_without_gpu(lib):
+    """The TSQR tile shapes the batched form's tuner chooses from: shape 0 is
+    the default, and the solver workspace covers every shape (it is sized by
+    the largest footprint over them)."""
+    n = lib.tt_tile_shapes(None, None, 0)
+    assert n >= 2
+    lm = (ctypes.c_int32 * n)()
+    fi = (ctypes.c_int32 * n)()
+    assert lib.tt_tile_shapes(lm, fi, n) == n
+    assert (lm[0], fi[0]) == (2, 0)
+    assert len({(lm[i], fi[i]) for i in range(n)}) == n
+    assert all(1 <= lm[i] <= 8 and (fi[i] == 0 or fi[i] >= 2) for i in range(n))
+    assert lib.tt_fv_set_tile_shape(None, 0) != 0

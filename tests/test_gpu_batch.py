@@ -95,3 +95,38 @@ def test_batch_tune_picks_a_candidate(api):
         st = b.stats(i)
         assert st["device_status"] == 0 and max(st["rank"]) <= d["rank_cap"]
     b.close()
+
+
+def test_every_tile_shape_matches_oracle_b(api):
+    """Each TSQR tile shape (leaf rows, merge fan-in) only reorders the
+    rounding's round-off: an Upwind5 step at 256^2 (faces 256 x 768, so the
+    cores' TSQR trees have several leaves and merge levels) matches Oracle B
+    at equal ranks under every shape."""
+    shapes = api.tile_shapes()
+    assert shapes[0] == (2, 0)
+    w = dict(eqn="nonlinear", scheme="up5", n=256, steps=1, tol=1e-8, cap=24, ic="bumps", amp=0.1,
+             amp_range=(0.01, 0.1), nbumps=3, seed=77, cfl=0.4, f=0.0)
+    Q, p = initial_tt(w)
+    ref = TB.step(Q, w, p, seed=0)
+    scales = field_scales(ref, "nonlinear", p, p["dt"])
+    for k in range(len(shapes)):
+        s = api.Solver(dev(api, Q, w["cap"]), "nonlinear", "up5", 256, p["dt"], w["tol"], w["cap"], g=p["g"],
+                       H=p["H"], f=p["f"], seed=0)
+        s.set_tile_shape(k)
+        s.step(1)
+        check_fields(s.get(), ref, 1e-10, scales, what=("shape", k, shapes[k]))
+        s.close()
+
+
+def test_batch_tile_tuner_gives_each_member_a_shape(api):
+    inst = instances(api)
+    b = api.Batch([(dev(api, Q, d["rank_cap"]), d) for w, Q, p, d in inst], workers=4)
+    K = len(api.tile_shapes())
+    shape_of, rates = b.tune_tiles(steps_per_trial=1, rounds=1)
+    assert len(shape_of) == len(inst) and all(0 <= k < K for k in shape_of)
+    assert sorted(rates) == list(range(K)) and all(r > 0 for r in rates.values())
+    b.step(1)
+    for i, (_, _, _, d) in enumerate(inst):
+        st = b.stats(i)
+        assert st["device_status"] == 0 and max(st["rank"]) <= d["rank_cap"]
+    b.close()
