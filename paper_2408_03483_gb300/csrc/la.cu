@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <type_traits>
 #include <cooperative_groups.h>
+#include <mutex>
 
 #include "tt_common.cuh"
 
@@ -1032,6 +1033,9 @@ constexpr int SVD_MIXED_MIN = 8;      // FP32 pre-rotation from this deflated ra
 constexpr int SVD_MIXED_SWEEPS = 6;   // cap of FP32 sweeps
 constexpr float SVD_MIXED_TOL = 1e-5f;  // FP32 phase: rotate while |g| > 1e-5 sqrt(a b)
 constexpr int SVD_CHOLQR_MIN = 60;      // deflated rank from which V0 is orthonormalised by Cholesky QR
+constexpr int SVD_MAX_CLUSTER = 8;      // CTAs of the FP64 sweeps' cluster, at most
+// FP64 scratch of one CTA: Householder vectors, taus, V0 (twice), G or T
+__host__ __device__ inline size_t svd_scratch_doubles(int p) { return (size_t)4 * p * p + p; }
 
 __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restrict__ Min, int p, double tol, int cap,
                                                           double defl, double* US, double* Vout, double* sig,
@@ -1049,6 +1053,12 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   __shared__ float cnf[128];
   __shared__ double gam[64], rc_c[64], rc_s[64];  // per pair of a round (q/2 <= 56)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // a launch over a cluster of cl CTAs: every CTA runs the same steps on the
+  // same data up to the FP64 sweeps, each in its own slice of the scratch
+  // (the grid is one cluster: rank = blockIdx.x; cluster calls only when cl > 1)
+  namespace cg = cooperative_groups;
+  const int cl = (int)gridDim.x, me = (int)blockIdx.x;
+  scr += (size_t)me * svd_scratch_doubles(p);
   double* HV = scr;                  // Householder vectors, p x p
   double* htau = scr + (size_t)p * p;
   double* Vg = htau + p;             // pre-rotation scratch: pd x pd
@@ -1080,7 +1090,9 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   const double fro2 = s_fro2;
   if (!isfinite(fro2)) {
     // NaN/Inf input: flag it and return a rank-1 zero factorisation instead
-    // of letting non-finite norms drive the pivot and sort indices
+    // of letting non-finite norms drive the pivot and sort indices (CTA 0;
+    // the others leave: no cluster barrier has been reached)
+    if (me != 0) return;
     for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
       US[t] = 0.0;
       Vout[t] = ((t % p) == (t / p)) ? 1.0 : 0.0;
@@ -1444,6 +1456,30 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
     __syncthreads();
   }
   const double eps = DBL_EPSILON * p, eps2 = eps * eps;
+  // ---- 2b. FP64 sweeps.  In a cluster, CTA `me` takes the pairs
+  // [plo, phi) of every round and writes the two columns of A and V it
+  // rotates, and their norms, into every other CTA's shared memory, so that
+  // all CTAs hold the same A, V and norms after each round's cluster
+  // barrier; every pair sees the same inputs as in one CTA, so the result
+  // is bit-identical to the single-CTA kernel.
+  const int npairs = q / 2;
+  const int plo = (int)((long)npairs * me / cl), phi = (int)((long)npairs * (me + 1) / cl);
+  // stores of a value into the same shared-memory slot of every CTA
+  auto put_all = [&](double* slot, double v) {
+    if (cl == 1) {
+      *slot = v;
+    } else {
+      cg::cluster_group cluster = cg::this_cluster();
+      for (int cc = 0; cc < cl; ++cc) *cluster.map_shared_rank(slot, cc) = v;
+    }
+  };
+  auto csync = [&] {
+    if (cl > 1)
+      cg::this_cluster().sync();
+    else
+      __syncthreads();
+  };
+  csync();  // every CTA is running before its shared memory is written
   int sweep = 0;
   for (; sweep < SVD_MAX_SWEEPS && pd > 1; ++sweep) {
     // exact squared column norms at the start of the sweep; inside the sweep
@@ -1458,13 +1494,15 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
       s_rot = 0;
       s_tmax = 0;
     }
-    __syncthreads();
+    // in a cluster, no CTA updates another's norms before that one has
+    // computed them
+    csync();
     for (int step = 0; step < q - 1; ++step) {
       // (a) H lanes per pair: the off-diagonal g = <c_i, c_j>
-      for (int base = w * PW; base < q / 2; base += nw * PW) {
+      for (int base = plo + w * PW; base < phi; base += nw * PW) {
         const int pr = base + lane / H;
         int i = 0, j = 0;
-        bool ok = pr < q / 2;
+        bool ok = pr < phi;
         if (ok) {
           i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
           j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
@@ -1483,7 +1521,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
       // (b) warp 0, one lane per pair: the rotations of the whole round (an
       // FP64 instruction costs its SMSP the same with 1 or 32 active lanes)
       if (w == 0) {
-        for (int pr = lane; pr < q / 2; pr += 32) {
+        for (int pr = plo + lane; pr < phi; pr += 32) {
           const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
           const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
           double c = 1.0, sn = 0.0;
@@ -1508,8 +1546,9 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
                 t = (dd >= 0.0 ? 2.0 * ga : -2.0 * ga) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * ga * ga)));
               c = rsqrt(fma(t, t, 1.0));
               sn = c * t;
-              cn[i] = fma(-t, ga, al);
-              cn[j] = fma(t, ga, be);
+              const double ni = fma(-t, ga, al), nj = fma(t, ga, be);
+              put_all(&cn[i], ni);
+              put_all(&cn[j], nj);
               // |t| as its float bit pattern: non-negative floats order like ints
               atomicMax(&s_tmax, __float_as_int(fminf((float)fabs(t), 1.0f)));
               s_rot = 1;
@@ -1521,40 +1560,52 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
       }
       __syncthreads();
       // (c) H lanes per pair: apply the rotation to L and V (no shuffles:
-      // the lanes of a pair go their own way)
-      for (int pr = w * PW + lane / H; pr < q / 2; pr += nw * PW) {
+      // the lanes of a pair go their own way), in every CTA of the cluster
+      for (int pr = plo + w * PW + lane / H; pr < phi; pr += nw * PW) {
         const double sn = rc_s[pr];
         if (sn == 0.0) continue;
         const double c = rc_c[pr];
         const int i = (pr == 0) ? 0 : 1 + ((pr - 1 + step) % (q - 1));
         const int j = 1 + ((q - 1 - pr - 1 + step) % (q - 1));
-        double* ci = A + (size_t)i * p;
-        double* cj = A + (size_t)j * p;
         for (int r = sub; r < p; r += H) {
-          const double x = ci[r], y = cj[r];
-          ci[r] = c * x - sn * y;
-          cj[r] = sn * x + c * y;
+          const double x = A[r + (size_t)i * p], y = A[r + (size_t)j * p];
+          const double nx = c * x - sn * y, ny = sn * x + c * y;
+          put_all(&A[r + (size_t)i * p], nx);
+          put_all(&A[r + (size_t)j * p], ny);
         }
-        double* vi = J + (size_t)i * pd;
-        double* vj = J + (size_t)j * pd;
         for (int r = sub; r < pd; r += H) {
-          const double x = vi[r], y = vj[r];
-          vi[r] = c * x - sn * y;
-          vj[r] = sn * x + c * y;
+          const double x = J[r + (size_t)i * pd], y = J[r + (size_t)j * pd];
+          const double nx = c * x - sn * y, ny = sn * x + c * y;
+          put_all(&J[r + (size_t)i * pd], nx);
+          put_all(&J[r + (size_t)j * pd], ny);
         }
       }
-      __syncthreads();
+      csync();
     }
-    if (s_rot == 0) break;
+    // the sweep's outcome over the cluster: every CTA reads every CTA's
+    // flags, then waits until all have read them before they are reset
+    int rot = s_rot, tmax = s_tmax;
+    if (cl > 1) {
+      cg::cluster_group cluster = cg::this_cluster();
+      for (int cc = 0; cc < cl; ++cc) {
+        rot |= *cluster.map_shared_rank(&s_rot, cc);
+        tmax = max(tmax, *cluster.map_shared_rank(&s_tmax, cc));
+      }
+      cluster.sync();
+    }
+    if (rot == 0) break;
     // every rotation of this sweep was below 1e-7: quadratic convergence puts
     // the remaining off-diagonal at ~1e-14 relative, so the confirming sweep
     // (which would rotate nothing above the threshold) is skipped
-    if (__int_as_float(s_tmax) < 1e-7f) {
+    if (__int_as_float(tmax) < 1e-7f) {
       ++sweep;
       break;
     }
     __syncthreads();
   }
+  // the rest runs in CTA 0 alone (no shared memory of another CTA is touched
+  // after the last cluster barrier)
+  if (me != 0) return;
   // ---- 3. singular values, order, truncation
   for (int j = w; j < pd; j += nw) {
     double s = 0.0;
@@ -1673,22 +1724,84 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
   }
 }
 
+// CTAs that share a p x p SVD's FP64 sweeps: each takes 1/cl of a round's
+// pairs for one cluster barrier per round, which pays where a round's work
+// (p/2 pairs of ~9p FP64 operations) is well above the barrier's cost.
+// TT_SVD_CLUSTER (environment, read once): 0 or 1 keeps one CTA, 2, 4 or 8
+// sets the size from p = 48 up.
+static int svd_cluster_size(int p) {
+  static const int forced = [] {
+    const char* e = std::getenv("TT_SVD_CLUSTER");
+    return e ? std::atoi(e) : -1;
+  }();
+  if (forced >= 0) return (forced == 2 || forced == 4 || forced == 8) && p >= 48 ? forced : 1;
+  return p >= 96 ? 8 : p >= 48 ? 4 : 1;
+}
+
+static bool svd_cluster_ok(int cl) {
+  static int ok[SVD_MAX_CLUSTER + 1] = {};  // 0 unknown, 1 yes, 2 no
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (ok[cl] == 0) {
+    ok[cl] = 2;
+    if (smem_attr_once_impl(reinterpret_cast<const void*>(k_svd_small)) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cl);
+      cfg.blockDim = dim3(SVD_THREADS);
+      cfg.dynamicSmemBytes = 2 * (size_t)112 * 112 * 8;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, k_svd_small, &cfg) == cudaSuccess && nc > 0) ok[cl] = 1;
+      (void)cudaGetLastError();
+    }
+  }
+  return ok[cl] == 1;
+}
+
 void jacobi_svd(Exec& ex, const double* M, int p, double tol, int cap, double* US, double* V, double* sig,
                 int* k_out, double* tail_out) {
   TT_REQUIRE(p >= 1 && p <= 112, TT_ERR_ARG);
   Scope sc(*ex.ar);
-  double* scr = ex.ar->get<double>((size_t)4 * p * p + p);
+  // scratch for the cluster size of p whatever the device supports, so that
+  // the sizing pass needs no device
+  const int cl_want = svd_cluster_size(p);
+  double* scr = ex.ar->get<double>((size_t)cl_want * svd_scratch_doubles(p));
   if (ex.dry) return;
   const size_t smem = 2 * (size_t)p * p * 8;
   smem_attr_once(k_svd_small);
+  const int cl = (cl_want > 1 && svd_cluster_ok(cl_want)) ? cl_want : 1;
   // deflation level: far below the truncation tolerance and the 1e-10 parity
   // bar on the FP64 path; the precision forms' cores carry FP32 round-off
   // (~1e-7 relative), so there it deflates at 1e-2 of their tolerance
   const double defl = ex.precision == TT_FP64 ? std::max(std::min(1e-13, 1e-2 * tol), 1e-15)
                                               : std::max(1e-2 * tol, 1e-13);
   // algorithmic work: pivoted QR (4/3 p^3) plus a nominal 3 Jacobi sweeps
-  TT_KERNEL(ex, K_JACOBI, 4.0 / 3.0 * p * (double)p * p + 3.0 * (p * (p - 1) / 2.0) * 18.0 * p,
-            8.0 * 4.0 * p * (double)p,
+  const double fl = 4.0 / 3.0 * p * (double)p * p + 3.0 * (p * (p - 1) / 2.0) * 18.0 * p;
+  if (cl > 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(SVD_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ex.s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    TT_KERNEL(ex, K_JACOBI, fl, 8.0 * 4.0 * p * (double)p,
+              TT_CUDA(cudaLaunchKernelEx(&cfg, k_svd_small, M, p, tol, cap, defl, US, V, sig, k_out, tail_out, scr,
+                                         ex.dev_status)));
+    return;
+  }
+  TT_KERNEL(ex, K_JACOBI, fl, 8.0 * 4.0 * p * (double)p,
             k_svd_small<<<1, SVD_THREADS, smem, ex.s>>>(M, p, tol, cap, defl, US, V, sig, k_out, tail_out, scr,
                                                         ex.dev_status));
 }
