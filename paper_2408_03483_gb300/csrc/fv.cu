@@ -1318,6 +1318,7 @@ tt_status tt_fv_init(const tt_fv_params* p, const tt2 q0[3], void* ws, size_t ws
     S.ex.prof = &S.prof;
     S.ex.pool = &S.pool;
     S.ex.precision = p->precision;
+    S.ex.svd_cluster = false;  // a stage runs many roundings at once
     for (int c = 0; c < 3; ++c) {
       S.Qn[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);
       S.Qs[c] = alloc_tt(S.ar, p->nx, p->ny, p->rank_cap);

@@ -1726,9 +1726,11 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd_small(const double* __restr
 
 // CTAs that share a p x p SVD's FP64 sweeps: each takes 1/cl of a round's
 // pairs for one cluster barrier per round, which pays where a round's work
-// (p/2 pairs of ~9p FP64 operations) is well above the barrier's cost.
-// TT_SVD_CLUSTER (environment, read once): 0 or 1 keeps one CTA, 2, 4 or 8
-// sets the size from p = 48 up.
+// (p/2 pairs of ~9p FP64 operations) is well above the barrier's cost
+// (p = 68: 2.8 -> 2.0 ms, p = 112: 9.5 -> 5.9 ms).  Used where the Exec allows
+// it (the standalone entry points, not the solver's stages).  TT_SVD_CLUSTER
+// (environment, read once): 0 or 1 keeps one CTA, 2, 4 or 8 sets the size from
+// p = 48 up.
 static int svd_cluster_size(int p) {
   static const int forced = [] {
     const char* e = std::getenv("TT_SVD_CLUSTER");
@@ -1775,7 +1777,7 @@ void jacobi_svd(Exec& ex, const double* M, int p, double tol, int cap, double* U
   if (ex.dry) return;
   const size_t smem = 2 * (size_t)p * p * 8;
   smem_attr_once(k_svd_small);
-  const int cl = (cl_want > 1 && svd_cluster_ok(cl_want)) ? cl_want : 1;
+  const int cl = (cl_want > 1 && ex.svd_cluster && svd_cluster_ok(cl_want)) ? cl_want : 1;
   // deflation level: far below the truncation tolerance and the 1e-10 parity
   // bar on the FP64 path; the precision forms' cores carry FP32 round-off
   // (~1e-7 relative), so there it deflates at 1e-2 of their tolerance

@@ -154,6 +154,7 @@ static void child_exec(const Exec& parent, Exec& c, Arena* a, cudaStream_t s, Pr
   c.precision = parent.precision;
   c.qr_leaf_mult = parent.qr_leaf_mult;
   c.qr_fanin = parent.qr_fanin;
+  c.svd_cluster = parent.svd_cluster;
   c.pivot_net = parent.pivot_net;
   c.pivot_rec = parent.pivot_rec;
   c.h_pinned = hi;

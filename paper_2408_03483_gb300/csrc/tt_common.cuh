@@ -163,6 +163,11 @@ struct Exec {
   // two, 122 with three and 125 with four (fewer leaves and merge nodes
   // competing for the SMs), the same at 256^2.
   int qr_leaf_mult = 2, qr_fanin = 0;
+  // the small SVD may spread its FP64 sweeps over a thread-block cluster: on
+  // for the standalone entry points, off in the solver, whose stage runs many
+  // roundings at once (the 4096^2 step measured 1.5 % faster with one CTA per
+  // SVD: 122.3 / 123.2 against 124.5 / 124.5 ms)
+  bool svd_cluster = true;
 };
 
 // Wait on the host until ex.s has drained (the sync point of a read-back).
