@@ -28,7 +28,12 @@
  *   kernels then produce a harmless placeholder instead of indexing with
  *   it); TT_ERR_TIMEOUT: a tensor-core kernel's bounded wait expired.
  *   Reaching a rank cap truncates to the cap and is counted, not an error.
- * - All arithmetic is IEEE FP64.
+ * - Arithmetic: IEEE FP64 throughout in the plain path (precision TT_FP64);
+ *   the precision forms (TT_FP32, TT_TF32, TT_BF16) run the rounding
+ *   contractions in FP32 on CUDA cores or on tcgen05 tensor cores with FP32
+ *   accumulation (split operands, FP32-accurate), while the small SVDs,
+ *   maxvol's choices of rows, the Taylor scaling and every stored core stay
+ *   FP64; tt_contract exposes the contraction in each precision.
  */
 #ifndef TT_FV_H
 #define TT_FV_H
@@ -86,7 +91,9 @@ typedef struct {
   double dt;          /* time step */
   double tol;         /* relative Frobenius truncation tolerance of every round */
   int32_t rank_cap;   /* rank cap of every round */
-  int32_t precision;  /* TT_FP64, or TT_FP32: the precision form (FP32 rounding contractions, FP64 SVDs) */
+  int32_t precision;  /* TT_FP64 (plain), or a precision form: TT_FP32 (FP32 rounding contractions on CUDA
+                         cores), TT_TF32 / TT_BF16 (their large products on tcgen05 with split operands);
+                         SVDs and stored cores stay FP64 */
   int32_t pivots;     /* TT_PIVOT_MAXVOL, or TT_PIVOT_LEARNED: crosses start from the pivots of the
                          network set by tt_fv_set_pivot_net (maxvol start until one is set) */
   int32_t kick;       /* cross kick fibres per sweep (default 4 if <= 0) */
