@@ -121,12 +121,17 @@ typedef struct {
                              solution, 1..TT_MAX_WAVES; the workspace is sized for it */
 } tt_fv_params;
 
-/* One plane wave of an external source: amp cos(kx x + ky y - omega t + phase)
- * on the right-hand side of field `field` (0: h or eta, 1: hu or u, 2: hv or v),
- * e.g. the forcing that makes the manufactured solution of Sec. 5.4 exact. */
+/* One wave amp exp(-decay x) cos(kx x + ky y - omega t + phase) of field
+ * `field` (0: h or eta, 1: hu or u, 2: hv or v): a plane wave when decay = 0,
+ * e.g. a term of the forcing that makes the manufactured solution of Sec. 5.4
+ * exact or of the barotropic tide of Sec. 5.3; damped in x when decay > 0,
+ * e.g. a term of the coastal Kelvin wave of Sec. 5.1 (decay = 1/R).  Its cell
+ * averages are exact: the y factor's centre value times sinc(ky dy/2), the x
+ * factors' from the integral of exp((-decay + i kx) x) over the cell. */
 typedef struct {
   int32_t field;
   double amp, kx, ky, omega, phase;
+  double decay;
 } tt_wave;
 enum { TT_MAX_WAVES = 16 };
 

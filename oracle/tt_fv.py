@@ -408,23 +408,41 @@ def _tol_u(w, c):
 
 
 def waves_tt(waves, field, n1, n2, t, lx, ly, rows=None):
-    """Cell averages of sum amp cos(kx x + ky y - omega t + phase) over the
-    waves of `field` as TT cores (first core on the x cells `rows`, by
-    default 0..n1-1): a plane wave averaged over a cell is its centre value
-    times sinc(kx dx/2) sinc(ky dy/2), and cos(a + b) = cos a cos b -
-    sin a sin b is rank 2."""
+    """Cell averages of sum amp exp(-decay x) cos(kx x + ky y - omega t +
+    phase) over the waves of `field` as TT cores (first core on the x cells
+    `rows`, by default 0..n1-1).  A wave is (field, amp, kx, ky, omega,
+    phase[, decay]); decay = 0 unless given (the coastal Kelvin wave of
+    Sec. 5.1 has decay = 1/R).  cos(a + b) = cos a cos b - sin a sin b is rank
+    2; the y factors average to their centre values times sinc(ky dy/2); the x
+    factors exp(-decay x) cos(kx x) and -exp(-decay x) sin(kx x) average to
+    the real and minus the imaginary part of (1/dx) times the integral of
+    exp(w x), w = -decay + i kx, over the cell -- for decay = 0 their centre
+    values times sinc(kx dx/2)."""
     dx, dy = lx / n1, ly / n2
-    xc = ((np.arange(n1) if rows is None else np.asarray(rows)) + 0.5) * dx
+    xi = np.arange(n1) if rows is None else np.asarray(rows)
+    xc = (xi + 0.5) * dx
     yc = (np.arange(n2) + 0.5) * dy
     A, B = [], []
-    for c, amp, kx, ky, om, ph in waves:
+    for wave in waves:
+        c, amp, kx, ky, om, ph = wave[:6]
+        decay = wave[6] if len(wave) > 6 else 0.0
         if c != field:
             continue
-        sx = np.sinc(kx * dx / (2 * np.pi))  # numpy's sinc is sin(pi z)/(pi z)
-        sy = np.sinc(ky * dy / (2 * np.pi))
-        a = kx * xc
+        sy = np.sinc(ky * dy / (2 * np.pi))  # numpy's sinc is sin(pi z)/(pi z)
+        if decay == 0.0:
+            sx = np.sinc(kx * dx / (2 * np.pi))
+            a = kx * xc
+            fc, fs = sx * np.cos(a), sx * np.sin(a)
+        else:
+            wz = complex(-decay, kx)
+            lo = xi * dx
+            # (e^{w hi} - e^{w lo}) / (w dx) = e^{w lo} (e^{w dx} - 1) / (w dx)
+            step = complex(np.expm1(-decay * dx) * np.cos(kx * dx) - 2.0 * np.sin(kx * dx / 2) ** 2,
+                           np.exp(-decay * dx) * np.sin(kx * dx))
+            val = np.exp(wz * lo) * step / (wz * dx)
+            fc, fs = val.real, val.imag
         b = ky * yc - om * t + ph
-        A += [sx * np.cos(a), -sx * np.sin(a)]
+        A += [fc, -fs]
         B += [amp * sy * np.cos(b), amp * sy * np.sin(b)]
     if not A:
         return None

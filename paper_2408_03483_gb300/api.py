@@ -235,12 +235,12 @@ class Solver:
         C.check("tt_fv_set", self.lib.tt_fv_set(self.h, arr))
 
     def set_forcing(self, waves, t0=0.0):
-        """waves: (field, amp, kx, ky, omega, phase) plane waves of the source."""
+        """waves: (field, amp, kx, ky, omega, phase[, decay]) waves of the source."""
         arr = (C.tt_wave * max(1, len(waves)))(*[C.tt_wave(int(f), *map(float, rest)) for f, *rest in waves])
         C.check("tt_fv_set_forcing", self.lib.tt_fv_set_forcing(self.h, arr, len(waves), float(t0)))
 
     def set_boundary(self, waves, t0=0.0):
-        """waves: (field, amp, kx, ky, omega, phase) plane waves of the exact
+        """waves: (field, amp, kx, ky, omega, phase[, decay]) waves of the exact
         solution whose cell averages fill the x-boundary ghost cells."""
         arr = (C.tt_wave * max(1, len(waves)))(*[C.tt_wave(int(f), *map(float, rest)) for f, *rest in waves])
         C.check("tt_fv_set_boundary", self.lib.tt_fv_set_boundary(self.h, arr, len(waves), float(t0)))

@@ -54,7 +54,8 @@ class tt_fv_params(ctypes.Structure):
 
 class tt_wave(ctypes.Structure):
     _fields_ = [("field", ctypes.c_int32), ("amp", ctypes.c_double), ("kx", ctypes.c_double),
-                ("ky", ctypes.c_double), ("omega", ctypes.c_double), ("phase", ctypes.c_double)]
+                ("ky", ctypes.c_double), ("omega", ctypes.c_double), ("phase", ctypes.c_double),
+                ("decay", ctypes.c_double)]
 
 
 class tt_fv_stats(ctypes.Structure):

@@ -326,9 +326,31 @@ static int nq_of(int recon) { return recon == TT_UP3 ? 2 : 3; }
 struct WaveSet {
   int n;
   double amp[TT_MAX_WAVES], kx[TT_MAX_WAVES], ky[TT_MAX_WAVES], om[TT_MAX_WAVES], ph[TT_MAX_WAVES];
+  double dk[TT_MAX_WAVES];  // decay in x (0: a plane wave)
 };
 
 __device__ __forceinline__ double sinc_dev(double z) { return z == 0.0 ? 1.0 : sin(z) / z; }
+
+// Averages over the cell [i dx, (i + 1) dx] of exp(-dk x) cos(kx x) (cx) and
+// exp(-dk x) sin(kx x) (sx): for dk = 0 the centre values times
+// sinc(kx dx / 2); otherwise the real and imaginary parts of
+// exp(w x_i) (exp(w dx) - 1) / (w dx), w = -dk + i kx, with exp(w dx) - 1
+// formed from expm1 and a half-angle sine (no cancellation for small dx).
+__device__ __forceinline__ void wave_x(double kx, double dk, int i, double dx, double& cx, double& sx) {
+  if (dk == 0.0) {
+    const double a = kx * (i + 0.5) * dx, s = sinc_dev(0.5 * kx * dx);
+    cx = s * cos(a);
+    sx = s * sin(a);
+    return;
+  }
+  const double x1 = i * dx, e1 = exp(-dk * x1), c1 = cos(kx * x1), s1 = sin(kx * x1);
+  const double hs = sin(0.5 * kx * dx);
+  const double dr = expm1(-dk * dx) * cos(kx * dx) - 2.0 * hs * hs, di = exp(-dk * dx) * sin(kx * dx);
+  const double pr = e1 * (c1 * dr - s1 * di), pim = e1 * (c1 * di + s1 * dr);
+  const double m = 1.0 / ((dk * dk + kx * kx) * dx);
+  cx = (-dk * pr + kx * pim) * m;
+  sx = (-kx * pr - dk * pim) * m;
+}
 
 // Cell averages of sum_w amp_w cos(kx_w x + ky_w y - om_w t + ph_w) as a TT of
 // rank 2 n: A[:, 2w] = sx cos(kx xc), A[:, 2w+1] = -sx sin(kx xc),
@@ -341,8 +363,9 @@ __global__ void k_wave_cores(WaveSet w, double t, int n1, int n2, double dx, dou
   for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
     if (q < na) {
       const int i = int(q % n1), col = int(q / n1), v = col >> 1;
-      const double a = w.kx[v] * (i + 0.5) * dx, sx = sinc_dev(0.5 * w.kx[v] * dx);
-      A[q] = (col & 1) ? -sx * sin(a) : sx * cos(a);
+      double cx, sx;
+      wave_x(w.kx[v], w.dk[v], i, dx, cx, sx);
+      A[q] = (col & 1) ? -sx : cx;
     } else {
       const long r = q - na;
       const int j = int(r % n2), col = int(r / n2), v = col >> 1;
@@ -377,6 +400,7 @@ static bool source_tt(Solver& S, Exec& ex, int c, TT& out) {
       ws.ky[ws.n] = w.ky;
       ws.om[ws.n] = w.omega;
       ws.ph[ws.n] = w.phase;
+      ws.dk[ws.n] = w.decay;
       ws.n++;
     }
   const long total = (long)(S.p.nx + S.p.ny) * 2 * nw;
@@ -429,8 +453,9 @@ __global__ void k_extend_x(const double* __restrict__ A, const double* __restric
         if (!ghost) v = A[(i - kGhost) + (size_t)col * nx];
       } else if (ghost) {
         const int wc = col - r, wv = wc >> 1;
-        const double a = w.kx[wv] * (i - kGhost + 0.5) * dx, sx = sinc_dev(0.5 * w.kx[wv] * dx);
-        v = (wc & 1) ? -sx * sin(a) : sx * cos(a);
+        double cx, sx;
+        wave_x(w.kx[wv], w.dk[wv], i - kGhost, dx, cx, sx);
+        v = (wc & 1) ? -sx : cx;
       }
       Ae[q] = v;
     } else {
@@ -464,6 +489,7 @@ static TT extend_x(Solver& S, Exec& ex, const TT& q, int c) {
         ws.ky[ws.n] = w.ky;
         ws.om[ws.n] = w.omega;
         ws.ph[ws.n] = w.phase;
+        ws.dk[ws.n] = w.decay;
         ws.n++;
       }
     nw = ws.n;
@@ -1399,7 +1425,7 @@ tt_status tt_fv_set_forcing(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwaves
   for (int i = 0; i < nwaves; ++i) {
     const tt_wave& w = waves[i];
     if (w.field < 0 || w.field > 2 || !std::isfinite(w.amp) || !std::isfinite(w.kx) || !std::isfinite(w.ky) ||
-        !std::isfinite(w.omega) || !std::isfinite(w.phase))
+        !std::isfinite(w.omega) || !std::isfinite(w.phase) || !std::isfinite(w.decay))
       return TT_ERR_ARG;
     if (++per[w.field] > S.p.forcing_waves) return TT_ERR_ARG;
   }
@@ -1416,7 +1442,7 @@ tt_status tt_fv_set_boundary(tt_fv_ctx* ctx, const tt_wave* waves, int32_t nwave
   for (int i = 0; i < nwaves; ++i) {
     const tt_wave& w = waves[i];
     if (w.field < 0 || w.field > 2 || !std::isfinite(w.amp) || !std::isfinite(w.kx) || !std::isfinite(w.ky) ||
-        !std::isfinite(w.omega) || !std::isfinite(w.phase))
+        !std::isfinite(w.omega) || !std::isfinite(w.phase) || !std::isfinite(w.decay))
       return TT_ERR_ARG;
     if (++per[w.field] > S.p.boundary_waves) return TT_ERR_ARG;
   }
